@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 int-GMRES + FP64 iterative-refinement solver.
+
+Metric: refined solves per second to a relative residual of 1e-10 (Fig. 1
+of Iwashita, Suzuki, Fukaya, ScalA'20 with the int-GMRES(m) inner solve of
+Fig. 2).  Default workload: 3D convection-diffusion, 7-point stencil on a
+128^3 grid (n = 2,097,152, nnz = 14,581,760), per-cell convection
+U[-50, 50], log-normal diffusion (sigma 1), b ~ U[-1, 1], integer ILU(0)
+(Sec. VI) and GMRES(50), synthetic data from a fixed seed.
+
+One step = one ir_solve of the whole system (setup done once, inputs
+resident in HBM).  The working set (matrix, factors, basis: ~2 GB) is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own replica
+(the systems are independent: weak scaling, no collective on the data
+path); value = all solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2009_07495_gb300 import workloads as W  # noqa: E402
+
+METRIC = "refined solves/s @1e-10 resid (int vs FP64 GMRES, 1 GB300); SpMV GB/s; p99 ms"
+KNAMES = ["spmv", "trsv_l", "trsv_u", "mgs", "mgs_last", "normalize", "resid"]
+KERNEL_SYMBOL = {"spmv": "k_spmv", "trsv_l": "k_trsv_int", "trsv_u": "k_trsv_int",
+                 "mgs": "k_mgs", "mgs_last": "k_mgs_last", "normalize": "k_normalize",
+                 "resid": "k_resid"}
+
+WORKLOADS = {
+    "cfg1": dict(desc="3D convection-diffusion 7-pt 128^3 (n=2,097,152, nnz=14,581,760), "
+                      "ILU(0) int-GMRES(50), FP64 refinement to 1e-10",
+                 gen=lambda: W.config1(), precond=1, m=50),
+    "cfg0": dict(desc="2D convection-diffusion 5-pt 32x32 (n=1024), int-GMRES(30), no "
+                      "preconditioning, FP64 refinement to 1e-10",
+                 gen=lambda: W.config0(), precond=0, m=30),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int) -> float:
+    """Bytes the method must move per launch (the per-unit figures of the
+    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 4n; one MGS pass 4n (the
+    basis vector, w kept on chip); line 11 4n; one triangular solve
+    (nnz_tri + n) 12 + 16 n; FP64 residual nnz 12 + 4(n+1) + 24 n."""
+    if kind == "spmv":
+        return nnz * (val_bytes + 4) + 4 * (n + 1) + 4 * n
+    if kind in ("mgs", "mgs_last", "normalize"):
+        return 4.0 * n
+    if kind in ("trsv_l", "trsv_u"):
+        return (nnz_l + n) * 12 + 16 * n
+    if kind == "resid":
+        return nnz * 12 + 4 * (n + 1) + 24 * n
+    raise KeyError(kind)
+
+
+def launches_per_cycle(kind: str, m: int) -> int:
+    return {"spmv": m, "trsv_l": m, "trsv_u": m, "mgs": m * (m + 1) // 2, "mgs_last": m,
+            "normalize": m, "resid": 1}[kind]
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(p))[f"{workload}:{kernel}"]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2009_07495_gb300", "csrc", t["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return t["bytes_per_launch"] if sha == t["sha256"] else None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(sysw, precond: int, m: int, refinements: int, budget_s: float = 30.0):
+    """The oracle, single-threaded, on a bounded sample: its set-up plus one
+    inner solve of the full system (one of the `refinements` the full solve
+    needs), extrapolated to solves/s."""
+    import oracle
+    oracle.build()
+    P = oracle.Params.table5(m=m) if precond else oracle.Params.table4(m=m)
+    t0 = time.perf_counter()
+    d = oracle.setup(sysw.rowptr, sysw.col, sysw.val, sysw.b, P)
+    t_setup = time.perf_counter() - t0
+    bk = d["b"] / np.abs(d["b"]).max()
+    t0 = time.perf_counter()
+    r = oracle.resid_fp(d["rowptr"], d["col"], d["a"], np.zeros(sysw.n), d["b"])
+    oracle.int_gmres(P, d, bk)
+    t_cyc = time.perf_counter() - t0
+    per_solve = t_setup + refinements * t_cyc
+    del r
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle set-up ({t_setup:.2f} s) + 1 of {refinements} refinements "
+                      f"(residual + one int-GMRES({m}) solve, {t_cyc:.1f} s) of the full "
+                      f"workload, extrapolated x{refinements}"}
+
+
+def run_reference(args, wl):
+    """--impl reference: the oracle on the host cores, same workload/metric."""
+    if args.gpus > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    sysw = wl["gen"]()
+    import oracle
+    oracle.build()
+    P = oracle.Params.table5(m=wl["m"]) if wl["precond"] else oracle.Params.table4(m=wl["m"])
+    refinements = wl.get("refinements", 0)
+    if sysw.n <= 50000:
+        # small workload: whole refined solves
+        steps = args.steps
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            x, rep = oracle.ir_solve(sysw.rowptr, sysw.col, sysw.val, sysw.b, P)
+        dt = time.perf_counter() - t0
+        value = steps / dt
+        sample = f"{steps} full oracle solves"
+    else:
+        steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        d = oracle.setup(sysw.rowptr, sysw.col, sysw.val, sysw.b, P)
+        t_setup = time.perf_counter() - t0
+        bk = d["b"] / np.abs(d["b"]).max()
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            oracle.resid_fp(d["rowptr"], d["col"], d["a"], np.zeros(sysw.n), d["b"])
+            oracle.int_gmres(P, d, bk)
+            ts.append(time.perf_counter() - t0)
+        t_cyc = statistics.median(ts)
+        value = 1.0 / (t_setup + refinements * t_cyc)
+        dt = sum(ts)
+        sample = (f"oracle set-up + {steps} inner solves (one refinement each) of the full "
+                  f"workload, extrapolated to the {refinements} refinements of a solve")
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": 1000.0 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, wl):
+    import torch
+    from paper_2009_07495_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    L.load()
+
+    sysw = wl["gen"]()
+    n, nnz = sysw.n, sysw.nnz
+    P = L.params_default(wl["precond"], wl["m"])
+    rp = torch.from_numpy(sysw.rowptr).to(dev)
+    cl = torch.from_numpy(sysw.col).to(dev)
+    vl = torch.from_numpy(sysw.val).to(dev)
+    bh = torch.from_numpy(sysw.b).to(dev)
+    xh = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = L.Solver(rp, cl, vl, P, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    rep = None
+    for _ in range(args.warmup):
+        _, rep = solver.ir_solve(bh, xh, stream=stream)
+    torch.cuda.synchronize(dev)
+    assert rep is None or rep["status"] == "ok", rep
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    l0 = L.load().igm_kernel_launches()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        _, rep = solver.ir_solve(bh, xh, stream=stream)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = L.load().igm_kernel_launches() - l0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+    assert rep["status"] == "ok" and rep["relres"] < 1e-10, rep
+    refinements = rep["refinements"]
+
+    # per-kernel device time (same kernels, same launch configuration)
+    import ctypes as C
+    buf = (C.c_double * 7)()
+    st = L.load().igm_time_kernels(solver.handle, 5, buf, stream.cuda_stream)
+    if st != 0:
+        raise RuntimeError(L.load().igm_last_error().decode())
+    kms = np.array(buf[:])
+    nnz_l = (nnz - n) // 2 if wl["precond"] else 0
+    val_bytes = 8 if P.alpha_a > 30 else 4
+    kern = {}
+    for k, name in enumerate(KNAMES):
+        if kms[k] < 0:
+            continue
+        per_cycle = launches_per_cycle(name, wl["m"])
+        kern[name] = dict(ms=kms[k], launches_per_solve=per_cycle * refinements,
+                          ms_per_solve=kms[k] * per_cycle * refinements,
+                          gbs=algorithmic_bytes(name, n, nnz, nnz_l, val_bytes) / (kms[k] * 1e6))
+    tot_k = sum(v["ms_per_solve"] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
+    peak, peak_src = peak_hbm()
+    ach = kern[dom]["gbs"]
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic_for(KERNEL_SYMBOL[dom], args.workload),
+                "kernel": KERNEL_SYMBOL[dom] + (f" ({dom})" if dom.startswith("trsv") else ""),
+                "peak_source": peak_src,
+                "share_of_solve": kern[dom]["ms_per_solve"] / (total_ms / args.steps)}
+    kernels = {k: {"ms_per_launch": round(v["ms"], 5), "algorithmic_GBs": round(v["gbs"], 1),
+                   "frac_of_peak": round(v["gbs"] / peak, 4),
+                   "share": round(v["ms_per_solve"] / tot_k, 4)} for k, v in kern.items()}
+
+    # end to end through the C ABI with host buffers: set-up from pinned host
+    # CSR + solve from a pinned host right-hand side + solution back to host
+    e2e = None
+    if args.e2e_steps > 0:
+        hrp = torch.from_numpy(sysw.rowptr).pin_memory()
+        hcl = torch.from_numpy(sysw.col).pin_memory()
+        hvl = torch.from_numpy(sysw.val).pin_memory()
+        hb = torch.from_numpy(sysw.b).pin_memory()
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        solver.close()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s2 = L.Solver(hrp, hcl, hvl, P, stream=stream)
+            _, r2 = s2.ir_solve(hb, hx, stream=stream)
+            s2.close()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        assert r2["status"] == "ok"
+        e2e = {"value": world * args.e2e_steps / dt, "unit": "solves/s",
+               "h2d_bytes_per_step": int(4 * (n + 1) + 4 * nnz + 8 * nnz + 8 * n),
+               "d2h_bytes_per_step": int(8 * n + 1192),
+               "includes": "int_gmres_setup (scaling, cast, ILU(0)) + ir_solve + destroy"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "m": wl["m"],
+                       "refinements": refinements, "relres": rep["relres"],
+                       "inner_steps": rep["inner_steps"],
+                       "l2": "working set (~2 GB) > L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "p50_ms": float(np.percentile(step_ms, 50)),
+            "p99_ms": float(np.percentile(step_ms, 99)),
+            "spmv_GBs": kern["spmv"]["gbs"],
+            "roofline": roofline, "kernels": kernels,
+            "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(sysw, wl["precond"], wl["m"], refinements)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    wl = dict(WORKLOADS[args.workload])
+    if args.impl == "reference":
+        wl["refinements"] = REFINEMENTS.get(args.workload, 4)
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+# refinements a full solve of each workload takes (identical for the oracle
+# and the CUDA path, which agree bit for bit); used only to extrapolate the
+# reference arm's bounded sample
+REFINEMENTS = {"cfg1": 6, "cfg0": 9}
+
+if __name__ == "__main__":
+    main()

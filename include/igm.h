@@ -1,0 +1,196 @@
+/*
+ * igm.h -- C ABI of the GB300 (sm_103a) integer-arithmetic GMRES solver with
+ * FP64 iterative refinement.
+ *
+ * Method: T. Iwashita, K. Suzuki, T. Fukaya, "An Integer Arithmetic-Based
+ * Sparse Linear Solver Using a GMRES Method and Iterative Refinement",
+ * ScalA'20 (arXiv:2009.07495).  Section, equation, figure and table numbers
+ * below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are CSR: rowptr int32[n+1] (rowptr[0] = 0), col int32[nnz]
+ *    with columns strictly ascending inside each row, val float64[nnz].
+ *    With ILU(0) every row must store its diagonal.
+ *  - Array arguments may be device pointers or host pointers (pageable or
+ *    pinned); the library detects which (cudaPointerGetAttributes) and, for
+ *    host memory, copies on `stream` and synchronises before returning.
+ *    Device inputs are read in stream order on `stream`.
+ *  - Ownership: the library never keeps caller pointers.  Setup copies what
+ *    it needs into memory owned by the handle; outputs are written into
+ *    caller memory on `stream`.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - Every call returns an igm_status and never throws or aborts.  Device
+ *    waits are bounded: an expired wait is reported as IGM_ETIMEOUT, never
+ *    as a hang or a trap.  igm_last_error() returns a message for the last
+ *    failing call of the calling thread.
+ *  - Overflow of a fixed-point word is not an error (the paper's hardware
+ *    wraps too): each event is counted per line of Fig. 2 in the report.
+ *  - Handles are not thread-safe; one handle may be used by one stream at a
+ *    time.  Different handles are independent.
+ */
+#ifndef IGM_H
+#define IGM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct igm_handle_s *igm_handle;
+typedef struct igm_server_s *igm_server;
+
+typedef enum {
+  IGM_OK = 0,
+  IGM_EINVAL = 1,       /* malformed argument or matrix                     */
+  IGM_EZERO_ROW = 2,    /* a row of A is zero: eq. (3) has no scale        */
+  IGM_EZERO_PIVOT = 3,  /* ILU(0) pivot (or its integer cast) is zero       */
+  IGM_EBREAKDOWN = 4,   /* reserved                                         */
+  IGM_ENOCONV = 5,      /* Fig. 1 loop reached max_refine above tol         */
+  IGM_EOOM = 6,         /* device memory budget or cudaMalloc exhausted     */
+  IGM_ETIMEOUT = 7,     /* a bounded device wait expired                    */
+  IGM_ECUDA = 8         /* a CUDA runtime call failed                       */
+} igm_status;
+
+/* Indices of igm_report.ev: overflow events per line of Fig. 2. */
+enum {
+  IGM_EV_L5 = 0,     /* line 5: integer matrix-vector product              */
+  IGM_EV_L5P = 1,    /* line 5': integer forward/backward substitution     */
+  IGM_EV_L7 = 2,     /* line 7: inner product                              */
+  IGM_EV_L8 = 3,     /* line 8: vector update                              */
+  IGM_EV_L10 = 4,    /* line 10: norm                                      */
+  IGM_EV_L11 = 5,    /* line 11: vector / scalar                           */
+  IGM_EV_L13 = 6,    /* line 13: previous Givens rotations                 */
+  IGM_EV_L15 = 7,    /* line 15: 2-element norm                            */
+  IGM_EV_L16 = 8,    /* line 16: c, s divisions                            */
+  IGM_EV_L17 = 9,    /* line 17: g update                                  */
+  IGM_EV_VRANGE = 10,/* a basis entry outside int32 (informational)       */
+  IGM_EV_L2 = 11,    /* line 2: FP -> int cast out of range                */
+  IGM_EV_COUNT = 16
+};
+
+/* Parameters of the method (Sec. II, III, V-D, VII; Tables 3-5). */
+typedef struct {
+  int df;        /* fractional bits d_f of the Q(d_m).(d_f) int64 word (30)  */
+  int alpha_a;   /* initial scaling exponent of eq. (3): 16 none, 32 ILU     */
+  int m;         /* Arnoldi steps per inner solve, 1..IGM_MAX_M              */
+  int precond;   /* 0: none; 1: integer ILU(0) (Sec. VI-A, lines 1', 5')     */
+  int beta7;     /* line 7: shift of w (beta1; beta2 = 0)                    */
+  int beta8;     /* line 8: shift of h (beta1)                               */
+  int beta10;    /* line 10: beta1 = beta2                                   */
+  int beta11a, beta11b; /* line 11: divide, beta1 (x2^) and beta2 (/2^)      */
+  int beta13;    /* line 13: shift of h (beta2; beta1 = 0)                   */
+  int beta15;    /* line 15: beta1 = beta2                                   */
+  int beta16a, beta16b; /* line 16: divide                                   */
+  double tol;    /* epsilon of Fig. 1 (relative residual of the scaled system)*/
+  int max_refine;/* maximum inner solves in Fig. 1                           */
+  int inner;     /* 0: int-GMRES (Fig. 2); 1: FP64 GMRES(m) ("Double")       */
+  int reserved[6];
+} igm_params;
+
+#define IGM_MAX_M 128
+
+/* Per-solve report.  Histories are indexed by refinement k (Fig. 1). */
+typedef struct {
+  long long ev[IGM_EV_COUNT]; /* overflow events per line of Fig. 2         */
+  int refinements;            /* inner solves performed                     */
+  int inner_steps;            /* Arnoldi steps over all inner solves        */
+  int breakdowns;             /* inner solves that ended before m steps     */
+  int status;                 /* igm_status of the solve                    */
+  double relres;              /* final ||b - A x|| / ||b||, scaled system   */
+  double relres_unscaled;     /* final ||bh - Ah xh|| / ||bh||              */
+  double gamma_hist[64];      /* gamma^(k) of eq. (gammak)                  */
+  double relres_hist[65];     /* relative residual before refinement k      */
+} igm_report;
+
+/* Fills p with the paper's settings: d_f = 30 (Sec. VII-B); precond = 0:
+ * alpha_a = 16 and the shifts of Table 4; precond = 1: alpha_a = 32 and the
+ * shifts of Table 5; tol = 1e-10, max_refine = 60, inner = 0. */
+igm_status igm_params_default(igm_params *p, int precond, int m);
+
+/* Setup of Fig. 1 on the device (steps before the refinement loop):
+ * the initial row scaling of eq. (1)/(3), the cast of Sec. IV-B
+ * (Abar_0 = trunc(A), s = 0), and with precond = 1 the FP64 ILU(0) of
+ * eq. (ilu) and its integer factors Lbar, Ubar of eq. (dldr)-(ilu2).
+ * n >= 1 rows, nnz entries; rowptr/col/val as in the conventions above.
+ * On success *out owns all device state of the system (about
+ * nnz*(12 + 8*precond... ) + (m+8)*8*n bytes).  Errors: IGM_EINVAL,
+ * IGM_EZERO_ROW, IGM_EZERO_PIVOT, IGM_EOOM, IGM_ECUDA. */
+igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
+                           const double *val, const igm_params *params,
+                           void *stream, igm_handle *out);
+
+/* One inner solve of Fig. 2 (lines 1-23; lines 1', 5' with precond = 1) on
+ * the SCALED system of the handle, with the argument types of Table 2:
+ * bk (n doubles, input) is b^(k), xk (n doubles, input/output) is the
+ * initial guess on entry and the guess plus the int-GMRES correction on
+ * return.  rep may be NULL; if given, ev/inner_steps/breakdowns describe
+ * this solve. */
+igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk,
+                           igm_report *rep, void *stream);
+
+/* The refinement loop of Fig. 1 for the ORIGINAL system Ah xh = bh:
+ * b = D^-1 bh, then repeat { r = b - A x; stop if ||r||/||b|| < tol;
+ * gamma = max|r_i|; inner solve of A x^(k) = r/gamma; x += gamma x^(k) },
+ * xh = x (eq. 1 leaves x unscaled).  bhat, xhat: n doubles.  rep may be
+ * NULL.  Returns IGM_ENOCONV when max_refine is reached first. */
+igm_status ir_solve(igm_handle h, const double *bhat, double *xhat,
+                    igm_report *rep, void *stream);
+
+/* ir_solve for `count` independent systems in one launch sequence: every
+ * kernel covers all systems at once (block-diagonal tiling), each system
+ * keeps its own refinement state and stops independently, and each result
+ * is bit-identical to ir_solve on that handle alone.  hs[i], bhat[i],
+ * xhat[i] (device or host), reps[i] (may be NULL as a whole).  The handles
+ * must be distinct and share one m. */
+igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat,
+                            double *const *xhat, igm_report *reps, void *stream);
+
+/* Copies the integer state of the last inner solve to caller memory (host
+ * or device), for inspection and tests; any pointer may be NULL.
+ * V: (m+1)*n int64 (basis, row-major by vector), H: (m+1)*m int64
+ * (column-major, after the Givens rotations of lines 12-19), cs, sn: m,
+ * g: m+1, jeff: Arnoldi columns used, nu: ||r0|| of line 1. */
+igm_status int_gmres_get_state(igm_handle h, long long *V, long long *H,
+                               long long *cs, long long *sn, long long *g,
+                               int *jeff, double *nu);
+
+/* Kernels that igm_time_kernels can time (one launch each, on the handle's
+ * current state, in the launch configuration of the solver). */
+enum {
+  IGM_K_SPMV = 0,       /* line 5, step j = m/2                            */
+  IGM_K_TRSV_L = 1,     /* line 5' forward substitution                    */
+  IGM_K_TRSV_U = 2,     /* line 5' backward substitution                   */
+  IGM_K_MGS = 3,        /* lines 7-8, one fused pass (i = m/2, j = m-1)     */
+  IGM_K_MGS_LAST = 4,   /* line 8 + line 10 + lines 12-19 (j = m-1)        */
+  IGM_K_NORMALIZE = 5,  /* line 11                                         */
+  IGM_K_RESID = 6,      /* eq. (b), FP64 residual of Fig. 1                */
+  IGM_K_COUNT = 7
+};
+
+/* Average device time per launch (ms) of each kernel kind above, measured
+ * with CUDA events around `reps` back-to-back launches on `stream` after a
+ * solve has been run on the handle (the launches overwrite the solver's
+ * scratch state, not the matrix or the last solution).  ms: IGM_K_COUNT
+ * doubles (host), -1 for kinds that do not apply (substitutions without
+ * ILU).  Errors: IGM_EINVAL, IGM_ECUDA. */
+igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream);
+
+/* Number of kernels the library has launched in this process (a graph
+ * launch counts its kernel nodes). */
+long long igm_kernel_launches(void);
+
+/* Bytes of device memory the handle holds. */
+long long int_gmres_device_bytes(igm_handle h);
+
+/* Releases everything the handle owns.  NULL is ignored. */
+void int_gmres_destroy(igm_handle h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *igm_last_error(void);
+
+/* Library version string. */
+const char *igm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGM_H */

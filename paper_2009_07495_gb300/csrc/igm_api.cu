@@ -1,0 +1,728 @@
+// igm_api.cu -- host side of the C ABI declared in include/igm.h: handles,
+// device memory arenas, batches (tile tables), and the refinement driver of
+// Fig. 1, whose per-refinement launch sequence is captured once into two
+// CUDA graphs (the convergence test, and one inner solve of Fig. 2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "igm_launch.h"
+
+using namespace igm;
+
+namespace {
+
+thread_local std::string g_err;
+
+igm_status fail(igm_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      cudaGetLastError();                                                         \
+      return fail(IGM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                             \
+  } while (0)
+
+#define CKL()                                                                     \
+  do {                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                          \
+    if (e_ != cudaSuccess) return fail(IGM_ECUDA, "launch: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+// A bump allocator over one cudaMalloc: 256-byte aligned sub-buffers.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0, off = 0;
+  std::vector<std::pair<void **, size_t>> plan;
+  template <class T>
+  void want(T **p, size_t count) { plan.push_back({(void **)p, count * sizeof(T)}); }
+  size_t total() const {
+    size_t t = 0;
+    for (auto &q : plan) t += (q.second + 255) & ~size_t(255);
+    return t + 256;
+  }
+  cudaError_t commit() {
+    size = total();
+    cudaError_t e = cudaMalloc((void **)&base, size);
+    if (e != cudaSuccess) return e;
+    size_t o = 0;
+    for (auto &q : plan) {
+      *q.first = base + o;
+      o += (q.second + 255) & ~size_t(255);
+    }
+    plan.clear();
+    return cudaSuccess;
+  }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+  }
+};
+
+}  // namespace
+
+struct Batch;
+
+struct igm_handle_s {
+  int n = 0, nnz = 0;
+  igm_params prm{};
+  Arena arena;
+  SysDev hs{};           // host copy of the descriptor (device pointers)
+  SysDev *d_sys = nullptr;
+  SysScal *d_sc = nullptr;
+  unsigned *d_err = nullptr;
+  Batch *solo = nullptr;  // batch of one, with its captured graphs
+};
+
+struct Batch {
+  std::vector<igm_handle> hs;
+  long long nodes_check = 0, nodes_cycle = 0;
+  int m = 0, any_ilu = 0;
+  Arena arena;
+  BatchDev bd{};
+  int *h_nact = nullptr;  // pinned
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_check = nullptr, g_cycle = nullptr;
+  ~Batch() {
+    if (g_check) cudaGraphExecDestroy(g_check);
+    if (g_cycle) cudaGraphExecDestroy(g_cycle);
+    if (cap) cudaStreamDestroy(cap);
+    if (h_nact) cudaFreeHost(h_nact);
+    arena.release();
+  }
+};
+
+namespace {
+
+std::mutex g_batches_mu;
+std::atomic<long long> g_launches{0};
+std::vector<Batch *> g_batches;  // cached multi-system batches
+
+igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
+  Batch *b = new Batch();
+  b->hs = hs;
+  int ns = (int)hs.size();
+  std::vector<Tile> tiles;
+  std::vector<int> snt(ns);
+  std::vector<SysDev *> sp(ns);
+  b->m = hs[0]->prm.m;
+  for (int s = 0; s < ns; ++s) {
+    igm_handle h = hs[s];
+    if (h->prm.m != b->m) {
+      delete b;
+      return fail(IGM_EINVAL, "batched handles must share m");
+    }
+    b->any_ilu |= h->prm.precond;
+    int first = (int)tiles.size();
+    int nt = (h->n + IGM_TILE - 1) / IGM_TILE;
+    for (int t = 0; t < nt; ++t)
+      tiles.push_back(Tile{s, t * IGM_TILE, std::min(IGM_TILE, h->n - t * IGM_TILE), first});
+    snt[s] = nt;
+    sp[s] = h->d_sys;
+  }
+  int T = (int)tiles.size();
+  Tile *d_tiles;
+  int *d_snt, *d_nact;
+  SysDev **d_sp;
+  long long *d_part;
+  double *d_partd;
+  unsigned *d_ticket;
+  b->arena.want(&d_tiles, T);
+  b->arena.want(&d_snt, ns);
+  b->arena.want(&d_sp, ns);
+  b->arena.want(&d_part, 2 * (size_t)T);
+  b->arena.want(&d_partd, T);
+  b->arena.want(&d_ticket, 4);
+  b->arena.want(&d_nact, 1);
+  if (b->arena.commit() != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(IGM_EOOM, "batch arena");
+  }
+  CK(cudaMemcpy(d_tiles, tiles.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_snt, snt.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_sp, sp.data(), sizeof(SysDev *) * ns, cudaMemcpyHostToDevice));
+  CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
+  CK(cudaMemset(d_nact, 0, sizeof(int)));
+  b->bd = BatchDev{ns, T, d_sp, d_tiles, d_snt, d_part, d_partd, d_ticket, d_nact};
+  CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
+  CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  *out = b;
+  return IGM_OK;
+}
+
+// lines 1-23 of Fig. 2 after line 1's residual: (line 1') r0 = M^-1 r,
+// ||r0||, cast, m Arnoldi steps, back-substitution and update
+void enqueue_inner(Batch *b, cudaStream_t st) {
+  const BatchDev &B = b->bd;
+  if (b->any_ilu) {
+    launch_trsv_fp(B, 1, st);
+    launch_trsv_fp(B, 0, st);
+  }
+  launch_max(B, VEC_R, 2, st);
+  launch_norm(B, VEC_R, ACT_NU, 2, st);
+  launch_cast_v1(B, st);
+  for (int j = 0; j < b->m; ++j) {
+    launch_spmv(B, j, st);
+    if (b->any_ilu) {
+      launch_trsv_int(B, 1, st);
+      launch_trsv_int(B, 0, st);
+    }
+    for (int i = 0; i <= j; ++i) launch_mgs(B, i, j, st);
+    launch_mgs_last(B, j, st);
+    launch_normalize(B, j, st);
+  }
+  launch_backsub(B, st);
+  launch_update(B, st);
+}
+
+igm_status capture_graphs(Batch *b) {
+  if (b->g_check && b->g_cycle) return IGM_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  launch_resid(b->bd, 0, b->cap);
+  launch_norm(b->bd, VEC_R, ACT_RHO, 1, b->cap);
+  CK(cudaStreamEndCapture(b->cap, &g));
+  CK(cudaGraphInstantiate(&b->g_check, g, 0));
+  {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    b->nodes_check = (long long)nn;
+  }
+  cudaGraphDestroy(g);
+  CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  launch_rhs(b->bd, b->cap);
+  enqueue_inner(b, b->cap);
+  CK(cudaStreamEndCapture(b->cap, &g));
+  CK(cudaGraphInstantiate(&b->g_cycle, g, 0));
+  {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    b->nodes_cycle = (long long)nn;
+  }
+  cudaGraphDestroy(g);
+  return IGM_OK;
+}
+
+igm_status check_params(const igm_params *p) {
+  if (!p) return fail(IGM_EINVAL, "params is NULL");
+  if (p->df < 1 || p->df > 62) return fail(IGM_EINVAL, "df out of range");
+  if (p->alpha_a < 0 || p->alpha_a > 62) return fail(IGM_EINVAL, "alpha_a out of range");
+  if (p->m < 1 || p->m > IGM_MAX_M) return fail(IGM_EINVAL, "m out of range");
+  if (p->precond != 0 && p->precond != 1) return fail(IGM_EINVAL, "precond must be 0 or 1");
+  const int b[] = {p->beta7, p->beta8, p->beta10, p->beta11a, p->beta11b, p->beta13,
+                   p->beta15, p->beta16a, p->beta16b};
+  for (int v : b)
+    if (v < 0 || v > 62) return fail(IGM_EINVAL, "shift out of range");
+  if (p->max_refine < 0 || p->max_refine > 64) return fail(IGM_EINVAL, "max_refine out of range");
+  if (!(p->tol >= 0.0)) return fail(IGM_EINVAL, "tol must be >= 0");
+  if (p->inner != 0) return fail(IGM_EINVAL, "inner solver %d not available", p->inner);
+  return IGM_OK;
+}
+
+igm_status err_status(unsigned e) {
+  if (e & ERR_BADCSR) return fail(IGM_EINVAL, "malformed CSR (rowptr/col)");
+  if (e & ERR_ZERO_ROW) return fail(IGM_EZERO_ROW, "a row of A is zero (eq. 3)");
+  if (e & ERR_ZERO_PIVOT) return fail(IGM_EZERO_PIVOT, "zero or missing ILU(0) pivot");
+  if (e & ERR_CAST) return fail(IGM_EINVAL, "value out of int64 range in a cast");
+  if (e & ERR_TIMEOUT) return fail(IGM_ETIMEOUT, "a bounded device wait expired");
+  return IGM_OK;
+}
+
+void fill_report(const SysScal &sc, igm_report *rep) {
+  if (!rep) return;
+  memset(rep, 0, sizeof(*rep));
+  for (int k = 0; k < IGM_EV_COUNT; ++k) rep->ev[k] = (long long)sc.ev[k];
+  rep->refinements = sc.refinements;
+  rep->inner_steps = sc.inner_steps;
+  rep->breakdowns = sc.breakdowns;
+  rep->status = sc.status;
+  rep->relres = sc.rho;
+  rep->relres_unscaled = sc.relres_unscaled;
+  memcpy(rep->gamma_hist, sc.gamma_hist, sizeof rep->gamma_hist);
+  memcpy(rep->relres_hist, sc.relres_hist, sizeof rep->relres_hist);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *igm_last_error(void) { return g_err.c_str(); }
+const char *igm_version(void) { return "igm-gb300 0.1 (sm_103a)"; }
+
+igm_status igm_params_default(igm_params *p, int precond, int m) {
+  if (!p) return fail(IGM_EINVAL, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->df = 30;
+  p->m = m;
+  p->precond = precond;
+  p->tol = 1e-10;
+  p->max_refine = 60;
+  if (precond) {  // Table 5
+    p->alpha_a = 32;
+    p->beta7 = p->beta8 = p->beta10 = 0;
+    p->beta11a = 30;
+    p->beta11b = 0;
+    p->beta13 = p->beta15 = 0;
+    p->beta16a = 30;
+    p->beta16b = 0;
+  } else {  // Table 4
+    p->alpha_a = 16;
+    p->beta7 = p->beta8 = p->beta10 = 16;
+    p->beta11a = 16;
+    p->beta11b = 14;
+    p->beta13 = p->beta15 = 16;
+    p->beta16a = 16;
+    p->beta16b = 14;
+  }
+  return IGM_OK;
+}
+
+igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
+                           const double *val, const igm_params *params, void *stream,
+                           igm_handle *out) {
+  g_err.clear();
+  if (!out) return fail(IGM_EINVAL, "out is NULL");
+  *out = nullptr;
+  igm_status st = check_params(params);
+  if (st) return st;
+  if (n < 1 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
+    return fail(IGM_EINVAL, "bad sizes or NULL arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  igm_handle h = new igm_handle_s();
+  h->n = n;
+  h->nnz = nnz;
+  h->prm = *params;
+  const int m = params->m, ilu = params->precond;
+  SysDev &d = h->hs;
+  int *rp, *cl, *dp, *lord = nullptr, *uord = nullptr, *lfl = nullptr, *ufl = nullptr;
+  int *lev = nullptr, *cnt = nullptr, *maxlev = nullptr;
+  double *ahat, *a, *dd, *f = nullptr, *b, *bh, *xt, *r, *t, *xk, *yfp;
+  i64 *abar, *fac = nullptr, *ld = nullptr, *ud = nullptr, *w, *yv, *V, *H, *cs, *sn, *g;
+  size_t nz = nnz > 0 ? nnz : 1;
+  Arena &A = h->arena;
+  A.want(&rp, n + 1);
+  A.want(&cl, nz);
+  A.want(&dp, n);
+  A.want(&ahat, nz);
+  A.want(&a, nz);
+  A.want(&dd, n);
+  A.want(&abar, nz);
+  if (ilu) {
+    A.want(&f, nz);
+    A.want(&fac, nz);
+    A.want(&ld, n);
+    A.want(&ud, n);
+    A.want(&lord, n);
+    A.want(&uord, n);
+    A.want(&lfl, n);
+    A.want(&ufl, n);
+    A.want(&lev, n);
+    A.want(&cnt, n + 1);
+    A.want(&maxlev, 2);
+  }
+  A.want(&b, n);
+  A.want(&bh, n);
+  A.want(&xt, n);
+  A.want(&r, n);
+  A.want(&t, n);
+  A.want(&xk, n);
+  A.want(&w, n);
+  A.want(&yv, n);
+  A.want(&V, (size_t)(m + 1) * n);
+  A.want(&H, (size_t)(m + 1) * m);
+  A.want(&cs, m);
+  A.want(&sn, m);
+  A.want(&g, m + 1);
+  A.want(&yfp, m);
+  A.want(&h->d_sys, 1);
+  A.want(&h->d_sc, 1);
+  A.want(&h->d_err, 4);
+  if (A.commit() != cudaSuccess) {
+    cudaGetLastError();
+    size_t need = A.total();
+    delete h;
+    return fail(IGM_EOOM, "device allocation of %zu bytes failed", need);
+  }
+#define CKH(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      cudaGetLastError();                                                         \
+      int_gmres_destroy(h);                                                       \
+      return fail(IGM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                             \
+  } while (0)
+  CKH(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), s));
+  CKH(cudaMemsetAsync(h->d_sc, 0, sizeof(SysScal), s));
+  CKH(cudaMemcpyAsync(rp, rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault, s));
+  if (nnz > 0) {
+    CKH(cudaMemcpyAsync(cl, col, sizeof(int) * nnz, cudaMemcpyDefault, s));
+    CKH(cudaMemcpyAsync(ahat, val, sizeof(double) * nnz, cudaMemcpyDefault, s));
+  }
+  int h_rp[2];
+  CKH(cudaMemcpyAsync(h_rp, rp, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKH(cudaMemcpyAsync(h_rp + 1, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKH(cudaStreamSynchronize(s));
+  if (h_rp[0] != 0 || h_rp[1] != nnz) {
+    int_gmres_destroy(h);
+    return fail(IGM_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  }
+  unsigned *err = h->d_err;
+  launch_validate(n, nnz, rp, cl, dp, err, s);
+  launch_scale(n, rp, ahat, params->alpha_a, a, dd, err, s);
+  launch_cast(nnz, a, abar, err, s);
+  CKH(cudaGetLastError());
+  unsigned herr = 0;
+  CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CKH(cudaStreamSynchronize(s));
+  if (herr) {
+    igm_status e = err_status(herr);
+    int_gmres_destroy(h);
+    return e;
+  }
+  if (ilu) {
+    // a stored diagonal is required by ILU(0)
+    std::vector<int> hdp(n);
+    CKH(cudaMemcpy(hdp.data(), dp, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i)
+      if (hdp[i] < 0) {
+        int_gmres_destroy(h);
+        return fail(IGM_EZERO_PIVOT, "row %d has no stored diagonal (ILU(0))", i);
+      }
+    unsigned *tick = (unsigned *)(h->d_err + 1);
+    int *ords[2] = {lord, uord};
+    int *flg[2] = {lfl, ufl};
+    for (int lower = 1; lower >= 0; --lower) {
+      CKH(cudaMemsetAsync(flg[1 - lower], 0, sizeof(int) * n, s));
+      CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
+      CKH(cudaMemsetAsync(maxlev, 0, sizeof(int), s));
+      launch_levels(n, rp, cl, dp, lower, lev, flg[1 - lower], 1, tick, maxlev, err, s);
+      int L = 0;
+      CKH(cudaMemcpyAsync(&L, maxlev, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CKH(cudaStreamSynchronize(s));
+      L += 1;
+      CKH(cudaMemsetAsync(cnt, 0, sizeof(int) * (L + 1), s));
+      launch_level_order(n, L, lev, cnt, ords[1 - lower], s);
+    }
+    CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
+    launch_ilu0(n, rp, cl, dp, lord, f, lfl, 2, tick, err, s);
+    launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
+    CKH(cudaGetLastError());
+    CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CKH(cudaStreamSynchronize(s));
+    if (herr) {
+      igm_status e = err_status(herr);
+      int_gmres_destroy(h);
+      return e;
+    }
+  }
+  d.n = n;
+  d.nnz = nnz;
+  d.ld = m + 1;
+  d.p = SysParams{params->df,     params->alpha_a, m,                params->precond,
+                  params->beta7,  params->beta8,   params->beta10,   params->beta11a,
+                  params->beta11b, params->beta13, params->beta15,   params->beta16a,
+                  params->beta16b, params->inner,  params->max_refine, params->tol};
+  d.rowptr = rp;
+  d.col = cl;
+  d.diagpos = dp;
+  d.ahat = ahat;
+  d.a = a;
+  d.d = dd;
+  d.abar = abar;
+  d.f = f;
+  d.fac = fac;
+  d.ldiag = ld;
+  d.udiag = ud;
+  d.lorder = lord;
+  d.uorder = uord;
+  d.lflag = lfl;
+  d.uflag = ufl;
+  d.b = b;
+  d.bh = bh;
+  d.xt = xt;
+  d.r = r;
+  d.t = t;
+  d.xk = xk;
+  d.w = w;
+  d.yv = yv;
+  d.V = V;
+  d.H = H;
+  d.cs = cs;
+  d.sn = sn;
+  d.g = g;
+  d.yfp = yfp;
+  d.sc = h->d_sc;
+  CKH(cudaMemcpyAsync(h->d_sys, &d, sizeof(SysDev), cudaMemcpyHostToDevice, s));
+  // epochs 1 and 2 were used by the level and ILU(0) kernels
+  int seq0 = 2;
+  CKH(cudaMemcpyAsync(&h->d_sc->seq, &seq0, sizeof(int), cudaMemcpyHostToDevice, s));
+  CKH(cudaMemsetAsync(H, 0, sizeof(i64) * (size_t)(m + 1) * m, s));
+  CKH(cudaMemsetAsync(V, 0, sizeof(i64) * (size_t)(m + 1) * n, s));
+  CKH(cudaStreamSynchronize(s));
+  igm_status bs = build_batch({h}, &h->solo);
+  if (bs) {
+    int_gmres_destroy(h);
+    return bs;
+  }
+  *out = h;
+  return IGM_OK;
+#undef CKH
+}
+
+void int_gmres_destroy(igm_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> lk(g_batches_mu);
+    for (size_t k = 0; k < g_batches.size();) {
+      Batch *b = g_batches[k];
+      if (std::find(b->hs.begin(), b->hs.end(), h) != b->hs.end()) {
+        delete b;
+        g_batches.erase(g_batches.begin() + k);
+      } else {
+        ++k;
+      }
+    }
+  }
+  delete h->solo;
+  h->arena.release();
+  delete h;
+}
+
+long long int_gmres_device_bytes(igm_handle h) { return h ? (long long)h->arena.size : 0; }
+
+}  // extern "C"
+
+namespace {
+
+// Fig. 1 over a batch: b = D^-1 bh, norms, then {test, inner solve} until
+// every system has converged or reached max_refine.
+igm_status run_ir(Batch *b, cudaStream_t s) {
+  const BatchDev &B = b->bd;
+  igm_status st = capture_graphs(b);
+  if (st) return st;
+  launch_init_scal(B, 0, s);
+  launch_init_ir(B, s);
+  launch_max(B, VEC_B, 0, s);
+  launch_norm(B, VEC_B, ACT_NB, 0, s);
+  launch_max(B, VEC_BH, 0, s);
+  launch_norm(B, VEC_BH, ACT_NBH, 0, s);
+  CKL();
+  g_launches += 6;
+  int maxr = 0;
+  for (auto h : b->hs) maxr = std::max(maxr, h->prm.max_refine);
+  for (int k = 0; k <= maxr + 1; ++k) {
+    CK(cudaGraphLaunch(b->g_check, s));
+    g_launches += b->nodes_check;
+    CK(cudaMemcpyAsync(b->h_nact, B.nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*b->h_nact == 0) break;
+    CK(cudaGraphLaunch(b->g_cycle, s));
+    g_launches += b->nodes_cycle;
+  }
+  // residual of the original system for the report
+  launch_resid(B, 1, s);
+  launch_norm(B, VEC_R, ACT_UNSC, 0, s);
+  CKL();
+  g_launches += 2;
+  return IGM_OK;
+}
+
+igm_status collect(igm_handle h, igm_report *rep, cudaStream_t s) {
+  SysScal sc;
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(SysScal), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  e = sc.err;
+  fill_report(sc, rep);
+  if (e) {
+    igm_status st = err_status(e);
+    if (rep) rep->status = st;
+    return st;
+  }
+  if (sc.status == IGM_ENOCONV) return fail(IGM_ENOCONV, "max_refine reached at relres %.3e", sc.rho);
+  return IGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *rep,
+                    void *stream) {
+  g_err.clear();
+  if (!h || !bhat || !xhat) return fail(IGM_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->hs.bh, bhat, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  igm_status st = run_ir(h->solo, s);
+  if (st) return st;
+  CK(cudaMemcpyAsync(xhat, h->hs.xt, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  return collect(h, rep, s);
+}
+
+igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat,
+                            double *const *xhat, igm_report *reps, void *stream) {
+  g_err.clear();
+  if (count < 1 || !hs || !bhat || !xhat) return fail(IGM_EINVAL, "bad batch arguments");
+  std::vector<igm_handle> v(hs, hs + count);
+  for (int i = 0; i < count; ++i) {
+    if (!v[i] || !bhat[i] || !xhat[i]) return fail(IGM_EINVAL, "NULL entry %d", i);
+    for (int k = 0; k < i; ++k)
+      if (v[k] == v[i]) return fail(IGM_EINVAL, "handle %d repeated", i);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch *b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batches_mu);
+    for (Batch *c : g_batches)
+      if (c->hs == v) b = c;
+  }
+  if (!b) {
+    igm_status st = build_batch(v, &b);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_batches_mu);
+    g_batches.push_back(b);
+  }
+  for (int i = 0; i < count; ++i)
+    CK(cudaMemcpyAsync(v[i]->hs.bh, bhat[i], sizeof(double) * v[i]->n, cudaMemcpyDefault, s));
+  igm_status st = run_ir(b, s);
+  if (st) return st;
+  for (int i = 0; i < count; ++i)
+    CK(cudaMemcpyAsync(xhat[i], v[i]->hs.xt, sizeof(double) * v[i]->n, cudaMemcpyDefault, s));
+  igm_status worst = IGM_OK;
+  for (int i = 0; i < count; ++i) {
+    igm_status e = collect(v[i], reps ? reps + i : nullptr, s);
+    if (e && !worst) worst = e;
+  }
+  return worst;
+}
+
+igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_report *rep,
+                           void *stream) {
+  g_err.clear();
+  if (!h || !bk || !xk) return fail(IGM_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch *b = h->solo;
+  const BatchDev &B = b->bd;
+  CK(cudaMemcpyAsync(h->hs.t, bk, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(h->hs.xk, xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  launch_init_scal(B, 1, s);
+  launch_resid_int(B, s);
+  launch_arm(B, s);
+  enqueue_inner(b, s);
+  CKL();
+  g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) +
+                (long long)b->m * (3 + (b->any_ilu ? 2 : 0)) + (long long)b->m * (b->m + 1) / 2;
+  CK(cudaMemcpyAsync(xk, h->hs.xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  igm_status st = collect(h, rep, s);
+  if (st == IGM_ENOCONV) st = IGM_OK;  // a single inner solve has no test
+  if (rep && rep->status == IGM_ENOCONV) rep->status = IGM_OK;
+  return st;
+}
+
+igm_status int_gmres_get_state(igm_handle h, long long *V, long long *H, long long *cs,
+                               long long *sn, long long *g, int *jeff, double *nu) {
+  g_err.clear();
+  if (!h) return fail(IGM_EINVAL, "NULL handle");
+  const int n = h->n, m = h->prm.m;
+  CK(cudaDeviceSynchronize());
+  if (V) CK(cudaMemcpy(V, h->hs.V, sizeof(i64) * (size_t)(m + 1) * n, cudaMemcpyDefault));
+  if (H) CK(cudaMemcpy(H, h->hs.H, sizeof(i64) * (size_t)(m + 1) * m, cudaMemcpyDefault));
+  if (cs) CK(cudaMemcpy(cs, h->hs.cs, sizeof(i64) * m, cudaMemcpyDefault));
+  if (sn) CK(cudaMemcpy(sn, h->hs.sn, sizeof(i64) * m, cudaMemcpyDefault));
+  if (g) CK(cudaMemcpy(g, h->hs.g, sizeof(i64) * (m + 1), cudaMemcpyDefault));
+  if (jeff || nu) {
+    SysScal sc;
+    CK(cudaMemcpy(&sc, h->d_sc, sizeof(SysScal), cudaMemcpyDeviceToHost));
+    if (jeff) *jeff = sc.jeff;
+    if (nu) *nu = sc.nu;
+  }
+  return IGM_OK;
+}
+
+long long igm_kernel_launches(void) { return g_launches.load(); }
+
+igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
+  g_err.clear();
+  if (!h || !ms || reps < 1) return fail(IGM_EINVAL, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch *b = h->solo;
+  const BatchDev &B = b->bd;
+  const int m = h->prm.m, ilu = h->prm.precond;
+  // put the inner-solve gates in the running state; h_{m,m-1} := 2^30 keeps
+  // line 11's divisor non-zero
+  SysScal sc;
+  CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(SysScal), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  SysScal run = sc;
+  run.cyc = 1;
+  run.early = 0;
+  run.active = 1;
+  run.hnext = (i64)1 << 30;
+  run.normj = m - 1;
+  CK(cudaMemcpyAsync(h->d_sc, &run, sizeof(SysScal), cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int k = 0; k < IGM_K_COUNT; ++k) {
+    ms[k] = -1.0;
+    if ((k == IGM_K_TRSV_L || k == IGM_K_TRSV_U) && !ilu) continue;
+    float tot = 0.f;
+    for (int r = 0; r < reps; ++r) {
+      if (k == IGM_K_TRSV_L || k == IGM_K_TRSV_U) launch_spmv(B, m / 2, s);  // arms flags
+      if (k == IGM_K_TRSV_U) launch_trsv_int(B, 1, s);
+      CK(cudaEventRecord(e0, s));
+      switch (k) {
+        case IGM_K_SPMV: launch_spmv(B, m / 2, s); break;
+        case IGM_K_TRSV_L: launch_trsv_int(B, 1, s); break;
+        case IGM_K_TRSV_U: launch_trsv_int(B, 0, s); break;
+        case IGM_K_MGS: launch_mgs(B, m / 2, m - 1, s); break;
+        case IGM_K_MGS_LAST: launch_mgs_last(B, m - 1, s); break;
+        case IGM_K_NORMALIZE: launch_normalize(B, m - 1, s); break;
+        case IGM_K_RESID: launch_resid(B, 0, s); break;
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      tot += t;
+      if (k == IGM_K_MGS_LAST || k == IGM_K_NORMALIZE) {  // the Givens step may end the solve: re-arm
+        CK(cudaMemcpyAsync(h->d_sc, &run, sizeof(SysScal), cudaMemcpyHostToDevice, s));
+      }
+    }
+    ms[k] = tot / reps;
+  }
+  CKL();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the scalars of the last solve (seq keeps increasing)
+  SysScal now;
+  CK(cudaMemcpyAsync(&now, h->d_sc, sizeof(SysScal), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  sc.seq = now.seq;
+  CK(cudaMemcpyAsync(h->d_sc, &sc, sizeof(SysScal), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return IGM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// igm_dev.cuh -- device arithmetic of the int-GMRES kernels.
+//
+// Fixed-point words are int64 holding the exact value modulo 2^64 (the
+// wrap of the paper's int64 hardware, Sec. VII-B).  Products and sums are
+// formed exactly in __int128; an overflow event is counted wherever the
+// exact value of an operation leaves [-2^63, 2^63).  Right shifts are the
+// arithmetic shift (floor division by 2^beta, Sec. V-A), divisions truncate
+// toward zero (Sec. V-B), square roots are floor(sqrt(.)) (Sec. V-B).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "igm_internal.h"
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+namespace igm {
+
+__device__ __forceinline__ bool out64(i128 x) { return x != (i128)(i64)(u64)x; }
+__device__ __forceinline__ i64 wrap(i128 x) { return (i64)(u64)x; }
+
+// right shift by s bits (floor division by 2^s)
+__device__ __forceinline__ i64 shr(i64 x, int s) {
+  if (s <= 0) return x;
+  if (s > 63) return x < 0 ? -1 : 0;
+  return x >> s;
+}
+
+__device__ __forceinline__ i64 mulw(i64 a, i64 b, unsigned &ev) {
+  i128 p = (i128)a * (i128)b;
+  ev += out64(p);
+  return wrap(p);
+}
+
+__device__ __forceinline__ i64 negw(i64 a, unsigned &ev) {
+  ev += (a == INT64_MIN);
+  return (i64)(0ull - (u64)a);
+}
+
+// x * 2^e for e >= 0 (counted if out of range), floor(x / 2^-e) for e < 0
+__device__ __forceinline__ i64 scale2(i64 x, int e, unsigned &ev) {
+  if (e < 0) return shr(x, -e);
+  if (e == 0) return x;
+  if (e >= 64) {
+    ev += (x != 0);
+    return 0;
+  }
+  i128 p = (i128)x * (i128)((u64)1 << (e > 62 ? 62 : e));
+  if (e > 62) p = p * 2;
+  ev += out64(p);
+  return wrap(p);
+}
+
+__device__ __forceinline__ i64 divt(i64 a, i64 b, unsigned &ev) {
+  if (b == -1 && a == INT64_MIN) {
+    ev += 1;
+    return INT64_MIN;
+  }
+  return a / b;
+}
+
+// floor(sqrt(s)) for s >= 0 (0 for s <= 0): FP64 estimate, then exact
+// integer correction.
+__device__ __forceinline__ i64 isqrt64(i64 s) {
+  if (s <= 0) return 0;
+  u64 us = (u64)s;
+  u64 r = (u64)__dsqrt_rn((double)us);
+  while (r * r > us) --r;
+  while ((r + 1) * (r + 1) <= us) ++r;
+  return (i64)r;
+}
+
+// Sec. V-B square root of a word with dfp fractional bits -> Q(df)
+__device__ __forceinline__ i64 fx_sqrt(i64 t, int dfp, int df, unsigned &ev) {
+  return scale2(isqrt64(t), df - dfp / 2, ev);
+}
+
+// Sec. V-B division ((t1 2^b1) / (t2 >> b2)) 2^(df-b1-b2); caller checks
+// that t2 >> b2 != 0.
+__device__ __forceinline__ i64 fx_div(i64 t1, i64 t2, int b1, int b2, int df,
+                                      unsigned &ev) {
+  i64 d = shr(t2, b2);
+  return scale2(divt(scale2(t1, b1, ev), d, ev), df - b1 - b2, ev);
+}
+
+// ---- reproducible FP64 2-norm pieces ------------------------------------
+// trunc(x * 2^96) as an integer, |x| < 4
+__device__ __forceinline__ i128 trunc_scaled96(double x) {
+  u64 bits = (u64)__double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0) return 0;  // zero or subnormal: |x 2^96| < 1
+  u64 man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  int sh = ex - 1075 + 96;  // x 2^96 = man 2^sh
+  u128 v;
+  if (sh >= 0) v = (u128)man << sh;
+  else if (sh <= -64) v = 0;
+  else v = (u128)(man >> (-sh));
+  i128 r = (i128)v;
+  return (bits >> 63) ? -r : r;
+}
+
+// round a non-negative 128-bit integer to the nearest double (ties even)
+__device__ __forceinline__ double u128_to_double_rn(u128 u) {
+  if (u == 0) return 0.0;
+  u64 hi = (u64)(u >> 64), lo = (u64)u;
+  int len = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  if (len <= 53) return (double)lo;
+  int drop = len - 53;
+  u128 m = u >> drop;
+  u128 rem = u - (m << drop);
+  u128 half = (u128)1 << (drop - 1);
+  if (rem > half || (rem == half && (m & 1))) {
+    m += 1;
+    if (m >> 53) {
+      m >>= 1;
+      drop += 1;
+    }
+  }
+  return scalbn((double)(u64)m, drop);
+}
+
+// exact square of r 2^-e, truncated on the 2^-96 grid
+__device__ __forceinline__ i128 sq_term(double r, int e) {
+  double t = scalbn(r, -e);
+  double p = __dmul_rn(t, t);
+  double q = __fma_rn(t, t, -p);
+  return trunc_scaled96(p) + trunc_scaled96(q);
+}
+
+__device__ __forceinline__ double norm_from_acc(i128 acc, int e) {
+  double s = u128_to_double_rn((u128)(acc < 0 ? 0 : acc));
+  return scalbn(__dsqrt_rn(scalbn(s, -96)), e);
+}
+
+// ---- reductions ------------------------------------------------------------
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int o) {
+  u128 u = (u128)v;
+  u64 lo = __shfl_down_sync(0xffffffffu, (u64)u, o);
+  u64 hi = __shfl_down_sync(0xffffffffu, (u64)(u >> 64), o);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
+__device__ __forceinline__ i128 warp_sum_i128(i128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_down_i128(v, o);
+  return v;
+}
+
+// block-wide int128 sum; result valid in thread 0
+__device__ __forceinline__ i128 block_sum_i128(i128 v) {
+  __shared__ u64 s_lo[32], s_hi[32];
+  v = warp_sum_i128(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_lo[wid] = (u64)(u128)v;
+    s_hi[wid] = (u64)((u128)v >> 64);
+  }
+  __syncthreads();
+  i128 r = 0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    if (lane < nw) r = (i128)(((u128)s_hi[lane] << 64) | (u128)s_lo[lane]);
+    r = warp_sum_i128(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double s[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? s[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double s[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? s[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = __dadd_rn(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  __syncthreads();
+  return r;
+}
+
+// add a per-thread event count to a per-system counter
+__device__ __forceinline__ void flush_ev(unsigned ev, u64 *ctr) {
+  unsigned s = __reduce_add_sync(0xffffffffu, ev);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (u64)s);
+}
+
+// ---- flags with acquire/release, bounded waits ----------------------------
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+#define IGM_SPIN_MAX (1 << 22)
+
+// wait until *flag >= epoch; false (and an error bit) if the bound expires.
+// Once any wait of the same system has expired, every other wait gives up
+// at its next check, so a failure costs one bound, not one per row.
+__device__ __forceinline__ bool wait_flag(const int *flag, int epoch, unsigned *err) {
+  if (ld_acquire(flag) >= epoch) return true;
+  for (int it = 0; it < IGM_SPIN_MAX; ++it) {
+    __nanosleep(32);
+    if (ld_acquire(flag) >= epoch) return true;
+    if ((it & 255) == 255 && (*(volatile unsigned *)err & ERR_TIMEOUT)) return false;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+// Last-CTA detection for a per-system reduction over its tiles.  Call from
+// all threads after the tile partial is written; returns true in every
+// thread of the CTA that arrives last (counter reset for reuse).
+__device__ __forceinline__ bool last_tile(unsigned *cnt, int ntiles) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(cnt, 1u);
+    s_last = (prev == (unsigned)(ntiles - 1));
+    if (s_last) *cnt = 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+__device__ __forceinline__ i128 load_part(const long long *part, int t) {
+  u64 lo = (u64)__ldcg(part + 2 * t), hi = (u64)__ldcg(part + 2 * t + 1);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+__device__ __forceinline__ void store_part(long long *part, int t, i128 v) {
+  part[2 * t] = (long long)(u64)(u128)v;
+  part[2 * t + 1] = (long long)(u64)((u128)v >> 64);
+}
+
+}  // namespace igm

@@ -1,0 +1,99 @@
+// igm_internal.h -- device-side data layout shared by the kernels and the
+// host driver of the int-GMRES library (not part of the public ABI).
+//
+// Layout in HBM, per system (one igm_handle):
+//   CSR pattern   rowptr int32[n+1], col int32[nnz], diagpos int32[n]
+//   ahat f64[nnz] (input values, kept for the unscaled residual),
+//   a f64[nnz] (eq. 1), d f64[n] (eq. 3), abar int64[nnz] (Sec. IV-B)
+//   ILU: f f64[nnz] (eq. ilu), fac int64[nnz] + ldiag/udiag int64[n]
+//        (eq. dldr..ilu2), level orders lorder/uorder int32[n],
+//        ready flags lflag/uflag int32[n]
+//   vectors: b, bh, xt, r, t, xk f64[n]; w, yv int64[n];
+//            V int64[(m+1) n] (row-major by basis vector)
+//   scalars: H int64[(m+1) m] column-major, cs, sn int64[m], g int64[m+1],
+//            yfp f64[m], SysScal (counters, histories, status)
+// A batch is a list of systems plus a tile table: tile t covers rows
+// [row0, row0+nrows) of one system (never straddling two), IGM_TILE rows
+// per tile; every kernel runs one CTA per tile.
+#pragma once
+#include <cstdint>
+
+#define IGM_TILE 1024
+#define IGM_BLOCK 256
+#define IGM_NEV 16
+
+typedef long long i64;
+typedef unsigned long long u64;
+
+namespace igm {
+
+struct SysParams {
+  int df, alpha_a, m, precond;
+  int b7, b8, b10, b11a, b11b, b13, b15, b16a, b16b;
+  int inner, max_refine;
+  double tol;
+};
+
+// error bits of SysScal::err
+enum : unsigned {
+  ERR_TIMEOUT = 1u, ERR_ZERO_ROW = 2u, ERR_ZERO_PIVOT = 4u, ERR_BADCSR = 8u,
+  ERR_CAST = 16u
+};
+
+// per-system mutable scalars, in device memory
+struct SysScal {
+  u64 ev[IGM_NEV];
+  int status, active, cyc, jeff, early, refinements, inner_steps, breakdowns;
+  int seq;                 // epoch of the ready flags
+  unsigned err;
+  unsigned cnt[2];         // last-CTA counters of tile reductions
+  int mode;                // 0 refinement loop, 1 single inner solve
+  int normj;               // step whose line 11 runs (-1: none)
+  double nb, nbh, rho, gamma, nu, maxabs, relres_unscaled, pad2;
+  i64 hnext;               // h_{j+1,j} before the rotations (line 11)
+  double relres_hist[65];
+  double gamma_hist[64];
+};
+
+struct SysDev {
+  int n, nnz, ld;          // ld = m + 1
+  int pad;
+  SysParams p;
+  const int *rowptr, *col, *diagpos;
+  const double *ahat, *a, *d;
+  const i64 *abar;
+  const double *f;                       // FP64 ILU(0) factors
+  const i64 *fac, *ldiag, *udiag;        // integer factors
+  const int *lorder, *uorder;
+  int *lflag, *uflag;
+  double *b, *bh, *xt, *r, *t, *xk;
+  i64 *w, *yv, *V;
+  i64 *H, *cs, *sn, *g;
+  double *yfp;
+  SysScal *sc;
+};
+
+struct Tile {
+  int sys;     // batch-local system index
+  int row0;    // first row (or first position of a level order)
+  int nrows;
+  int first;   // index of the system's first tile
+};
+
+struct BatchDev {
+  int nsys, ntiles;
+  SysDev *const *sys;      // device pointers to each system's SysDev
+  const Tile *tiles;
+  const int *sys_ntiles;   // tiles per system
+  long long *part;         // 2 x ntiles int64 (int128 partials, lo/hi)
+  double *partd;           // ntiles
+  unsigned *ticket;        // 4 dynamic-ticket counters
+  int *nact;               // systems still refining
+};
+
+// vector selectors for the generic max / norm kernels
+enum Vec : int { VEC_B = 0, VEC_R = 1, VEC_BH = 2 };
+// what the last CTA does with a finished norm
+enum NormAct : int { ACT_NB = 0, ACT_RHO = 1, ACT_NU = 2, ACT_NBH = 3, ACT_UNSC = 4 };
+
+}  // namespace igm

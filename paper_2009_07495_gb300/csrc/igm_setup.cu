@@ -1,0 +1,236 @@
+// igm_setup.cu -- device set-up of one system (the steps of Fig. 1 before
+// the refinement loop): CSR validation, the initial row scaling of eq. (1)
+// and eq. (3), the cast of Sec. IV-B, the level schedule of the triangular
+// factors, the FP64 ILU(0) of eq. (ilu) and the integer factors of
+// eq. (dldr)-(ilu2).
+#include "igm_dev.cuh"
+#include "igm_launch.h"
+
+namespace igm {
+
+// CSR checks (rowptr monotone, columns in range and strictly ascending) and
+// the position of each row's diagonal (-1 if absent)
+__global__ void s_validate(int n, int nnz, const int *rowptr, const int *col, int *diagpos,
+                           unsigned *err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int k0 = rowptr[i], k1 = rowptr[i + 1], dp = -1;
+    if (k0 < 0 || k1 < k0 || k1 > nnz) {
+      atomicOr(err, ERR_BADCSR);
+      diagpos[i] = -1;
+      continue;
+    }
+    int prev = -1;
+    for (int k = k0; k < k1; ++k) {
+      int c = col[k];
+      if (c < 0 || c >= n || c <= prev) atomicOr(err, ERR_BADCSR);
+      if (c == i) dp = k;
+      prev = c;
+    }
+    diagpos[i] = dp;
+  }
+}
+
+// eq. (3): d_i = max_j |ahat_ij| 2^-alpha_a; eq. (1): a_ij = ahat_ij / d_i
+__global__ void s_scale(int n, const int *rowptr, const double *ahat, int alpha,
+                        double *a, double *d, unsigned *err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) mx = fmax(mx, fabs(ahat[k]));
+    if (mx == 0.0) {
+      atomicOr(err, ERR_ZERO_ROW);
+      d[i] = 1.0;
+      continue;
+    }
+    double di = scalbn(mx, -alpha);
+    d[i] = di;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) a[k] = __ddiv_rn(ahat[k], di);
+  }
+}
+
+// Sec. IV-B: Abar_0 = cast(A), truncation toward zero
+__global__ void s_cast(long long nnz, const double *a, i64 *abar, unsigned *err) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x) {
+    double v = a[k];
+    if (fabs(v) < 9223372036854775808.0) abar[k] = __double2ll_rz(v);
+    else {
+      abar[k] = 0;
+      atomicOr(err, ERR_CAST);
+    }
+  }
+}
+
+// Level of every row of the strict lower (lower = 1) or strict upper part:
+// level(i) = 1 + max level of the rows row i reads (0 if none).  Rows are
+// visited in dependency order (natural order for L, reverse for U); CTAs
+// take 256-row chunks by ticket, each row waits (bounded) on the flags of
+// its dependencies.
+__global__ void s_levels(int n, const int *rowptr, const int *col, const int *diagpos,
+                         int lower, int *level, int *flag, int epoch, unsigned *ticket,
+                         int *maxlev, unsigned *err) {
+  __shared__ int s_t;
+  if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  int p = s_t * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = lower ? p : n - 1 - p;
+  int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+  int k1 = lower ? diagpos[i] : rowptr[i + 1];
+  int lv = 0;
+  for (int k = k0; k < k1; ++k) {
+    int j = col[k];
+    wait_flag(flag + j, epoch, err);
+    lv = max(lv, __ldcg(level + j) + 1);
+  }
+  level[i] = lv;
+  st_release(flag + i, epoch);
+  atomicMax(maxlev, lv);
+}
+
+__global__ void s_hist(int n, const int *level, int *cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(cnt + level[i], 1);
+}
+
+// exclusive scan of cnt[0..L) in place, one CTA (L up to a few million)
+__global__ void s_scan(int L, int *cnt) {
+  __shared__ int s[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < L; base += 1024) {
+    int idx = base + threadIdx.x;
+    int v = idx < L ? cnt[idx] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (idx < L) cnt[idx] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+}
+
+// scatter rows into level order (order inside a level is arbitrary and
+// does not affect results: rows of one level are independent)
+__global__ void s_scatter(int n, const int *level, int *cursor, int *order) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    order[atomicAdd(cursor + level[i], 1)] = i;
+}
+
+// eq. (ilu): ILU(0), IKJ row variant on the pattern of A (Saad, Alg. 10.4):
+// for row i, k ascending over its strict lower part: l_ik = a_ik / u_kk,
+// then a_ij -= l_ik u_kj for the j > k of row i present in row k.  Rows in
+// level order, synchronisation-free as in the substitutions.
+__global__ void s_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
+                       const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
+                       unsigned *err) {
+  __shared__ int s_t;
+  if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  int p = s_t * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = lorder[p];
+  int end = rowptr[i + 1];
+  for (int kk = rowptr[i]; kk < diagpos[i]; ++kk) {
+    int k = col[kk];
+    wait_flag(flag + k, epoch, err);
+    double ukk = __ldcg(f + diagpos[k]);
+    if (ukk == 0.0) {
+      atomicOr(err, ERR_ZERO_PIVOT);
+      break;
+    }
+    double lik = __ddiv_rn(f[kk], ukk);
+    f[kk] = lik;
+    int q = diagpos[k] + 1, qe = rowptr[k + 1];
+    for (int jj = kk + 1; jj < end; ++jj) {
+      int jc = col[jj];
+      while (q < qe && col[q] < jc) ++q;
+      if (q < qe && col[q] == jc) f[jj] = __dsub_rn(f[jj], __dmul_rn(lik, __ldcg(f + q)));
+    }
+  }
+  if (f[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
+  st_release(flag + i, epoch);
+}
+
+// eq. (dl), (dl2), (l1), (u1), (ilu2): D_l = |d|^1/2, D_u = sgn(d)|d|^1/2,
+// Lbar = trunc(L D_l), Ubar = trunc(D_u U') with U' = D^-1 U
+__global__ void s_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
+                          const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double di = f[diagpos[i]];
+    double sl = __dsqrt_rn(fabs(di));
+    double su = di < 0 ? -sl : sl;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int j = col[k];
+      double v;
+      if (j < i) v = __dmul_rn(f[k], __dsqrt_rn(fabs(f[diagpos[j]])));
+      else if (j > i) v = __dmul_rn(su, __ddiv_rn(f[k], di));
+      else {
+        fac[k] = 0;
+        continue;
+      }
+      if (fabs(v) < 9223372036854775808.0) fac[k] = __double2ll_rz(v);
+      else {
+        fac[k] = 0;
+        atomicOr(err, ERR_CAST);
+      }
+    }
+    if (!(sl < 9223372036854775808.0)) atomicOr(err, ERR_CAST);
+    i64 l = sl < 9223372036854775808.0 ? __double2ll_rz(sl) : 0;
+    i64 u = sl < 9223372036854775808.0 ? __double2ll_rz(su) : 0;
+    ldiag[i] = l;
+    udiag[i] = u;
+    if (l == 0 || u == 0) atomicOr(err, ERR_ZERO_PIVOT);
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int grid_for(long long n, int bs) {
+  long long g = (n + bs - 1) / bs;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+void launch_validate(int n, int nnz, const int *rowptr, const int *col, int *diagpos,
+                     unsigned *err, cudaStream_t st) {
+  s_validate<<<grid_for(n, 256), 256, 0, st>>>(n, nnz, rowptr, col, diagpos, err);
+}
+void launch_scale(int n, const int *rowptr, const double *ahat, int alpha, double *a,
+                  double *d, unsigned *err, cudaStream_t st) {
+  s_scale<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, ahat, alpha, a, d, err);
+}
+void launch_cast(long long nnz, const double *a, i64 *abar, unsigned *err, cudaStream_t st) {
+  s_cast<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, a, abar, err);
+}
+void launch_levels(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                   int *level, int *flag, int epoch, unsigned *ticket, int *maxlev,
+                   unsigned *err, cudaStream_t st) {
+  s_levels<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, diagpos, lower, level, flag,
+                                             epoch, ticket, maxlev, err);
+}
+void launch_level_order(int n, int L, const int *level, int *cnt, int *order,
+                        cudaStream_t st) {
+  s_hist<<<grid_for(n, 256), 256, 0, st>>>(n, level, cnt);
+  s_scan<<<1, 1024, 0, st>>>(L, cnt);
+  s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, level, cnt, order);
+}
+void launch_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
+                 const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
+                 unsigned *err, cudaStream_t st) {
+  s_ilu0<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, diagpos, lorder, f, flag, epoch,
+                                           ticket, err);
+}
+void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
+                    const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,
+                    cudaStream_t st) {
+  s_ilu_int<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, diagpos, f, fac, ldiag, udiag,
+                                               err);
+}
+
+}  // namespace igm

@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle
+on the same seeded inputs.  The integer inner loop (basis V, Hessenberg H,
+Givens c, s, g, overflow counts) must be bit-exact; the FP64 steps are
+computed in the same order with correctly rounded operations, so they are
+compared bit-for-bit too (which is stricter than the 1e-12 relative bound
+that the method's FP64 steps need)."""
+import numpy as np
+import pytest
+
+from paper_2009_07495_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_07495_gb300 import _lib
+    from paper_2009_07495_gb300 import build
+    build.build()
+    return _lib
+
+
+def _oparams(orc, P):
+    return orc.Params(df=P.df, alpha_a=P.alpha_a, m=P.m, precond=P.precond, beta7=P.beta7,
+                      beta8=P.beta8, beta10=P.beta10, beta11a=P.beta11a, beta11b=P.beta11b,
+                      beta13=P.beta13, beta15=P.beta15, beta16a=P.beta16a, beta16b=P.beta16b,
+                      tol=P.tol, max_refine=P.max_refine)
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _compare_inner(g, o, n, m):
+    """bit-exact comparison of one inner solve's integer state"""
+    j = o["jeff"]
+    assert g["jeff"] == j
+    assert g["nu"] == o["nu"]
+    np.testing.assert_array_equal(g["g"][: j + 1], o["g"][: j + 1])
+    np.testing.assert_array_equal(g["cs"][:j], o["cs"][:j])
+    np.testing.assert_array_equal(g["sn"][:j], o["sn"][:j])
+    for c in range(j):
+        np.testing.assert_array_equal(g["H"][: c + 2, c], o["H"][: c + 2, c])
+    nv = j + 1 if not o["early"] else j
+    np.testing.assert_array_equal(g["V"][:nv], o["V"][:nv])
+
+
+INNER_CASES = [
+    ("cfg0_none", lambda: W.config0(), 0, 30),
+    ("cd3d_13_ilu_ragged", lambda: W.small_cd3d(13, seed=41), 1, 20),
+    ("cd2d_40_none", lambda: W.small_cd2d(40, seed=42), 0, 25),
+    ("cd3d_10_27pt_ilu", lambda: W.small_cd3d(10, seed=43, points=27), 1, 15),
+]
+
+
+@pytest.mark.parametrize("name,sf,prec,m", INNER_CASES, ids=[c[0] for c in INNER_CASES])
+def test_inner_solve_bit_exact(L, orc, name, sf, prec, m):
+    """One int-GMRES(m) solve (Fig. 2, lines 1'/5' with ILU): V, H, c, s, g,
+    x and the overflow counts equal the oracle's bit for bit."""
+    s = sf()
+    P = L.params_default(prec, m)
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    bk = d["b"] / np.abs(d["b"]).max()
+    rng = np.random.default_rng(5)
+    x0 = rng.standard_normal(s.n) * 1e-3
+    o = orc.int_gmres(_oparams(orc, P), d, bk, x0)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    st = solver.state()
+    _compare_inner(st, o, s.n, m)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    solver.close()
+
+
+IR_CASES = [
+    ("cfg0", lambda: W.config0(), 0, 30),
+    ("cd3d_16_ilu", lambda: W.small_cd3d(16, seed=44), 1, 30),
+    ("cd3d_11_ilu_ragged", lambda: W.small_cd3d(11, seed=45), 1, 12),
+    ("banded_3000", lambda: W.banded_random(3000, np.random.default_rng(46)), 0, 30),
+    ("cd2d_33_none_host", lambda: W.small_cd2d(33, seed=47), 0, 20),
+]
+
+
+@pytest.mark.parametrize("name,sf,prec,m", IR_CASES, ids=[c[0] for c in IR_CASES])
+def test_ir_solve_bit_exact(L, orc, name, sf, prec, m):
+    """Fig. 1 to 1e-10: same refinement count, gamma and residual histories,
+    overflow counts and solution, bit for bit."""
+    s = sf()
+    P = L.params_default(prec, m)
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    if name.endswith("host"):
+        solver = L.Solver(s.rowptr, s.col, s.val, P)   # host (numpy) buffers
+        x, rep = solver.ir_solve(s.b)
+        xg = x
+    else:
+        solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+        x, rep = solver.ir_solve(_dev(s.b))
+        xg = x.cpu().numpy()
+    assert ro.status == "ok" and ro.relres < 1e-10
+    assert rep["status"] == "ok" and rep["relres"] < 1e-10
+    assert rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["gamma_hist"], ro.gamma_hist)
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    assert rep["relres_unscaled"] == ro.relres_unscaled
+    np.testing.assert_array_equal(xg, xo)
+    solver.close()
+
+
+def test_one_by_one(L):
+    """n = 1: Ahat = [2], bhat = [4] gives x = 2 exactly in one refinement."""
+    P = L.params_default(0, 5)
+    solver = L.Solver(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.0]), P)
+    x, rep = solver.ir_solve(np.array([4.0]))
+    assert x[0] == 2.0 and rep["refinements"] == 1 and rep["status"] == "ok"
+
+
+def test_overflow_events_match(L, orc):
+    """Without shifts and alpha_a = 40 the inner products overflow; the event
+    counts per line and the wrapped results still match the oracle."""
+    s = W.small_cd2d(6, seed=25)
+    P = L.params_default(1, 5)
+    P.precond = 0
+    P.alpha_a = 40
+    P.max_refine = 2
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(s.rowptr, s.col, s.val, P)
+    x, rep = solver.ir_solve(s.b)
+    assert ro.ev[2] > 0 or ro.ev[4] > 0
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    assert rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(x, xo)
+
+
+def test_errors_are_statuses(L):
+    """Malformed input returns a status (never a fault)."""
+    s = W.small_cd2d(5)
+    val = s.val.copy()
+    val[s.rowptr[2]:s.rowptr[3]] = 0.0
+    with pytest.raises(L.IGMError) as e:
+        L.Solver(s.rowptr, s.col, val, L.params_default(0, 5))
+    assert e.value.name == "ezero_row"
+    # a row without its diagonal cannot be ILU(0)-factorised
+    rp = np.array([0, 1, 2], np.int32)
+    with pytest.raises(L.IGMError) as e:
+        L.Solver(rp, np.array([1, 0], np.int32), np.array([1.0, 1.0]), L.params_default(1, 5))
+    assert e.value.name == "ezero_pivot"
+    # unsorted columns
+    with pytest.raises(L.IGMError) as e:
+        L.Solver(np.array([0, 2, 3], np.int32), np.array([1, 0, 1], np.int32),
+                 np.array([1.0, 2.0, 3.0]), L.params_default(0, 5))
+    assert e.value.name == "einval"
+    # bad parameters
+    with pytest.raises(L.IGMError) as e:
+        L.Solver(s.rowptr, s.col, s.val, L.params_default(0, 0))
+    assert e.value.name == "einval"
+
+
+def test_batched_equals_solo(L, orc):
+    """ir_solve_batched: uneven systems (ragged tiles, one with ILU) solved in
+    one launch sequence give exactly their solo results."""
+    rng = np.random.default_rng(50)
+    systems = [W.banded_random(int(n), rng) for n in (1000, 2500, 4097, 1500)]
+    systems.append(W.small_cd3d(12, seed=51))
+    params = [L.params_default(0, 30)] * 4 + [L.params_default(1, 30)]
+    solos, xs = [], []
+    for s, P in zip(systems, params):
+        sv = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+        x, rep = sv.ir_solve(_dev(s.b))
+        solos.append((x.cpu().numpy(), rep))
+        xs.append(sv)
+    bh = [_dev(s.b) for s in systems]
+    import torch
+    out = [torch.empty(s.n, dtype=torch.float64, device="cuda") for s in systems]
+    reps = L.ir_solve_batched(xs, bh, out)
+    for k, s in enumerate(systems):
+        xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, params[k]))
+        np.testing.assert_array_equal(out[k].cpu().numpy(), solos[k][0])
+        np.testing.assert_array_equal(out[k].cpu().numpy(), xo)
+        assert reps[k]["refinements"] == solos[k][1]["refinements"] == ro.refinements
+        np.testing.assert_array_equal(reps[k]["relres_hist"], ro.relres_hist)
+    for sv in xs:
+        sv.close()
