@@ -39,10 +39,9 @@ import numpy as np  # noqa: E402
 from paper_2009_07495_gb300 import workloads as W  # noqa: E402
 
 METRIC = "refined solves/s @1e-10 resid (int vs FP64 GMRES, 1 GB300); SpMV GB/s; p99 ms"
-KNAMES = ["spmv", "trsv_l", "trsv_u", "mgs", "mgs_last", "normalize", "resid"]
+KNAMES = ["spmv", "trsv_l", "trsv_u", "arnoldi", "resid"]
 KERNEL_SYMBOL = {"spmv": "k_spmv", "trsv_l": "k_trsv_int", "trsv_u": "k_trsv_int",
-                 "mgs": "k_mgs", "mgs_last": "k_mgs_last", "normalize": "k_normalize",
-                 "resid": "k_resid"}
+                 "arnoldi": "k_mgs_step", "resid": "k_resid"}
 
 WORKLOADS = {
     "cfg1": dict(desc="3D convection-diffusion 7-pt 128^3 (n=2,097,152, nnz=14,581,760), "
@@ -51,6 +50,12 @@ WORKLOADS = {
     "cfg0": dict(desc="2D convection-diffusion 5-pt 32x32 (n=1024), int-GMRES(30), no "
                       "preconditioning, FP64 refinement to 1e-10",
                  gen=lambda: W.config0(), precond=0, m=30),
+    "cfg2": dict(desc="batch of 512 banded random systems, n log-uniform [1k, 64k], 5-27 "
+                      "nnz/row within +-64, int-GMRES(30) no preconditioning, refinement "
+                      "to 1e-10, one batched launch sequence", precond=0, m=30),
+    "cfg3": dict(desc="serving stream: Poisson arrivals 2k req/s, 2D 5-pt / 3D 7-pt / 3D "
+                      "27-pt convection-diffusion, sides U[16,160], Peclet log-U[0.1,100], "
+                      "tol 1e-8 or 1e-10, 150 GB budget, continuous batching", m=30),
 }
 
 
@@ -64,6 +69,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batch", type=int, default=512, help="cfg2: systems in the batch")
+    ap.add_argument("--requests", type=int, default=400, help="cfg3: requests served")
     return ap.parse_args()
 
 
@@ -127,15 +134,17 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int) -> float:
+def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
+                      m: int) -> float:
     """Bytes the method must move per launch (the per-unit figures of the
-    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 4n; one MGS pass 4n (the
-    basis vector, w kept on chip); line 11 4n; one triangular solve
-    (nnz_tri + n) 12 + 16 n; FP64 residual nnz 12 + 4(n+1) + 24 n."""
+    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 4n; Arnoldi step j = m-1:
+    one basis vector per MGS pass (4n each, w kept on chip) for m passes plus
+    the line-11 write (4n); one triangular solve (nnz_tri + n) 12 + 16 n;
+    FP64 residual nnz 12 + 4(n+1) + 24 n."""
     if kind == "spmv":
         return nnz * (val_bytes + 4) + 4 * (n + 1) + 4 * n
-    if kind in ("mgs", "mgs_last", "normalize"):
-        return 4.0 * n
+    if kind == "arnoldi":
+        return 4.0 * n * (m + 1)
     if kind in ("trsv_l", "trsv_u"):
         return (nnz_l + n) * 12 + 16 * n
     if kind == "resid":
@@ -143,9 +152,12 @@ def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int) -
     raise KeyError(kind)
 
 
-def launches_per_cycle(kind: str, m: int) -> int:
-    return {"spmv": m, "trsv_l": m, "trsv_u": m, "mgs": m * (m + 1) // 2, "mgs_last": m,
-            "normalize": m, "resid": 1}[kind]
+def launches_per_cycle(kind: str, m: int) -> float:
+    """Launches per inner solve; the Arnoldi kernel is timed at its longest
+    step (m+1 passes), so its count is scaled to the average step of
+    (j+2) passes, j = 0..m-1."""
+    return {"spmv": m, "trsv_l": m, "trsv_u": m, "arnoldi": m * (m + 3) / 2 / (m + 1),
+            "resid": 1}[kind]
 
 
 def traffic_for(kernel: str, workload: str):
@@ -296,8 +308,8 @@ def run_ours(args, wl):
 
     # per-kernel device time (same kernels, same launch configuration)
     import ctypes as C
-    buf = (C.c_double * 7)()
-    st = L.load().igm_time_kernels(solver.handle, 5, buf, stream.cuda_stream)
+    buf = (C.c_double * 5)()
+    st = L.load().igm_time_kernels(solver.handle, 3, buf, stream.cuda_stream)
     if st != 0:
         raise RuntimeError(L.load().igm_last_error().decode())
     kms = np.array(buf[:])
@@ -310,7 +322,8 @@ def run_ours(args, wl):
         per_cycle = launches_per_cycle(name, wl["m"])
         kern[name] = dict(ms=kms[k], launches_per_solve=per_cycle * refinements,
                           ms_per_solve=kms[k] * per_cycle * refinements,
-                          gbs=algorithmic_bytes(name, n, nnz, nnz_l, val_bytes) / (kms[k] * 1e6))
+                          gbs=algorithmic_bytes(name, n, nnz, nnz_l, val_bytes, wl["m"])
+                          / (kms[k] * 1e6))
     tot_k = sum(v["ms_per_solve"] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
     peak, peak_src = peak_hbm()
@@ -323,6 +336,27 @@ def run_ours(args, wl):
     kernels = {k: {"ms_per_launch": round(v["ms"], 5), "algorithmic_GBs": round(v["gbs"], 1),
                    "frac_of_peak": round(v["gbs"] / peak, 4),
                    "share": round(v["ms_per_solve"] / tot_k, 4)} for k, v in kern.items()}
+
+    # the FP64 GMRES(m) comparison solver ("Double" of Sec. VII) on the same
+    # GPU, workload and refinement loop
+    fp64 = None
+    if not args.no_fp64:
+        Pf = P.replace(inner=1)
+        sf = L.Solver(rp, cl, vl, Pf, stream=stream)
+        _, rf = sf.ir_solve(bh, xh, stream=stream)
+        kf = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(kf):
+            _, rf = sf.ir_solve(bh, xh, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / kf
+        fp64 = {"value": world * 1000.0 / ms, "unit": "solves/s", "ms_per_solve": ms,
+                "refinements": rf["refinements"], "relres": rf["relres"], "steps": kf,
+                "status": rf["status"]}
+        sf.close()
 
     # end to end through the C ABI with host buffers: set-up from pinned host
     # CSR + solve from a pinned host right-hand side + solution back to host
@@ -366,12 +400,116 @@ def run_ours(args, wl):
             "p99_ms": float(np.percentile(step_ms, 99)),
             "spmv_GBs": kern["spmv"]["gbs"],
             "roofline": roofline, "kernels": kernels,
-            "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+            "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
+            "fp64_gmres": fp64}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(sysw, wl["precond"], wl["m"], refinements)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_batched(args, wl):
+    """cfg2: ir_solve_batched over all systems vs one ir_solve per system
+    (same kernels, one system per launch sequence) vs the FP64 solver."""
+    import torch
+    from paper_2009_07495_gb300 import _lib as L
+    dev = torch.device("cuda", 0)
+    systems = W.config2(count=args.batch)
+    P = L.params_default(0, wl["m"])
+    solvers, bs, xs = [], [], []
+    for sy in systems:
+        solvers.append(L.Solver(torch.from_numpy(sy.rowptr).to(dev), torch.from_numpy(sy.col).to(dev),
+                                torch.from_numpy(sy.val).to(dev), P))
+        bs.append(torch.from_numpy(sy.b).to(dev))
+        xs.append(torch.empty(sy.n, dtype=torch.float64, device=dev))
+    reps = L.ir_solve_batched(solvers, bs, xs)          # warm-up (graph capture)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        reps = L.ir_solve_batched(solvers, bs, xs)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    assert all(r["status"] == "ok" and r["relres"] < 1e-10 for r in reps)
+    # one solve per launch sequence
+    for k in range(len(solvers)):
+        solvers[k].ir_solve(bs[k], xs[k])
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for k in range(len(solvers)):
+        t1 = time.perf_counter()
+        solvers[k].ir_solve(bs[k], xs[k])
+        lat.append(time.perf_counter() - t1)
+    torch.cuda.synchronize()
+    dt_one = time.perf_counter() - t0
+    for sv in solvers:
+        sv.close()
+    # the FP64 comparison solver, batched
+    Pf = P.replace(inner=1)
+    fsolv = [L.Solver(torch.from_numpy(sy.rowptr).to(dev), torch.from_numpy(sy.col).to(dev),
+                      torch.from_numpy(sy.val).to(dev), Pf) for sy in systems]
+    L.ir_solve_batched(fsolv, bs, xs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rf = L.ir_solve_batched(fsolv, bs, xs)
+    torch.cuda.synchronize()
+    dt_f = time.perf_counter() - t0
+    for sv in fsolv:
+        sv.close()
+    nsys = len(systems)
+    line = {"metric": METRIC, "value": nsys / dt, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "ms_per_step": 1000 * dt, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "systems": nsys, "rows": int(sum(x.n for x in systems)),
+                       "nnz": int(sum(x.nnz for x in systems)),
+                       "refinements_max": max(r["refinements"] for r in reps)},
+            "one_solve_per_launch": {"value": nsys / dt_one, "unit": "solves/s",
+                                     "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                                     "p99_ms": 1000 * float(np.percentile(lat, 99))},
+            "fp64_gmres_batched": {"value": nsys / dt_f, "unit": "solves/s",
+                                   "ok": all(r["status"] == "ok" for r in rf)},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, wl):
+    """cfg3: the first --requests requests of the serving stream, submitted at
+    their Poisson arrival times to a continuous-batching server."""
+    from paper_2009_07495_gb300 import _lib as L
+    reqs = W.config3_requests()[: args.requests]
+    systems = [W.request_system(r) for r in reqs]
+    m = wl["m"]
+    srv = L.Server(budget_bytes=150 * (1 << 30), m=m)
+    ids = []
+    t0 = time.perf_counter()
+    for r, sy in zip(reqs, systems):
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        P = L.params_default(0 if r.kind == "2d5" else 1, m, tol=r.tol)
+        ids.append(srv.submit(sy.rowptr, sy.col, sy.val, sy.b, P))
+    lats, oks = [], 0
+    for i in ids:
+        done, x, rep, lat = srv.poll(i, wait_ms=-1)
+        lats.append(lat)
+        oks += rep["status"] == "ok"
+    dt = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    line = {"metric": METRIC, "value": len(ids) / dt, "unit": "solves/s", "n_gpus": 1,
+            "steps": len(ids), "warmup": 0, "ms_per_step": 1000 * dt / len(ids),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "requests": len(ids),
+                       "offered_rate": 2000.0, "rows_total": int(sum(x.n for x in systems))},
+            "p50_ms": 1000 * float(np.percentile(lats, 50)),
+            "p99_ms": 1000 * float(np.percentile(lats, 99)),
+            "completed_ok": oks, "server": st}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -380,6 +518,10 @@ def main():
     if args.impl == "reference":
         wl["refinements"] = REFINEMENTS.get(args.workload, 4)
         run_reference(args, wl)
+    elif args.workload == "cfg2":
+        run_batched(args, wl)
+    elif args.workload == "cfg3":
+        run_serve(args, wl)
     else:
         run_ours(args, wl)
 

@@ -83,7 +83,8 @@ typedef struct {
   double tol;    /* epsilon of Fig. 1 (relative residual of the scaled system)*/
   int max_refine;/* maximum inner solves in Fig. 1                           */
   int inner;     /* 0: int-GMRES (Fig. 2); 1: FP64 GMRES(m) ("Double")       */
-  int reserved[6];
+  int trsv_chunk;/* rows per chunk of the line-5' substitutions (0: automatic)*/
+  int reserved[5];
 } igm_params;
 
 #define IGM_MAX_M 128
@@ -159,11 +160,10 @@ enum {
   IGM_K_SPMV = 0,       /* line 5, step j = m/2                            */
   IGM_K_TRSV_L = 1,     /* line 5' forward substitution                    */
   IGM_K_TRSV_U = 2,     /* line 5' backward substitution                   */
-  IGM_K_MGS = 3,        /* lines 7-8, one fused pass (i = m/2, j = m-1)     */
-  IGM_K_MGS_LAST = 4,   /* line 8 + line 10 + lines 12-19 (j = m-1)        */
-  IGM_K_NORMALIZE = 5,  /* line 11                                         */
-  IGM_K_RESID = 6,      /* eq. (b), FP64 residual of Fig. 1                */
-  IGM_K_COUNT = 7
+  IGM_K_ARNOLDI = 3,    /* lines 6-19 of the last step j = m-1 (m+1 MGS
+                           passes, norm, line 11, Givens)                  */
+  IGM_K_RESID = 4,      /* eq. (b), FP64 residual of Fig. 1                */
+  IGM_K_COUNT = 5
 };
 
 /* Average device time per launch (ms) of each kernel kind above, measured
@@ -177,6 +177,55 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream);
 /* Number of kernels the library has launched in this process (a graph
  * launch counts its kernel nodes). */
 long long igm_kernel_launches(void);
+
+/* ---- Serving: continuous batching of independent solves ---------------
+ * A server owns a worker thread and a CUDA stream.  Submitted requests
+ * (host arrays, copied at submission) wait in a FIFO queue; the worker
+ * admits them while the device memory of admitted systems stays within
+ * budget_bytes (and at most max_active are active), sets each one up on the
+ * device (int_gmres_setup) and keeps its matrix, factors, basis and
+ * refinement state resident until it finishes.  Work proceeds in rounds:
+ * one convergence test (Fig. 1) and one inner solve (Fig. 2) for every
+ * active system in the same kernels; requests that arrive meanwhile join
+ * at the next round, finished ones leave.  Each result is bit-identical to
+ * ir_solve on the same system alone.  All requests of a server share m and
+ * the inner solver (the config's m and inner). */
+typedef struct {
+  long long budget_bytes; /* device memory for admitted systems (> 0)         */
+  int max_active;         /* systems in flight at once (0: no limit)        */
+  int m;                  /* restart length every request must use          */
+  int inner;              /* 0 int-GMRES, 1 FP64 GMRES                      */
+  int reserved[5];
+} igm_server_config;
+
+typedef struct {
+  long long submitted, completed, failed, rounds;
+  long long peak_bytes;        /* largest admitted device memory            */
+  double busy_s;               /* worker time spent in rounds               */
+} igm_server_stats;
+
+igm_status igm_server_create(const igm_server_config *cfg, igm_server *out);
+
+/* Queues one solve of Ah xh = bh (host CSR arrays and right-hand side,
+ * copied before return; params->m and inner must match the server's).
+ * *id receives the request id.  Errors: IGM_EINVAL, IGM_EOOM (the system
+ * alone exceeds the budget). */
+igm_status igm_server_submit(igm_server s, int n, int nnz, const int *rowptr,
+                             const int *col, const double *val, const double *bhat,
+                             const igm_params *params, long long *id);
+
+/* Waits up to wait_ms (0: no wait, -1: forever) for request id.  *done = 1
+ * when finished: xhat (host, n doubles, may be NULL) receives the solution
+ * and rep (may be NULL) the report; the request is then forgotten.  The
+ * return value is the solve's status once done, IGM_OK while pending.
+ * lat_s (may be NULL) receives submit-to-completion seconds. */
+igm_status igm_server_poll(igm_server s, long long id, int wait_ms, double *xhat,
+                           igm_report *rep, double *lat_s, int *done);
+
+igm_status igm_server_get_stats(igm_server s, igm_server_stats *st);
+
+/* Stops the worker after the current round; pending requests are dropped. */
+void igm_server_destroy(igm_server s);
 
 /* Bytes of device memory the handle holds. */
 long long int_gmres_device_bytes(igm_handle h);

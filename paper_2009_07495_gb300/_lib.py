@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("beta11a", C.c_int), ("beta11b", C.c_int), ("beta13", C.c_int),
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("trsv_chunk", C.c_int), ("reserved", C.c_int * 5)]
 
     def replace(self, **kw) -> "Params":
         p = Params()
@@ -65,6 +65,17 @@ class Report(C.Structure):
                     relres_hist=np.array(self.relres_hist[:min(k + 1, 65)]))
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_longlong), ("max_active", C.c_int), ("m", C.c_int),
+                ("inner", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong),
+                ("failed", C.c_longlong), ("rounds", C.c_longlong),
+                ("peak_bytes", C.c_longlong), ("busy_s", C.c_double)]
+
+
 _VP = C.c_void_p
 _I = C.c_int
 
@@ -84,6 +95,13 @@ def _declare(lib):
         "igm_time_kernels": (_I, [_VP, _I, C.POINTER(C.c_double), _VP]),
         "igm_kernel_launches": (C.c_longlong, []),
         "int_gmres_destroy": (None, [_VP]),
+        "igm_server_create": (_I, [C.POINTER(ServerConfig), C.POINTER(_VP)]),
+        "igm_server_submit": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, C.POINTER(Params),
+                                   C.POINTER(C.c_longlong)]),
+        "igm_server_poll": (_I, [_VP, C.c_longlong, _I, _VP, C.POINTER(Report),
+                                 C.POINTER(C.c_double), C.POINTER(_I)]),
+        "igm_server_get_stats": (_I, [_VP, C.POINTER(ServerStats)]),
+        "igm_server_destroy": (None, [_VP]),
         "igm_last_error": (C.c_char_p, []),
         "igm_version": (C.c_char_p, []),
     }
@@ -258,6 +276,61 @@ def ir_solve_batched(solvers, bhats, xhats, stream=None) -> list[dict]:
     if st not in (0, 5):
         _check(st)
     return [r.as_dict() for r in reps]
+
+
+class Server:
+    """Continuous-batching solve server (igm_server_*): submit host systems,
+    poll for results."""
+
+    def __init__(self, budget_bytes: int, m: int, inner: int = 0, max_active: int = 0):
+        self._s = _VP()
+        cfg = ServerConfig(int(budget_bytes), int(max_active), int(m), int(inner))
+        _check(load().igm_server_create(C.byref(cfg), C.byref(self._s)))
+        self.m, self.inner = m, inner
+        self._n = {}
+
+    def submit(self, rowptr, col, val, bhat, params: Params) -> int:
+        rp, cl = _Buf(rowptr, np.int32), _Buf(col, np.int32)
+        vl, b = _Buf(val, np.float64), _Buf(bhat, np.float64)
+        if rp.cuda or b.cuda:
+            raise TypeError("the server takes host arrays")
+        rid = C.c_longlong(0)
+        _check(load().igm_server_submit(self._s, rp.len - 1, cl.len, rp.ptr, cl.ptr, vl.ptr,
+                                        b.ptr, C.byref(params), C.byref(rid)))
+        self._n[rid.value] = rp.len - 1
+        return rid.value
+
+    def poll(self, rid: int, wait_ms: int = -1):
+        """(done, x, report dict, latency_s); x/report are None while pending."""
+        n = self._n[rid]
+        x = np.empty(n)
+        rep = Report()
+        lat = C.c_double(0)
+        done = C.c_int(0)
+        st = load().igm_server_poll(self._s, rid, int(wait_ms), x.ctypes.data, C.byref(rep),
+                                    C.byref(lat), C.byref(done))
+        if not done.value:
+            return False, None, None, None
+        del self._n[rid]
+        if st not in (0, 5):
+            _check(st)
+        return True, x, rep.as_dict(), lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().igm_server_get_stats(self._s, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._s:
+            load().igm_server_destroy(self._s)
+            self._s = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

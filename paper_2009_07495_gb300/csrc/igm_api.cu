@@ -13,11 +13,9 @@
 #include <string>
 #include <vector>
 
-#include "igm_launch.h"
+#include "igm_host.h"
 
 using namespace igm;
-
-namespace {
 
 thread_local std::string g_err;
 
@@ -31,103 +29,29 @@ igm_status fail(igm_status st, const char *fmt, ...) {
   return st;
 }
 
-#define CK(call)                                                                  \
-  do {                                                                            \
-    cudaError_t e_ = (call);                                                      \
-    if (e_ != cudaSuccess) {                                                      \
-      cudaGetLastError();                                                         \
-      return fail(IGM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
-    }                                                                             \
-  } while (0)
-
-#define CKL()                                                                     \
-  do {                                                                            \
-    cudaError_t e_ = cudaGetLastError();                                          \
-    if (e_ != cudaSuccess) return fail(IGM_ECUDA, "launch: %s", cudaGetErrorString(e_)); \
-  } while (0)
-
-// A bump allocator over one cudaMalloc: 256-byte aligned sub-buffers.
-struct Arena {
-  char *base = nullptr;
-  size_t size = 0, off = 0;
-  std::vector<std::pair<void **, size_t>> plan;
-  template <class T>
-  void want(T **p, size_t count) { plan.push_back({(void **)p, count * sizeof(T)}); }
-  size_t total() const {
-    size_t t = 0;
-    for (auto &q : plan) t += (q.second + 255) & ~size_t(255);
-    return t + 256;
-  }
-  cudaError_t commit() {
-    size = total();
-    cudaError_t e = cudaMalloc((void **)&base, size);
-    if (e != cudaSuccess) return e;
-    size_t o = 0;
-    for (auto &q : plan) {
-      *q.first = base + o;
-      o += (q.second + 255) & ~size_t(255);
-    }
-    plan.clear();
-    return cudaSuccess;
-  }
-  void release() {
-    if (base) cudaFree(base);
-    base = nullptr;
-  }
-};
-
-}  // namespace
-
-struct Batch;
-
-struct igm_handle_s {
-  int n = 0, nnz = 0;
-  igm_params prm{};
-  Arena arena;
-  SysDev hs{};           // host copy of the descriptor (device pointers)
-  SysDev *d_sys = nullptr;
-  SysScal *d_sc = nullptr;
-  unsigned *d_err = nullptr;
-  Batch *solo = nullptr;  // batch of one, with its captured graphs
-};
-
-struct Batch {
-  std::vector<igm_handle> hs;
-  long long nodes_check = 0, nodes_cycle = 0;
-  int m = 0, any_ilu = 0;
-  Arena arena;
-  BatchDev bd{};
-  int *h_nact = nullptr;  // pinned
-  cudaStream_t cap = nullptr;
-  cudaGraphExec_t g_check = nullptr, g_cycle = nullptr;
-  ~Batch() {
-    if (g_check) cudaGraphExecDestroy(g_check);
-    if (g_cycle) cudaGraphExecDestroy(g_cycle);
-    if (cap) cudaStreamDestroy(cap);
-    if (h_nact) cudaFreeHost(h_nact);
-    arena.release();
-  }
-};
+std::atomic<long long> g_launches{0};
 
 namespace {
 
 std::mutex g_batches_mu;
-std::atomic<long long> g_launches{0};
 std::vector<Batch *> g_batches;  // cached multi-system batches
+
+}  // namespace
 
 igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   Batch *b = new Batch();
   b->hs = hs;
   int ns = (int)hs.size();
-  std::vector<Tile> tiles;
+  std::vector<Tile> tiles, ctiles;
   std::vector<int> snt(ns);
   std::vector<SysDev *> sp(ns);
   b->m = hs[0]->prm.m;
+  b->inner = hs[0]->prm.inner;
   for (int s = 0; s < ns; ++s) {
     igm_handle h = hs[s];
-    if (h->prm.m != b->m) {
+    if (h->prm.m != b->m || h->prm.inner != b->inner) {
       delete b;
-      return fail(IGM_EINVAL, "batched handles must share m");
+      return fail(IGM_EINVAL, "batched handles must share m and the inner solver");
     }
     b->any_ilu |= h->prm.precond;
     int first = (int)tiles.size();
@@ -136,15 +60,26 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
       tiles.push_back(Tile{s, t * IGM_TILE, std::min(IGM_TILE, h->n - t * IGM_TILE), first});
     snt[s] = nt;
     sp[s] = h->d_sys;
+    int cfirst = (int)ctiles.size();
+    for (int c = 0; c < h->hs.lnchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
   }
+  int CT = (int)ctiles.size();
+  Tile *d_ctiles = nullptr;
   int T = (int)tiles.size();
   Tile *d_tiles;
   int *d_snt, *d_nact;
   SysDev **d_sp;
   long long *d_part;
   double *d_partd;
-  unsigned *d_ticket;
+  unsigned *d_ticket, *d_bar;
+  u64 *d_acc;
+  double *d_cpart;
+  int maxg = persistent_grid(T);
   b->arena.want(&d_tiles, T);
+  b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
+  b->arena.want(&d_bar, 2);
+  b->arena.want(&d_acc, 6 * (size_t)ns);
+  b->arena.want(&d_cpart, 3 * (size_t)maxg * ns);
   b->arena.want(&d_snt, ns);
   b->arena.want(&d_sp, ns);
   b->arena.want(&d_part, 2 * (size_t)T);
@@ -157,21 +92,31 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
     return fail(IGM_EOOM, "batch arena");
   }
   CK(cudaMemcpy(d_tiles, tiles.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice));
+  if (CT > 0) CK(cudaMemcpy(d_ctiles, ctiles.data(), sizeof(Tile) * CT, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_snt, snt.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sp, sp.data(), sizeof(SysDev *) * ns, cudaMemcpyHostToDevice));
   CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
   CK(cudaMemset(d_nact, 0, sizeof(int)));
-  b->bd = BatchDev{ns, T, d_sp, d_tiles, d_snt, d_part, d_partd, d_ticket, d_nact};
+  CK(cudaMemset(d_bar, 0, 2 * sizeof(unsigned)));
+  CK(cudaMemset(d_acc, 0, 6 * sizeof(u64) * ns));
+  b->bd = BatchDev{ns,       T,      CT,    d_ctiles, d_sp,    d_tiles, d_snt,
+                   d_part,   d_partd, d_ticket, d_nact, d_bar, d_acc,   d_cpart, maxg};
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;
   return IGM_OK;
 }
 
+namespace {
+
 // lines 1-23 of Fig. 2 after line 1's residual: (line 1') r0 = M^-1 r,
 // ||r0||, cast, m Arnoldi steps, back-substitution and update
 void enqueue_inner(Batch *b, cudaStream_t st) {
   const BatchDev &B = b->bd;
+  if (b->inner == 1) {
+    launch_fp64_inner(B, b->m, b->any_ilu, st);
+    return;
+  }
   if (b->any_ilu) {
     launch_trsv_fp(B, 1, st);
     launch_trsv_fp(B, 0, st);
@@ -182,12 +127,10 @@ void enqueue_inner(Batch *b, cudaStream_t st) {
   for (int j = 0; j < b->m; ++j) {
     launch_spmv(B, j, st);
     if (b->any_ilu) {
-      launch_trsv_int(B, 1, st);
-      launch_trsv_int(B, 0, st);
+      launch_trsv_chunk(B, 1, st);
+      launch_trsv_chunk(B, 0, st);
     }
-    for (int i = 0; i <= j; ++i) launch_mgs(B, i, j, st);
-    launch_mgs_last(B, j, st);
-    launch_normalize(B, j, st);
+    launch_mgs_step(B, j, st);
   }
   launch_backsub(B, st);
   launch_update(B, st);
@@ -221,6 +164,18 @@ igm_status capture_graphs(Batch *b) {
   return IGM_OK;
 }
 
+// rows per substitution chunk: about one chunk per SM, a multiple of 1024
+int auto_chunk(int n) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long r = ((long long)n + sms - 1) / sms;
+  r = (r + 1023) / 1024 * 1024;
+  if (r < 1024) r = 1024;
+  if (r > (1 << 20)) r = 1 << 20;
+  return (int)r;
+}
+
 igm_status check_params(const igm_params *p) {
   if (!p) return fail(IGM_EINVAL, "params is NULL");
   if (p->df < 1 || p->df > 62) return fail(IGM_EINVAL, "df out of range");
@@ -233,7 +188,8 @@ igm_status check_params(const igm_params *p) {
     if (v < 0 || v > 62) return fail(IGM_EINVAL, "shift out of range");
   if (p->max_refine < 0 || p->max_refine > 64) return fail(IGM_EINVAL, "max_refine out of range");
   if (!(p->tol >= 0.0)) return fail(IGM_EINVAL, "tol must be >= 0");
-  if (p->inner != 0) return fail(IGM_EINVAL, "inner solver %d not available", p->inner);
+  if (p->inner != 0 && p->inner != 1) return fail(IGM_EINVAL, "inner must be 0 or 1");
+  if (p->trsv_chunk < 0) return fail(IGM_EINVAL, "trsv_chunk must be >= 0");
   return IGM_OK;
 }
 
@@ -313,7 +269,11 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   const int m = params->m, ilu = params->precond;
   SysDev &d = h->hs;
   int *rp, *cl, *dp, *lord = nullptr, *uord = nullptr, *lfl = nullptr, *ufl = nullptr;
-  int *lev = nullptr, *cnt = nullptr, *maxlev = nullptr;
+  int *llev = nullptr, *ulev = nullptr, *llptr = nullptr, *ulptr = nullptr;
+  int *llevb = nullptr, *ulevb = nullptr, *chmax = nullptr, *cnt = nullptr;
+  u64 *lprog = nullptr, *uprog = nullptr;
+  int R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n);
+  int nch = (n + R - 1) / R;
   double *ahat, *a, *dd, *f = nullptr, *b, *bh, *xt, *r, *t, *xk, *yfp;
   i64 *abar, *fac = nullptr, *ld = nullptr, *ud = nullptr, *w, *yv, *V, *H, *cs, *sn, *g;
   size_t nz = nnz > 0 ? nnz : 1;
@@ -334,9 +294,16 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     A.want(&uord, n);
     A.want(&lfl, n);
     A.want(&ufl, n);
-    A.want(&lev, n);
+    A.want(&llev, n);
+    A.want(&ulev, n);
+    A.want(&llptr, n + 1);
+    A.want(&ulptr, n + 1);
+    A.want(&llevb, nch + 1);
+    A.want(&ulevb, nch + 1);
+    A.want(&lprog, nch);
+    A.want(&uprog, nch);
+    A.want(&chmax, nch);
     A.want(&cnt, n + 1);
-    A.want(&maxlev, 2);
   }
   A.want(&b, n);
   A.want(&bh, n);
@@ -407,21 +374,31 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
         int_gmres_destroy(h);
         return fail(IGM_EZERO_PIVOT, "row %d has no stored diagonal (ILU(0))", i);
       }
+    // chunked level schedules of the two factors (L: chunks from the top,
+    // U: from the bottom; levels local to each chunk)
     unsigned *tick = (unsigned *)(h->d_err + 1);
-    int *ords[2] = {lord, uord};
-    int *flg[2] = {lfl, ufl};
+    int *ords[2] = {lord, uord}, *flg[2] = {lfl, ufl}, *levs[2] = {llev, ulev};
+    int *lptrs[2] = {llptr, ulptr}, *levbs[2] = {llevb, ulevb};
+    std::vector<int> hmax(nch), hlevb(nch + 1);
     for (int lower = 1; lower >= 0; --lower) {
-      CKH(cudaMemsetAsync(flg[1 - lower], 0, sizeof(int) * n, s));
+      int f = 1 - lower;
+      CKH(cudaMemsetAsync(flg[f], 0, sizeof(int) * n, s));
       CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
-      CKH(cudaMemsetAsync(maxlev, 0, sizeof(int), s));
-      launch_levels(n, rp, cl, dp, lower, lev, flg[1 - lower], 1, tick, maxlev, err, s);
-      int L = 0;
-      CKH(cudaMemcpyAsync(&L, maxlev, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CKH(cudaMemsetAsync(chmax, 0, sizeof(int) * nch, s));
+      launch_levels(n, rp, cl, dp, lower, R, levs[f], flg[f], 1, tick, chmax, err, s);
+      CKH(cudaMemcpyAsync(hmax.data(), chmax, sizeof(int) * nch, cudaMemcpyDeviceToHost, s));
       CKH(cudaStreamSynchronize(s));
-      L += 1;
+      hlevb[0] = 0;
+      for (int c = 0; c < nch; ++c) hlevb[c + 1] = hlevb[c] + hmax[c] + 1;
+      int L = hlevb[nch];
+      CKH(cudaMemcpyAsync(levbs[f], hlevb.data(), sizeof(int) * (nch + 1),
+                          cudaMemcpyHostToDevice, s));
       CKH(cudaMemsetAsync(cnt, 0, sizeof(int) * (L + 1), s));
-      launch_level_order(n, L, lev, cnt, ords[1 - lower], s);
+      launch_level_order(n, lower, R, L, levs[f], levbs[f], cnt, lptrs[f], ords[f], s);
+      CKH(cudaStreamSynchronize(s));
     }
+    CKH(cudaMemsetAsync(lprog, 0, sizeof(u64) * nch, s));
+    CKH(cudaMemsetAsync(uprog, 0, sizeof(u64) * nch, s));
     CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
     CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
     launch_ilu0(n, rp, cl, dp, lord, f, lfl, 2, tick, err, s);
@@ -455,6 +432,16 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.udiag = ud;
   d.lorder = lord;
   d.uorder = uord;
+  d.llptr = llptr;
+  d.ulptr = ulptr;
+  d.llevb = llevb;
+  d.ulevb = ulevb;
+  d.chunk = R;
+  d.lnchunk = d.unchunk = ilu ? nch : 0;
+  d.llev = llev;
+  d.ulev = ulev;
+  d.lprog = lprog;
+  d.uprog = uprog;
   d.lflag = lfl;
   d.uflag = ufl;
   d.b = b;
@@ -513,14 +500,12 @@ long long int_gmres_device_bytes(igm_handle h) { return h ? (long long)h->arena.
 
 }  // extern "C"
 
-namespace {
+// ---- helpers shared with the serving runtime ------------------------------
 
-// Fig. 1 over a batch: b = D^-1 bh, norms, then {test, inner solve} until
-// every system has converged or reached max_refine.
-igm_status run_ir(Batch *b, cudaStream_t s) {
+// Fig. 1 set-up of every system of a batch: state reset, b = D^-1 bh, x = 0,
+// ||b|| and ||bh||
+igm_status ir_init_host(Batch *b, cudaStream_t s) {
   const BatchDev &B = b->bd;
-  igm_status st = capture_graphs(b);
-  if (st) return st;
   launch_init_scal(B, 0, s);
   launch_init_ir(B, s);
   launch_max(B, VEC_B, 0, s);
@@ -529,6 +514,41 @@ igm_status run_ir(Batch *b, cudaStream_t s) {
   launch_norm(B, VEC_BH, ACT_NBH, 0, s);
   CKL();
   g_launches += 6;
+  return IGM_OK;
+}
+
+// residual of the original system, for the report
+igm_status ir_finish_host(Batch *b, cudaStream_t s) {
+  launch_resid(b->bd, 1, s);
+  launch_norm(b->bd, VEC_R, ACT_UNSC, 0, s);
+  CKL();
+  g_launches += 2;
+  return IGM_OK;
+}
+
+void enqueue_inner_host(Batch *b, cudaStream_t st) { enqueue_inner(b, st); }
+
+// device bytes int_gmres_setup will hold for a system (an upper estimate of
+// the arena: every buffer rounded up to 256 bytes)
+long long handle_bytes_estimate(int n, int nnz, const igm_params *p) {
+  long long N = n, Z = nnz > 0 ? nnz : 1, m = p->m, r = 0;
+  r += 4 * (N + 1) + 4 * Z + 4 * N;                 // rowptr, col, diagpos
+  r += 8 * Z * 3 + 8 * N;                           // ahat, a, abar, d
+  if (p->precond) r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
+  r += 8 * N * 8 + 8 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
+  return r + 64 * 256 + (long long)sizeof(SysScal) + sizeof(SysDev);
+}
+
+namespace {
+
+// Fig. 1 over a batch: b = D^-1 bh, norms, then {test, inner solve} until
+// every system has converged or reached max_refine.
+igm_status run_ir(Batch *b, cudaStream_t s) {
+  const BatchDev &B = b->bd;
+  igm_status st = capture_graphs(b);
+  if (st) return st;
+  st = ir_init_host(b, s);
+  if (st) return st;
   int maxr = 0;
   for (auto h : b->hs) maxr = std::max(maxr, h->prm.max_refine);
   for (int k = 0; k <= maxr + 1; ++k) {
@@ -540,15 +560,12 @@ igm_status run_ir(Batch *b, cudaStream_t s) {
     CK(cudaGraphLaunch(b->g_cycle, s));
     g_launches += b->nodes_cycle;
   }
-  // residual of the original system for the report
-  launch_resid(B, 1, s);
-  launch_norm(B, VEC_R, ACT_UNSC, 0, s);
-  CKL();
-  g_launches += 2;
-  return IGM_OK;
+  return ir_finish_host(b, s);
 }
 
-igm_status collect(igm_handle h, igm_report *rep, cudaStream_t s) {
+}  // namespace
+
+igm_status collect_host(igm_handle h, igm_report *rep, cudaStream_t s) {
   SysScal sc;
   unsigned e = 0;
   CK(cudaMemcpyAsync(&sc, h->d_sc, sizeof(SysScal), cudaMemcpyDeviceToHost, s));
@@ -564,8 +581,6 @@ igm_status collect(igm_handle h, igm_report *rep, cudaStream_t s) {
   return IGM_OK;
 }
 
-}  // namespace
-
 extern "C" {
 
 igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *rep,
@@ -577,7 +592,7 @@ igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *
   igm_status st = run_ir(h->solo, s);
   if (st) return st;
   CK(cudaMemcpyAsync(xhat, h->hs.xt, sizeof(double) * h->n, cudaMemcpyDefault, s));
-  return collect(h, rep, s);
+  return collect_host(h, rep, s);
 }
 
 igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat,
@@ -611,7 +626,7 @@ igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat
     CK(cudaMemcpyAsync(xhat[i], v[i]->hs.xt, sizeof(double) * v[i]->n, cudaMemcpyDefault, s));
   igm_status worst = IGM_OK;
   for (int i = 0; i < count; ++i) {
-    igm_status e = collect(v[i], reps ? reps + i : nullptr, s);
+    igm_status e = collect_host(v[i], reps ? reps + i : nullptr, s);
     if (e && !worst) worst = e;
   }
   return worst;
@@ -627,14 +642,14 @@ igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_repor
   CK(cudaMemcpyAsync(h->hs.t, bk, sizeof(double) * h->n, cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(h->hs.xk, xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
   launch_init_scal(B, 1, s);
-  launch_resid_int(B, s);
+  if (b->inner == 1) launch_fp64_resid_guess(B, s);
+  else launch_resid_int(B, s);
   launch_arm(B, s);
   enqueue_inner(b, s);
   CKL();
-  g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) +
-                (long long)b->m * (3 + (b->any_ilu ? 2 : 0)) + (long long)b->m * (b->m + 1) / 2;
+  g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) + (long long)b->m * (4 + (b->any_ilu ? 2 : 0));
   CK(cudaMemcpyAsync(xk, h->hs.xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
-  igm_status st = collect(h, rep, s);
+  igm_status st = collect_host(h, rep, s);
   if (st == IGM_ENOCONV) st = IGM_OK;  // a single inner solve has no test
   if (rep && rep->status == IGM_ENOCONV) rep->status = IGM_OK;
   return st;
@@ -679,7 +694,7 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
   run.early = 0;
   run.active = 1;
   run.hnext = (i64)1 << 30;
-  run.normj = m - 1;
+  run.normj = -1;
   CK(cudaMemcpyAsync(h->d_sc, &run, sizeof(SysScal), cudaMemcpyHostToDevice, s));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -690,15 +705,13 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
     float tot = 0.f;
     for (int r = 0; r < reps; ++r) {
       if (k == IGM_K_TRSV_L || k == IGM_K_TRSV_U) launch_spmv(B, m / 2, s);  // arms flags
-      if (k == IGM_K_TRSV_U) launch_trsv_int(B, 1, s);
+      if (k == IGM_K_TRSV_U) launch_trsv_chunk(B, 1, s);
       CK(cudaEventRecord(e0, s));
       switch (k) {
         case IGM_K_SPMV: launch_spmv(B, m / 2, s); break;
-        case IGM_K_TRSV_L: launch_trsv_int(B, 1, s); break;
-        case IGM_K_TRSV_U: launch_trsv_int(B, 0, s); break;
-        case IGM_K_MGS: launch_mgs(B, m / 2, m - 1, s); break;
-        case IGM_K_MGS_LAST: launch_mgs_last(B, m - 1, s); break;
-        case IGM_K_NORMALIZE: launch_normalize(B, m - 1, s); break;
+        case IGM_K_TRSV_L: launch_trsv_chunk(B, 1, s); break;
+        case IGM_K_TRSV_U: launch_trsv_chunk(B, 0, s); break;
+        case IGM_K_ARNOLDI: launch_mgs_step(B, m - 1, s); break;
         case IGM_K_RESID: launch_resid(B, 0, s); break;
       }
       CK(cudaEventRecord(e1, s));
@@ -706,7 +719,7 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, e0, e1));
       tot += t;
-      if (k == IGM_K_MGS_LAST || k == IGM_K_NORMALIZE) {  // the Givens step may end the solve: re-arm
+      if (k == IGM_K_ARNOLDI) {  // the Givens step may end the solve: re-arm
         CK(cudaMemcpyAsync(h->d_sc, &run, sizeof(SysScal), cudaMemcpyHostToDevice, s));
       }
     }

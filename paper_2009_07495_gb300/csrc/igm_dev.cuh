@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/igm.h"
 #include "igm_internal.h"
 
 typedef __int128 i128;
@@ -218,6 +219,15 @@ __device__ __forceinline__ void st_release(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ u64 ld_acquire64(const u64 *p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release64(u64 *p, u64 v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 #define IGM_SPIN_MAX (1 << 22)
 
 // wait until *flag >= epoch; false (and an error bit) if the bound expires.
@@ -228,6 +238,18 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int epoch, unsigned *
   for (int it = 0; it < IGM_SPIN_MAX; ++it) {
     __nanosleep(32);
     if (ld_acquire(flag) >= epoch) return true;
+    if ((it & 255) == 255 && (*(volatile unsigned *)err & ERR_TIMEOUT)) return false;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+// wait until *prog >= target (64-bit progress word), bounded like wait_flag
+__device__ __forceinline__ bool wait_prog(const u64 *prog, u64 target, unsigned *err) {
+  if (ld_acquire64(prog) >= target) return true;
+  for (int it = 0; it < IGM_SPIN_MAX; ++it) {
+    if (it > 32) __nanosleep(16);
+    if (ld_acquire64(prog) >= target) return true;
     if ((it & 255) == 255 && (*(volatile unsigned *)err & ERR_TIMEOUT)) return false;
   }
   atomicOr(err, ERR_TIMEOUT);
@@ -258,6 +280,50 @@ __device__ __forceinline__ i128 load_part(const long long *part, int t) {
 __device__ __forceinline__ void store_part(long long *part, int t, i128 v) {
   part[2 * t] = (long long)(u64)(u128)v;
   part[2 * t + 1] = (long long)(u64)((u128)v >> 64);
+}
+
+// Givens rotation update of column j (lines 12-19), one thread
+static __device__ __noinline__ void givens_col(const SysDev *s, SysScal *sc, int j, i64 hj1) {
+  const SysParams &P = s->p;
+  const int ld = s->ld, df = P.df;
+  i64 *H = s->H;
+  unsigned e13 = 0, e15 = 0, e16 = 0, e17 = 0;
+  bool zero = shr(hj1, P.b11b) == 0;
+  for (int i = 0; i < j; ++i) {
+    i64 a = shr(H[i + j * ld], P.b13), b = shr(H[i + 1 + j * ld], P.b13);
+    i64 p1 = mulw(s->cs[i], a, e13), p2 = mulw(s->sn[i], b, e13);
+    i128 t1 = (i128)p1 + (i128)p2;
+    e13 += out64(t1);
+    i64 p3 = mulw(negw(s->sn[i], e13), a, e13), p4 = mulw(s->cs[i], b, e13);
+    i128 t2 = (i128)p3 + (i128)p4;
+    e13 += out64(t2);
+    H[i + j * ld] = shr(wrap(t1), df - P.b13);
+    H[i + 1 + j * ld] = shr(wrap(t2), df - P.b13);
+  }
+  i64 hjj = H[j + j * ld], hn = H[j + 1 + j * ld];
+  i64 a15 = shr(hjj, P.b15), b15 = shr(hn, P.b15);
+  i128 s15 = (i128)mulw(a15, a15, e15) + (i128)mulw(b15, b15, e15);
+  e15 += out64(s15);
+  i64 tmp = fx_sqrt(wrap(s15), 2 * df - 2 * P.b15, df, e15);
+  if (shr(tmp, P.b16b) == 0) {
+    sc->early = 1;  // singular column: the solve uses j columns
+  } else {
+    i64 c = fx_div(hjj, tmp, P.b16a, P.b16b, df, e16);
+    i64 sn = fx_div(hn, tmp, P.b16a, P.b16b, df, e16);
+    s->cs[j] = c;
+    s->sn[j] = sn;
+    i64 gj = s->g[j];
+    s->g[j + 1] = shr(mulw(negw(sn, e17), gj, e17), df);
+    s->g[j] = shr(mulw(c, gj, e17), df);
+    H[j + j * ld] = tmp;
+    H[j + 1 + j * ld] = 0;
+    sc->jeff = j + 1;
+    if (zero) sc->early = 1;
+  }
+  if (e13) atomicAdd(&sc->ev[IGM_EV_L13], (u64)e13);
+  if (e15) atomicAdd(&sc->ev[IGM_EV_L15], (u64)e15);
+  if (e16) atomicAdd(&sc->ev[IGM_EV_L16], (u64)e16);
+  if (e17) atomicAdd(&sc->ev[IGM_EV_L17], (u64)e17);
 }
 
 }  // namespace igm

@@ -64,7 +64,13 @@ struct SysDev {
   const i64 *abar;
   const double *f;                       // FP64 ILU(0) factors
   const i64 *fac, *ldiag, *udiag;        // integer factors
-  const int *lorder, *uorder;
+  // substitution schedules: rows in chunk order, each chunk in local-level
+  // order (L: chunks from the top, U: from the bottom); lptr: start of each
+  // (chunk, level) group in the order; levb: first group of each chunk
+  const int *lorder, *uorder, *llptr, *ulptr, *llevb, *ulevb;
+  int chunk, lnchunk, unchunk;  // rows per chunk, chunks of L and U
+  const int *llev, *ulev;       // local level of every row in its chunk
+  u64 *lprog, *uprog;           // per chunk: (epoch << 32) | levels done
   int *lflag, *uflag;
   double *b, *bh, *xt, *r, *t, *xk;
   i64 *w, *yv, *V;
@@ -82,6 +88,8 @@ struct Tile {
 
 struct BatchDev {
   int nsys, ntiles;
+  int nctiles;             // substitution chunks over all systems
+  const Tile *ctiles;      // {sys, chunk index, -, first chunk tile}
   SysDev *const *sys;      // device pointers to each system's SysDev
   const Tile *tiles;
   const int *sys_ntiles;   // tiles per system
@@ -89,6 +97,10 @@ struct BatchDev {
   double *partd;           // ntiles
   unsigned *ticket;        // 4 dynamic-ticket counters
   int *nact;               // systems still refining
+  unsigned *bar;           // grid barrier: [0] arrivals, [1] generation
+  u64 *acc;                // 3 slots x nsys x {lo, hi}: exact int128 sums
+  double *cpart;           // 3 slots x maxG x nsys FP64 per-CTA partials
+  int maxg;                // CTAs of the persistent kernels
 };
 
 // vector selectors for the generic max / norm kernels

@@ -14,10 +14,10 @@ void launch_scale(int n, const int *rowptr, const double *ahat, int alpha, doubl
                   double *d, unsigned *err, cudaStream_t st);
 void launch_cast(long long nnz, const double *a, i64 *abar, unsigned *err, cudaStream_t st);
 void launch_levels(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
-                   int *level, int *flag, int epoch, unsigned *ticket, int *maxlev,
+                   int R, int *level, int *flag, int epoch, unsigned *ticket, int *chunkmax,
                    unsigned *err, cudaStream_t st);
-void launch_level_order(int n, int L, const int *level, int *cnt, int *order,
-                        cudaStream_t st);
+void launch_level_order(int n, int lower, int R, int L, const int *level, const int *levb,
+                        int *cnt, int *lptr, int *order, cudaStream_t st);
 void launch_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
                  const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
                  unsigned *err, cudaStream_t st);
@@ -35,13 +35,19 @@ void launch_resid_int(const BatchDev &B, cudaStream_t st);
 void launch_rhs(const BatchDev &B, cudaStream_t st);
 void launch_arm(const BatchDev &B, cudaStream_t st);
 void launch_trsv_fp(const BatchDev &B, int lower, cudaStream_t st);
-void launch_trsv_int(const BatchDev &B, int lower, cudaStream_t st);
+void launch_trsv_chunk(const BatchDev &B, int lower, cudaStream_t st);
 void launch_cast_v1(const BatchDev &B, cudaStream_t st);
 void launch_spmv(const BatchDev &B, int j, cudaStream_t st);
-void launch_mgs(const BatchDev &B, int i, int j, cudaStream_t st);
-void launch_mgs_last(const BatchDev &B, int j, cudaStream_t st);
-void launch_normalize(const BatchDev &B, int j, cudaStream_t st);
+// lines 6-19 of step j: persistent MGS + norm + line 11, then Givens
+void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st);
+void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st);
+int persistent_grid(int ntiles);  // CTAs of the persistent kernels
 void launch_backsub(const BatchDev &B, cudaStream_t st);
 void launch_update(const BatchDev &B, cudaStream_t st);
+void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st);
+
+// FP64 GMRES(m) comparison solver (lines 1-23 after line 1's residual)
+void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, cudaStream_t st);
+void launch_fp64_resid_guess(const BatchDev &B, cudaStream_t st);
 
 }  // namespace igm

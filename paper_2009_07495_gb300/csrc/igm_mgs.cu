@@ -1,0 +1,336 @@
+// igm_mgs.cu -- lines 6-11 of Fig. 2 (modified Gram-Schmidt, norm, division)
+// for one Arnoldi step j as ONE persistent kernel: all CTAs are co-resident
+// (cooperative launch) and sweep the rows of every system once per pass;
+// between passes the exact int128 sum of the pass is formed by two-word
+// atomics (low word with carry into the high word) and published by a
+// bounded grid barrier.  Pass i <= j fuses the line-8 update with h_{i-1,j}
+// and the line-7 inner product with v_i; pass j+1 fuses the last update with
+// the line-10 norm; then line 11 and (one thread per system) lines 12-19.
+// The basis streams from HBM once per pass; w stays in L2.
+#include "igm_dev.cuh"
+#include "igm_launch.h"
+
+namespace igm {
+
+// one CTA per SM: few grid-barrier arrivals, many rows in flight per CTA
+#define IGM_MGS_BLOCK 1024
+
+// sense-reversal grid barrier with a bounded wait; false if it expired
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int it = 0;
+      while (*gen == g) {
+        if (++it > IGM_SPIN_MAX) {
+          atomicOr(err, ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if (it > 64) __nanosleep(20);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void acc_add(u64 *a, i128 v) {
+  u64 lo = (u64)(u128)v, hi = (u64)((u128)v >> 64);
+  u64 old = atomicAdd(a, lo);
+  u64 carry = (old + lo) < old ? 1ull : 0ull;
+  atomicAdd(a + 1, hi + carry);
+}
+
+__device__ __forceinline__ i128 acc_load(const u64 *a) {
+  u64 lo = __ldcg((const unsigned long long *)a), hi = __ldcg((const unsigned long long *)a + 1);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
+__device__ __forceinline__ u64 *acc_slot(const BatchDev &B, int slot, int sys) {
+  return B.acc + 2 * ((size_t)slot * B.nsys + sys);
+}
+
+__device__ __forceinline__ bool m_step(const SysDev *s, int j) {
+  return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
+}
+
+__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j) {
+  const int G = gridDim.x;
+  unsigned *err0 = &B.sys[0]->sc->err;
+  for (int i = 0; i <= j + 1; ++i) {
+    const int slot = i % 3;
+    // slot (i+1)%3 was last read right after barrier i-2, before barrier i-1
+    if (blockIdx.x == 0)
+      for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
+        u64 *a = acc_slot(B, (i + 1) % 3, s);
+        a[0] = 0;
+        a[1] = 0;
+      }
+    for (int t = blockIdx.x; t < B.ntiles; t += G) {
+      Tile tl = B.tiles[t];
+      const SysDev *s = B.sys[tl.sys];
+      if (!m_step(s, j)) continue;
+      const SysParams &P = s->p;
+      const int n = s->n, df = P.df;
+      SysScal *sc = s->sc;
+      // h_{i-1,j} from the previous pass's exact sum
+      i64 hs = 0;
+      if (i > 0) {
+        i128 tot = acc_load(acc_slot(B, (i - 1) % 3, tl.sys));
+        i64 h = shr(wrap(tot), df - P.b7);
+        hs = shr(h, P.b8);
+      }
+      const i64 *vp = s->V + (size_t)(i > 0 ? i - 1 : 0) * n;
+      const i64 *vi = s->V + (size_t)(i <= j ? i : 0) * n;
+      unsigned evA = 0, evB = 0;
+      i128 part = 0;
+      for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
+        i64 wl = s->w[l];
+        if (i > 0) {
+          i64 p = shr(mulw(hs, vp[l], evB), df - P.b8);
+          i128 d = (i128)wl - (i128)p;
+          evB += out64(d);
+          wl = wrap(d);
+          s->w[l] = wl;
+        }
+        if (i <= j) {
+          part += (i128)mulw(shr(wl, P.b7), vi[l], evA);
+        } else {
+          i64 a = shr(wl, P.b10);
+          part += (i128)mulw(a, a, evA);
+        }
+      }
+      flush_ev(evB, &sc->ev[IGM_EV_L8]);
+      flush_ev(evA, &sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+      part = block_sum_i128(part);
+      if (threadIdx.x == 0) acc_add(acc_slot(B, slot, tl.sys), part);
+    }
+    if (!grid_sync(B.bar, err0)) return;
+    // one thread records h_{i,j} (and the total's overflow event) per system
+    if (blockIdx.x == 0)
+      for (int sidx = threadIdx.x; sidx < B.nsys; sidx += blockDim.x) {
+        const SysDev *s = B.sys[sidx];
+        if (!m_step(s, j)) continue;
+        const SysParams &P = s->p;
+        i128 tot = acc_load(acc_slot(B, slot, sidx));
+        unsigned e = out64(tot);
+        if (i <= j) {
+          s->H[i + j * s->ld] = shr(wrap(tot), P.df - P.b7);
+          if (e) atomicAdd(&s->sc->ev[IGM_EV_L7], (u64)e);
+        } else {
+          (void)fx_sqrt(wrap(tot), 2 * P.df - 2 * P.b10, P.df, e);
+          if (e) atomicAdd(&s->sc->ev[IGM_EV_L10], (u64)e);
+        }
+      }
+  }
+  // line 11 for every system whose divisor is non-zero
+  const int slot = (j + 1) % 3;
+  for (int t = blockIdx.x; t < B.ntiles; t += G) {
+    Tile tl = B.tiles[t];
+    const SysDev *s = B.sys[tl.sys];
+    if (!m_step(s, j)) continue;
+    const SysParams &P = s->p;
+    unsigned e10 = 0, ev = 0, evr = 0;
+    i64 hn = fx_sqrt(wrap(acc_load(acc_slot(B, slot, tl.sys))), 2 * P.df - 2 * P.b10, P.df, e10);
+    if (shr(hn, P.b11b) == 0) continue;
+    i64 *vn = s->V + (size_t)(j + 1) * s->n;
+    for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
+      i64 q = fx_div(s->w[l], hn, P.b11a, P.b11b, P.df, ev);
+      evr += (q < INT32_MIN || q > INT32_MAX);
+      vn[l] = q;
+    }
+    flush_ev(ev, &s->sc->ev[IGM_EV_L11]);
+    flush_ev(evr, &s->sc->ev[IGM_EV_VRANGE]);
+  }
+}
+
+// lines 10 (store) and 12-19 after k_mgs_step, one thread per system
+__global__ void k_givens_step(BatchDev B, int j) {
+  int si = blockIdx.x * blockDim.x + threadIdx.x;
+  if (si >= B.nsys) return;
+  const SysDev *s = B.sys[si];
+  SysScal *sc = s->sc;
+  if (!m_step(s, j)) return;
+  const SysParams &P = s->p;
+  unsigned e = 0;
+  i64 hj1 = fx_sqrt(wrap(acc_load(acc_slot(B, (j + 1) % 3, si))), 2 * P.df - 2 * P.b10, P.df, e);
+  s->H[j + 1 + j * s->ld] = hj1;
+  sc->hnext = hj1;
+  sc->normj = shr(hj1, P.b11b) == 0 ? -1 : j;
+  givens_col(s, sc, j, hj1);
+}
+
+// keeps accumulator slot 0 zero between steps (pass 0 of the next step sums
+// into it); runs after k_givens_step has read the last slot
+__global__ void k_acc_clear(BatchDev B) {
+  for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < B.nsys; si += gridDim.x * blockDim.x) {
+    u64 *a = acc_slot(B, 0, si);
+    a[0] = 0;
+    a[1] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same step for the FP64 comparison solver: per-CTA partial sums per
+// system, summed by every CTA in CTA order after the barrier, so the result
+// is deterministic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double *cpart_at(const BatchDev &B, int slot, int cta, int sys) {
+  return B.cpart + ((size_t)slot * B.maxg + cta) * B.nsys + sys;
+}
+
+__device__ __forceinline__ double cpart_sum(const BatchDev &B, int slot, int sys) {
+  double t = 0.0;
+  for (int c = 0; c < gridDim.x; ++c) t = __dadd_rn(t, __ldcg(cpart_at(B, slot, c, sys)));
+  return t;
+}
+
+__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) f_mgs_step(BatchDev B, int j) {
+  const int G = gridDim.x;
+  unsigned *err0 = &B.sys[0]->sc->err;
+  __shared__ double s_part;
+  for (int i = 0; i <= j + 1; ++i) {
+    const int slot = i % 3;
+    // this CTA's partials of every system start at zero
+    for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) *cpart_at(B, slot, blockIdx.x, s) = 0.0;
+    __syncthreads();
+    for (int t = blockIdx.x; t < B.ntiles; t += G) {
+      Tile tl = B.tiles[t];
+      const SysDev *s = B.sys[tl.sys];
+      if (!m_step(s, j)) continue;
+      const int n = s->n;
+      const double *V = reinterpret_cast<const double *>(s->V);
+      double *w = reinterpret_cast<double *>(s->w);
+      if (threadIdx.x == 0) s_part = i > 0 ? cpart_sum(B, (i - 1) % 3, tl.sys) : 0.0;
+      __syncthreads();
+      double h = s_part;
+      const double *vp = V + (size_t)(i > 0 ? i - 1 : 0) * n;
+      const double *vi = V + (size_t)(i <= j ? i : 0) * n;
+      double part = 0.0;
+      for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
+        double wl = w[l];
+        if (i > 0) {
+          wl = __dsub_rn(wl, __dmul_rn(h, vp[l]));
+          w[l] = wl;
+        }
+        part = __dadd_rn(part, __dmul_rn(wl, i <= j ? vi[l] : wl));
+      }
+      part = block_sum_d(part);
+      if (threadIdx.x == 0) {
+        double *cp = cpart_at(B, slot, blockIdx.x, tl.sys);
+        *cp = __dadd_rn(*cp, part);
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(B.bar, err0)) return;
+    if (blockIdx.x == 0)
+      for (int sidx = threadIdx.x; sidx < B.nsys; sidx += blockDim.x) {
+        const SysDev *s = B.sys[sidx];
+        if (!m_step(s, j) || i > j) continue;
+        reinterpret_cast<double *>(s->H)[i + j * s->ld] = cpart_sum(B, slot, sidx);
+      }
+  }
+  const int slot = (j + 1) % 3;
+  for (int t = blockIdx.x; t < B.ntiles; t += G) {
+    Tile tl = B.tiles[t];
+    const SysDev *s = B.sys[tl.sys];
+    if (!m_step(s, j)) continue;
+    __syncthreads();
+    if (threadIdx.x == 0) s_part = __dsqrt_rn(cpart_sum(B, slot, tl.sys));
+    __syncthreads();
+    double hn = s_part;
+    if (hn == 0.0) continue;
+    double *vn = reinterpret_cast<double *>(s->V) + (size_t)(j + 1) * s->n;
+    const double *w = reinterpret_cast<const double *>(s->w);
+    for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x)
+      vn[l] = __ddiv_rn(w[l], hn);
+  }
+}
+
+// h_{j+1,j} and the Givens rotation of column j (FP64), one thread per system
+__global__ void f_givens_step(BatchDev B, int j, int G) {
+  int si = blockIdx.x * blockDim.x + threadIdx.x;
+  if (si >= B.nsys) return;
+  const SysDev *s = B.sys[si];
+  SysScal *sc = s->sc;
+  if (!m_step(s, j)) return;
+  const int ld = s->ld, slot = (j + 1) % 3;
+  double t2 = 0.0;
+  for (int c = 0; c < G; ++c) t2 = __dadd_rn(t2, cpart_at(B, slot, c, si)[0]);
+  double hn = __dsqrt_rn(t2);
+  double *H = reinterpret_cast<double *>(s->H);
+  double *cs = reinterpret_cast<double *>(s->cs), *sn = reinterpret_cast<double *>(s->sn);
+  double *g = reinterpret_cast<double *>(s->g);
+  H[j + 1 + j * ld] = hn;
+  for (int i = 0; i < j; ++i) {
+    double x1 = H[i + j * ld], x2 = H[i + 1 + j * ld];
+    H[i + j * ld] = __dadd_rn(__dmul_rn(cs[i], x1), __dmul_rn(sn[i], x2));
+    H[i + 1 + j * ld] = __dadd_rn(__dmul_rn(-sn[i], x1), __dmul_rn(cs[i], x2));
+  }
+  double hjj = H[j + j * ld], hj1 = H[j + 1 + j * ld];
+  double t = __dsqrt_rn(__dadd_rn(__dmul_rn(hjj, hjj), __dmul_rn(hj1, hj1)));
+  if (t == 0.0) {
+    sc->early = 1;
+    return;
+  }
+  double c = __ddiv_rn(hjj, t), sv = __ddiv_rn(hj1, t);
+  cs[j] = c;
+  sn[j] = sv;
+  double gj = g[j];
+  g[j + 1] = __dmul_rn(-sv, gj);
+  g[j] = __dmul_rn(c, gj);
+  H[j + j * ld] = t;
+  H[j + 1 + j * ld] = 0.0;
+  sc->jeff = j + 1;
+  if (hn == 0.0) sc->early = 1;
+}
+
+static int g_mgs_blocks_per_sm = -1, g_num_sms = 0;
+
+int persistent_grid(int ntiles) {
+  if (g_mgs_blocks_per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step, IGM_MGS_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0);
+    g_mgs_blocks_per_sm = a < b ? a : b;
+    if (g_mgs_blocks_per_sm < 1) g_mgs_blocks_per_sm = 1;
+  }
+  int G = g_num_sms * g_mgs_blocks_per_sm;
+  if (G > ntiles) G = ntiles;
+  return G < 1 ? 1 : G;
+}
+
+void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
+  int G = persistent_grid(B.ntiles);
+  BatchDev b = B;
+  void *args[] = {&b, &j};
+  cudaLaunchCooperativeKernel((const void *)f_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);
+  f_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j, G);
+}
+
+void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
+  int G = persistent_grid(B.ntiles);
+  BatchDev b = B;
+  void *args[] = {&b, &j};
+  cudaLaunchCooperativeKernel((const void *)k_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);
+  k_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j);
+  k_acc_clear<<<(B.nsys + 255) / 256, 256, 0, st>>>(B);
+}
+
+}  // namespace igm

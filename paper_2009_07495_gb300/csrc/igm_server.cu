@@ -1,0 +1,327 @@
+// igm_server.cu -- serving runtime: continuous batching of independent
+// refinement solves (Fig. 1 with int-GMRES) on one GPU.
+//
+// Requests are queued on the host; a worker thread admits them in arrival
+// order while the device memory held by admitted systems stays within the
+// budget, sets each up on the device and keeps its state resident.  Each
+// round runs the convergence test of Fig. 1 and one inner solve of Fig. 2
+// for all active systems in the same kernels (a batch over their tiles);
+// systems admitted during a round join the next one, converged systems are
+// finalised and release their memory after the round.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "igm_host.h"
+
+using namespace igm;
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+  long long id = 0;
+  int n = 0, nnz = 0;
+  std::vector<int> rowptr, col;
+  std::vector<double> val, b, x;
+  igm_params prm{};
+  clk::time_point t_submit, t_done;
+  igm_report rep{};
+  igm_status status = IGM_OK;
+  bool done = false;
+  igm_handle h = nullptr;
+  long long bytes = 0;
+};
+
+}  // namespace
+
+struct igm_server_s {
+  igm_server_config cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request *> queue;
+  std::map<long long, Request *> all;
+  std::vector<Request *> active;
+  long long next_id = 1, used = 0;
+  igm_server_stats st{};
+  bool stop = false;
+  std::thread worker;
+  cudaStream_t stream = nullptr;
+  int dev = 0;
+  Batch *batch = nullptr;
+  bool dirty = true;
+  int4 *d_state = nullptr, *h_state = nullptr;
+  int state_cap = 0;
+};
+
+namespace {
+
+void finish(igm_server_s *S, Request *r, igm_status st) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->status = st;
+  r->rep.status = st;
+  r->t_done = clk::now();
+  r->done = true;
+  if (st == IGM_OK || st == IGM_ENOCONV) S->st.completed++;
+  else S->st.failed++;
+  S->cv_done.notify_all();
+}
+
+// set-up and Fig. 1 initialisation of one admitted request
+igm_status admit(igm_server_s *S, Request *r) {
+  igm_status st = int_gmres_setup(r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(),
+                                  &r->prm, S->stream, &r->h);
+  if (st) return st;
+  r->bytes = int_gmres_device_bytes(r->h);
+  CK(cudaMemcpyAsync(r->h->hs.bh, r->b.data(), sizeof(double) * r->n, cudaMemcpyHostToDevice,
+                     S->stream));
+  st = ir_init_host(r->h->solo, S->stream);
+  if (st) return st;
+  CK(cudaStreamSynchronize(S->stream));
+  // the host copies of the matrix are no longer needed
+  std::vector<int>().swap(r->rowptr);
+  std::vector<int>().swap(r->col);
+  std::vector<double>().swap(r->val);
+  return IGM_OK;
+}
+
+igm_status ensure_state(igm_server_s *S, int n) {
+  if (n <= S->state_cap) return IGM_OK;
+  if (S->d_state) cudaFree(S->d_state);
+  if (S->h_state) cudaFreeHost(S->h_state);
+  S->state_cap = n * 2;
+  CK(cudaMalloc((void **)&S->d_state, sizeof(int4) * S->state_cap));
+  CK(cudaMallocHost((void **)&S->h_state, sizeof(int4) * S->state_cap));
+  return IGM_OK;
+}
+
+// one round over the active set; finished requests are finalised after it
+igm_status round(igm_server_s *S) {
+  if (S->dirty) {
+    delete S->batch;
+    S->batch = nullptr;
+    std::vector<igm_handle> hs;
+    for (Request *r : S->active) hs.push_back(r->h);
+    igm_status st = build_batch(hs, &S->batch);
+    if (st) return st;
+    S->dirty = false;
+  }
+  Batch *b = S->batch;
+  const BatchDev &B = b->bd;
+  cudaStream_t s = S->stream;
+  igm_status st = ensure_state(S, B.nsys);
+  if (st) return st;
+  // convergence test of Fig. 1 for everyone, then one inner solve
+  launch_resid(B, 0, s);
+  launch_norm(B, VEC_R, ACT_RHO, 1, s);
+  launch_gather_state(B, S->d_state, s);
+  CKL();
+  g_launches += 3;
+  CK(cudaMemcpyAsync(S->h_state, S->d_state, sizeof(int4) * B.nsys, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool any = false;
+  for (int i = 0; i < B.nsys; ++i) any |= S->h_state[i].x != 0;
+  if (any) {
+    launch_rhs(B, s);
+    enqueue_inner_host(b, s);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+  }
+  S->st.rounds++;
+  // finalise the systems that left the refinement loop
+  std::vector<Request *> keep;
+  for (int i = 0; i < B.nsys; ++i) {
+    Request *r = S->active[i];
+    if (S->h_state[i].x != 0) {
+      keep.push_back(r);
+      continue;
+    }
+    igm_status fs = ir_finish_host(r->h->solo, s);
+    if (!fs) {
+      r->x.resize(r->n);
+      cudaMemcpyAsync(r->x.data(), r->h->hs.xt, sizeof(double) * r->n, cudaMemcpyDeviceToHost, s);
+      fs = collect_host(r->h, &r->rep, s);
+    }
+    int_gmres_destroy(r->h);
+    r->h = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->used -= r->bytes;
+    }
+    finish(S, r, fs);
+    S->dirty = true;
+  }
+  S->active.swap(keep);
+  return IGM_OK;
+}
+
+void worker_main(igm_server_s *S) {
+  cudaSetDevice(S->dev);
+  cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  for (;;) {
+    // admission by memory budget, in arrival order
+    for (;;) {
+      Request *r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->stop) break;
+        if (S->queue.empty() && S->active.empty())
+          S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        if (S->stop || S->queue.empty()) break;
+        if (S->cfg.max_active > 0 && (int)S->active.size() >= S->cfg.max_active) break;
+        Request *q = S->queue.front();
+        long long need = handle_bytes_estimate(q->n, q->nnz, &q->prm);
+        if (!S->active.empty() && S->used + need > S->cfg.budget_bytes) break;
+        S->queue.pop_front();
+        S->used += need;
+        r = q;
+      }
+      long long est = handle_bytes_estimate(r->n, r->nnz, &r->prm);
+      igm_status st = admit(S, r);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->used += (st ? 0 : r->bytes) - est;
+        if (S->used > S->st.peak_bytes) S->st.peak_bytes = S->used;
+      }
+      if (st) {
+        if (r->h) int_gmres_destroy(r->h);
+        r->h = nullptr;
+        finish(S, r, st);
+        continue;
+      }
+      S->active.push_back(r);
+      S->dirty = true;
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (S->stop) break;
+    }
+    if (S->active.empty()) continue;
+    auto t0 = clk::now();
+    igm_status st = round(S);
+    S->st.busy_s += std::chrono::duration<double>(clk::now() - t0).count();
+    if (st) {  // a failed round fails every active request
+      for (Request *r : S->active) {
+        if (r->h) int_gmres_destroy(r->h);
+        r->h = nullptr;
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->used -= r->bytes;
+        }
+        finish(S, r, st);
+      }
+      S->active.clear();
+      S->dirty = true;
+    }
+  }
+  for (Request *r : S->active)
+    if (r->h) int_gmres_destroy(r->h);
+  S->active.clear();
+  delete S->batch;
+  S->batch = nullptr;
+  if (S->d_state) cudaFree(S->d_state);
+  if (S->h_state) cudaFreeHost(S->h_state);
+  cudaStreamDestroy(S->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+igm_status igm_server_create(const igm_server_config *cfg, igm_server *out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(IGM_EINVAL, "NULL argument");
+  if (cfg->budget_bytes <= 0 || cfg->m < 1 || cfg->m > IGM_MAX_M || cfg->max_active < 0 ||
+      (cfg->inner != 0 && cfg->inner != 1))
+    return fail(IGM_EINVAL, "bad server configuration");
+  igm_server_s *S = new igm_server_s();
+  S->cfg = *cfg;
+  cudaGetDevice(&S->dev);
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return IGM_OK;
+}
+
+igm_status igm_server_submit(igm_server S, int n, int nnz, const int *rowptr, const int *col,
+                             const double *val, const double *bhat, const igm_params *params,
+                             long long *id) {
+  g_err.clear();
+  if (!S || !rowptr || !bhat || !params || !id || n < 1 || nnz < 0 ||
+      (nnz > 0 && (!col || !val)))
+    return fail(IGM_EINVAL, "bad arguments");
+  if (params->m != S->cfg.m || params->inner != S->cfg.inner)
+    return fail(IGM_EINVAL, "params.m / inner must match the server");
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(IGM_EINVAL, "rowptr[0] / rowptr[n]");
+  if (handle_bytes_estimate(n, nnz, params) > S->cfg.budget_bytes)
+    return fail(IGM_EOOM, "request needs more than the whole budget");
+  Request *r = new Request();
+  r->n = n;
+  r->nnz = nnz;
+  r->rowptr.assign(rowptr, rowptr + n + 1);
+  r->col.assign(col, col + nnz);
+  r->val.assign(val, val + nnz);
+  r->b.assign(bhat, bhat + n);
+  r->prm = *params;
+  r->t_submit = clk::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    S->all[r->id] = r;
+    S->queue.push_back(r);
+    S->st.submitted++;
+  }
+  S->cv_work.notify_one();
+  *id = r->id;
+  return IGM_OK;
+}
+
+igm_status igm_server_poll(igm_server S, long long id, int wait_ms, double *xhat,
+                           igm_report *rep, double *lat_s, int *done) {
+  g_err.clear();
+  if (!S || !done) return fail(IGM_EINVAL, "NULL argument");
+  *done = 0;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return fail(IGM_EINVAL, "unknown request %lld", id);
+  Request *r = it->second;
+  if (!r->done && wait_ms != 0) {
+    if (wait_ms < 0) S->cv_done.wait(lk, [&] { return r->done; });
+    else S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return r->done; });
+  }
+  if (!r->done) return IGM_OK;
+  *done = 1;
+  if (xhat && !r->x.empty()) memcpy(xhat, r->x.data(), sizeof(double) * r->n);
+  if (rep) *rep = r->rep;
+  if (lat_s) *lat_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  igm_status st = r->status;
+  S->all.erase(it);
+  delete r;
+  if (st) return fail(st, "request %lld: status %d", id, (int)st);
+  return IGM_OK;
+}
+
+igm_status igm_server_get_stats(igm_server S, igm_server_stats *st) {
+  if (!S || !st) return fail(IGM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  *st = S->st;
+  return IGM_OK;
+}
+
+void igm_server_destroy(igm_server S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto &kv : S->all) delete kv.second;
+  delete S;
+}
+
+}  // extern "C"

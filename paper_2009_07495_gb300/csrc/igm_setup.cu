@@ -60,40 +60,49 @@ __global__ void s_cast(long long nnz, const double *a, i64 *abar, unsigned *err)
   }
 }
 
-// Level of every row of the strict lower (lower = 1) or strict upper part:
-// level(i) = 1 + max level of the rows row i reads (0 if none).  Rows are
-// visited in dependency order (natural order for L, reverse for U); CTAs
-// take 256-row chunks by ticket, each row waits (bounded) on the flags of
-// its dependencies.
+// Chunk-local level of every row of the strict lower (lower = 1) or strict
+// upper part.  Positions p = 0..n-1 run in dependency order (row p for L,
+// row n-1-p for U) and are cut into chunks of R positions; the local level of
+// a row is 1 + the largest local level of the rows it reads inside its own
+// chunk (0 if none): rows of earlier chunks are not counted, they are waited
+// for at solve time.  CTAs take 256-position chunks of work by ticket; each
+// row waits (bounded) on the flags of its same-chunk dependencies.
 __global__ void s_levels(int n, const int *rowptr, const int *col, const int *diagpos,
-                         int lower, int *level, int *flag, int epoch, unsigned *ticket,
-                         int *maxlev, unsigned *err) {
+                         int lower, int R, int *level, int *flag, int epoch, unsigned *ticket,
+                         int *chunkmax, unsigned *err) {
   __shared__ int s_t;
   if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);
   __syncthreads();
   int p = s_t * blockDim.x + threadIdx.x;
   if (p >= n) return;
   int i = lower ? p : n - 1 - p;
+  int c = p / R;
+  int first = c * R;  // first position of the chunk
   int k0 = lower ? rowptr[i] : diagpos[i] + 1;
   int k1 = lower ? diagpos[i] : rowptr[i + 1];
   int lv = 0;
   for (int k = k0; k < k1; ++k) {
     int j = col[k];
+    int pj = lower ? j : n - 1 - j;
+    if (pj < first) continue;
     wait_flag(flag + j, epoch, err);
     lv = max(lv, __ldcg(level + j) + 1);
   }
   level[i] = lv;
   st_release(flag + i, epoch);
-  atomicMax(maxlev, lv);
+  atomicMax(chunkmax + c, lv);
 }
 
-__global__ void s_hist(int n, const int *level, int *cnt) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    atomicAdd(cnt + level[i], 1);
+// group key of a row: first group of its chunk + its local level
+__global__ void s_hist(int n, int lower, int R, const int *level, const int *levb, int *cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int p = lower ? i : n - 1 - i;
+    atomicAdd(cnt + levb[p / R] + level[i], 1);
+  }
 }
 
-// exclusive scan of cnt[0..L) in place, one CTA (L up to a few million)
-__global__ void s_scan(int L, int *cnt) {
+// exclusive scan of cnt[0..L) into out[0..L] (out[L] = total), one CTA
+__global__ void s_scan(int L, const int *cnt, int *out) {
   __shared__ int s[1024];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -109,18 +118,22 @@ __global__ void s_scan(int L, int *cnt) {
       s[threadIdx.x] += t;
       __syncthreads();
     }
-    if (idx < L) cnt[idx] = carry + s[threadIdx.x] - v;
+    if (idx < L) out[idx] = carry + s[threadIdx.x] - v;
     __syncthreads();
     if (threadIdx.x == 1023) carry += s[1023];
     __syncthreads();
   }
+  if (threadIdx.x == 0) out[L] = carry;
 }
 
-// scatter rows into level order (order inside a level is arbitrary and
-// does not affect results: rows of one level are independent)
-__global__ void s_scatter(int n, const int *level, int *cursor, int *order) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    order[atomicAdd(cursor + level[i], 1)] = i;
+// scatter rows into (chunk, level) groups; the order inside a group is
+// arbitrary and does not affect results (rows of one group are independent)
+__global__ void s_scatter(int n, int lower, int R, const int *level, const int *levb,
+                          int *cursor, int *order) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int p = lower ? i : n - 1 - i;
+    order[atomicAdd(cursor + levb[p / R] + level[i], 1)] = i;
+  }
 }
 
 // eq. (ilu): ILU(0), IKJ row variant on the pattern of A (Saad, Alg. 10.4):
@@ -209,16 +222,17 @@ void launch_cast(long long nnz, const double *a, i64 *abar, unsigned *err, cudaS
   s_cast<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, a, abar, err);
 }
 void launch_levels(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
-                   int *level, int *flag, int epoch, unsigned *ticket, int *maxlev,
+                   int R, int *level, int *flag, int epoch, unsigned *ticket, int *chunkmax,
                    unsigned *err, cudaStream_t st) {
-  s_levels<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, diagpos, lower, level, flag,
-                                             epoch, ticket, maxlev, err);
+  s_levels<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, diagpos, lower, R, level, flag,
+                                             epoch, ticket, chunkmax, err);
 }
-void launch_level_order(int n, int L, const int *level, int *cnt, int *order,
-                        cudaStream_t st) {
-  s_hist<<<grid_for(n, 256), 256, 0, st>>>(n, level, cnt);
-  s_scan<<<1, 1024, 0, st>>>(L, cnt);
-  s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, level, cnt, order);
+void launch_level_order(int n, int lower, int R, int L, const int *level, const int *levb,
+                        int *cnt, int *lptr, int *order, cudaStream_t st) {
+  s_hist<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt);
+  s_scan<<<1, 1024, 0, st>>>(L, cnt, lptr);
+  cudaMemcpyAsync(cnt, lptr, sizeof(int) * L, cudaMemcpyDeviceToDevice, st);
+  s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt, order);
 }
 void launch_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
                  const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,

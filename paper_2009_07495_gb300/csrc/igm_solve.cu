@@ -267,32 +267,61 @@ __global__ void k_trsv_fp(BatchDev B, int lower) {
   }
 }
 
-// line 5': integer substitutions, w -> yv (lower) and yv -> w (upper)
-__global__ void k_trsv_int(BatchDev B, int lower) {
-  int ti = take_ticket(&B.ticket[lower ? 2 : 3]);
-  Tile tl = B.tiles[ti];
-  const SysDev *s = B.sys[tl.sys];
+// line 5' by chunks: each CTA takes (by ticket, in dependency order) one
+// chunk of consecutive rows and walks its local levels, separated by CTA
+// barriers; a dependency inside the chunk was computed at an earlier local
+// level of the same CTA, a dependency in an earlier chunk is waited for on
+// that chunk's progress word, which the chunk publishes once per level.
+// Integer arithmetic as k_trsv_int (exact int128 numerator, truncating
+// division).
+#define IGM_TRSV_BLOCK 256
+__global__ void __launch_bounds__(IGM_TRSV_BLOCK) k_trsv_chunk(BatchDev B, int lower) {
+  __shared__ int s_t;
+  if (threadIdx.x == 0) s_t = (int)atomicAdd(&B.ticket[lower ? 2 : 3], 1u);
+  __syncthreads();
+  Tile ct = B.ctiles[s_t];
+  const SysDev *s = B.sys[ct.sys];
   SysScal *sc = s->sc;
   if (!g_step(sc) || !s->p.precond) return;
+  const int c = ct.row0, n = s->n, R = s->chunk;
+  const int first = c * R;
   const int *ord = lower ? s->lorder : s->uorder;
-  int *flag = lower ? s->lflag : s->uflag;
+  const int *lptr = lower ? s->llptr : s->ulptr;
+  const int *levb = lower ? s->llevb : s->ulevb;
+  const int *lev = lower ? s->llev : s->ulev;
+  u64 *prog = lower ? s->lprog : s->uprog;
+  const i64 *dg = lower ? s->ldiag : s->udiag;
   const i64 *in = lower ? s->w : s->yv;
   i64 *out = lower ? s->yv : s->w;
-  int ep = sc->seq;
+  const u64 ep = (u64)(unsigned)sc->seq << 32;
+  const int g0 = levb[c], g1 = levb[c + 1];
   unsigned ev = 0;
-  TILE_LOOP(p) {
-    int i = ord[p];
-    i128 acc = in[i];
-    int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
-    int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      int j = s->col[k];
-      wait_flag(flag + j, ep, &sc->err);
-      acc -= (i128)mulw(s->fac[k], (i64)__ldcg((const long long *)out + j), ev);
+  for (int g = g0; g < g1; ++g) {
+    for (int p = lptr[g] + threadIdx.x; p < lptr[g + 1]; p += blockDim.x) {
+      int i = ord[p];
+      i128 acc = in[i];
+      int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
+      int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
+      for (int k = k0; k < k1; ++k) {
+        int j = s->col[k];
+        int pj = lower ? j : n - 1 - j;
+        i64 yj;
+        if (pj >= first) {
+          yj = out[j];
+        } else {
+          wait_prog(prog + pj / R, ep | (u64)(lev[j] + 1), &sc->err);
+          yj = (i64)__ldcg((const long long *)out + j);
+        }
+        acc -= (i128)mulw(s->fac[k], yj, ev);
+      }
+      ev += out64(acc);
+      out[i] = divt(wrap(acc), dg[i], ev);
     }
-    ev += out64(acc);
-    out[i] = divt(wrap(acc), lower ? s->ldiag[i] : s->udiag[i], ev);
-    st_release(flag + i, ep);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release64(prog + c, ep | (u64)(g - g0 + 1));
+    }
   }
   flush_ev(ev, &sc->ev[IGM_EV_L5P]);
 }
@@ -348,154 +377,6 @@ __global__ void k_spmv(BatchDev B, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// lines 6-9, modified Gram-Schmidt, one pass per i: the line-8 update with
-// h_{i-1,j} (only h shifted) fused with the line-7 inner product with v_i
-// (only w shifted); the last CTA forms h_ij = sum >> (df - beta7).
-// ---------------------------------------------------------------------------
-__global__ void k_mgs(BatchDev B, int i, int j) {
-  Tile tl = B.tiles[blockIdx.x];
-  const SysDev *s = B.sys[tl.sys];
-  SysScal *sc = s->sc;
-  if (!g_step(sc) || j >= s->p.m) return;
-  const SysParams &P = s->p;
-  const int n = s->n, ld = s->ld, df = P.df;
-  const i64 *vi = s->V + (size_t)i * n;
-  const i64 *vp = s->V + (size_t)(i > 0 ? i - 1 : 0) * n;
-  i64 hs = i > 0 ? shr(s->H[(i - 1) + j * ld], P.b8) : 0;
-  unsigned ev7 = 0, ev8 = 0;
-  i128 acc = 0;
-  TILE_LOOP(l) {
-    i64 wl = s->w[l];
-    if (i > 0) {
-      i64 p = shr(mulw(hs, vp[l], ev8), df - P.b8);
-      i128 d = (i128)wl - (i128)p;
-      ev8 += out64(d);
-      wl = wrap(d);
-      s->w[l] = wl;
-    }
-    acc += (i128)mulw(shr(wl, P.b7), vi[l], ev7);
-  }
-  flush_ev(ev8, &sc->ev[IGM_EV_L8]);
-  acc = block_sum_i128(acc);
-  if (threadIdx.x == 0) store_part(B.part, blockIdx.x, acc);
-  if (last_tile(&sc->cnt[0], B.sys_ntiles[tl.sys])) {
-    if (threadIdx.x == 0) {
-      i128 tot = 0;
-      for (int t = 0; t < B.sys_ntiles[tl.sys]; ++t) tot += load_part(B.part, tl.first + t);
-      ev7 += out64(tot);
-      s->H[i + j * ld] = shr(wrap(tot), df - P.b7);
-    }
-  }
-  flush_ev(ev7, &sc->ev[IGM_EV_L7]);
-}
-
-// Givens rotation update of column j (lines 12-19), one thread
-__device__ void givens_col(const SysDev *s, SysScal *sc, int j, i64 hj1) {
-  const SysParams &P = s->p;
-  const int ld = s->ld, df = P.df;
-  i64 *H = s->H;
-  unsigned e13 = 0, e15 = 0, e16 = 0, e17 = 0;
-  bool zero = shr(hj1, P.b11b) == 0;
-  for (int i = 0; i < j; ++i) {
-    i64 a = shr(H[i + j * ld], P.b13), b = shr(H[i + 1 + j * ld], P.b13);
-    i64 p1 = mulw(s->cs[i], a, e13), p2 = mulw(s->sn[i], b, e13);
-    i128 t1 = (i128)p1 + (i128)p2;
-    e13 += out64(t1);
-    i64 p3 = mulw(negw(s->sn[i], e13), a, e13), p4 = mulw(s->cs[i], b, e13);
-    i128 t2 = (i128)p3 + (i128)p4;
-    e13 += out64(t2);
-    H[i + j * ld] = shr(wrap(t1), df - P.b13);
-    H[i + 1 + j * ld] = shr(wrap(t2), df - P.b13);
-  }
-  i64 hjj = H[j + j * ld], hn = H[j + 1 + j * ld];
-  i64 a15 = shr(hjj, P.b15), b15 = shr(hn, P.b15);
-  i128 s15 = (i128)mulw(a15, a15, e15) + (i128)mulw(b15, b15, e15);
-  e15 += out64(s15);
-  i64 tmp = fx_sqrt(wrap(s15), 2 * df - 2 * P.b15, df, e15);
-  if (shr(tmp, P.b16b) == 0) {
-    sc->early = 1;  // singular column: the solve uses j columns
-  } else {
-    i64 c = fx_div(hjj, tmp, P.b16a, P.b16b, df, e16);
-    i64 sn = fx_div(hn, tmp, P.b16a, P.b16b, df, e16);
-    s->cs[j] = c;
-    s->sn[j] = sn;
-    i64 gj = s->g[j];
-    s->g[j + 1] = shr(mulw(negw(sn, e17), gj, e17), df);
-    s->g[j] = shr(mulw(c, gj, e17), df);
-    H[j + j * ld] = tmp;
-    H[j + 1 + j * ld] = 0;
-    sc->jeff = j + 1;
-    if (zero) sc->early = 1;
-  }
-  if (e13) atomicAdd(&sc->ev[IGM_EV_L13], (u64)e13);
-  if (e15) atomicAdd(&sc->ev[IGM_EV_L15], (u64)e15);
-  if (e16) atomicAdd(&sc->ev[IGM_EV_L16], (u64)e16);
-  if (e17) atomicAdd(&sc->ev[IGM_EV_L17], (u64)e17);
-}
-
-// last MGS pass (line 8 with h_jj) fused with the line-10 norm; the last
-// CTA forms h_{j+1,j} and runs lines 12-19 for column j
-__global__ void k_mgs_last(BatchDev B, int j) {
-  Tile tl = B.tiles[blockIdx.x];
-  const SysDev *s = B.sys[tl.sys];
-  SysScal *sc = s->sc;
-  if (!g_step(sc) || j >= s->p.m) return;
-  const SysParams &P = s->p;
-  const int n = s->n, ld = s->ld, df = P.df;
-  const i64 *vp = s->V + (size_t)j * n;
-  i64 hs = shr(s->H[j + j * ld], P.b8);
-  unsigned ev10 = 0, ev8 = 0;
-  i128 acc = 0;
-  TILE_LOOP(l) {
-    i64 wl = s->w[l];
-    i64 p = shr(mulw(hs, vp[l], ev8), df - P.b8);
-    i128 d = (i128)wl - (i128)p;
-    ev8 += out64(d);
-    wl = wrap(d);
-    s->w[l] = wl;
-    i64 a = shr(wl, P.b10);
-    acc += (i128)mulw(a, a, ev10);
-  }
-  flush_ev(ev8, &sc->ev[IGM_EV_L8]);
-  acc = block_sum_i128(acc);
-  if (threadIdx.x == 0) store_part(B.part, blockIdx.x, acc);
-  if (last_tile(&sc->cnt[0], B.sys_ntiles[tl.sys])) {
-    if (threadIdx.x == 0) {
-      i128 tot = 0;
-      for (int t = 0; t < B.sys_ntiles[tl.sys]; ++t) tot += load_part(B.part, tl.first + t);
-      ev10 += out64(tot);
-      i64 hj1 = fx_sqrt(wrap(tot), 2 * df - 2 * P.b10, df, ev10);
-      s->H[j + 1 + j * ld] = hj1;
-      sc->hnext = hj1;
-      // line 11 comes before lines 12-19 in Fig. 2: it runs unless its own
-      // divisor is zero, whatever line 16 finds
-      sc->normj = shr(hj1, P.b11b) == 0 ? -1 : j;
-      givens_col(s, sc, j, hj1);
-    }
-  }
-  flush_ev(ev10, &sc->ev[IGM_EV_L10]);
-}
-
-// line 11: v_{j+1} = w / h_{j+1,j} (Sec. V-B division), unless breakdown
-__global__ void k_normalize(BatchDev B, int j) {
-  Tile tl = B.tiles[blockIdx.x];
-  const SysDev *s = B.sys[tl.sys];
-  SysScal *sc = s->sc;
-  if (!g_cyc(sc) || sc->normj != j || j >= s->p.m) return;
-  const SysParams &P = s->p;
-  i64 hn = sc->hnext;
-  i64 *vn = s->V + (size_t)(j + 1) * s->n;
-  unsigned ev = 0, evr = 0;
-  TILE_LOOP(l) {
-    i64 q = fx_div(s->w[l], hn, P.b11a, P.b11b, P.df, ev);
-    evr += (q < INT32_MIN || q > INT32_MAX);
-    vn[l] = q;
-  }
-  flush_ev(ev, &sc->ev[IGM_EV_L11]);
-  flush_ev(evr, &sc->ev[IGM_EV_VRANGE]);
-}
-
-// ---------------------------------------------------------------------------
 // lines 21-22: y = ||r0|| H^-1 g in FP64 (one thread per system)
 // ---------------------------------------------------------------------------
 __global__ void k_backsub(BatchDev B) {
@@ -537,6 +418,14 @@ __global__ void k_update(BatchDev B) {
   }
 }
 
+// per-system {active, status, error bits, refinements} for the host
+__global__ void k_gather_state(BatchDev B, int4 *out) {
+  int si = blockIdx.x * blockDim.x + threadIdx.x;
+  if (si >= B.nsys) return;
+  const SysScal *sc = B.sys[si]->sc;
+  out[si] = make_int4(sc->active, sc->status, (int)sc->err, sc->refinements);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -569,8 +458,8 @@ void launch_arm(const BatchDev &B, cudaStream_t st) {
 void launch_trsv_fp(const BatchDev &B, int lower, cudaStream_t st) {
   k_trsv_fp<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, lower);
 }
-void launch_trsv_int(const BatchDev &B, int lower, cudaStream_t st) {
-  k_trsv_int<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, lower);
+void launch_trsv_chunk(const BatchDev &B, int lower, cudaStream_t st) {
+  if (B.nctiles > 0) k_trsv_chunk<<<B.nctiles, IGM_TRSV_BLOCK, 0, st>>>(B, lower);
 }
 void launch_cast_v1(const BatchDev &B, cudaStream_t st) {
   k_cast_v1<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);
@@ -578,17 +467,11 @@ void launch_cast_v1(const BatchDev &B, cudaStream_t st) {
 void launch_spmv(const BatchDev &B, int j, cudaStream_t st) {
   k_spmv<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
 }
-void launch_mgs(const BatchDev &B, int i, int j, cudaStream_t st) {
-  k_mgs<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, i, j);
-}
-void launch_mgs_last(const BatchDev &B, int j, cudaStream_t st) {
-  k_mgs_last<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
-}
-void launch_normalize(const BatchDev &B, int j, cudaStream_t st) {
-  k_normalize<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
-}
 void launch_backsub(const BatchDev &B, cudaStream_t st) {
   k_backsub<<<nb_sys(B), 128, 0, st>>>(B);
+}
+void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st) {
+  k_gather_state<<<nb_sys(B), 128, 0, st>>>(B, out);
 }
 void launch_update(const BatchDev &B, cudaStream_t st) {
   k_update<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);

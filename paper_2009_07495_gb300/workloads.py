@@ -208,26 +208,32 @@ def banded_random(n: int, rng: np.random.Generator, bw: int = 64,
     off-diagonals, diagonal = (sum of |off-diagonals|) * U(1.05, 2.0),
     b = A x_true with x_true ~ N(0, 1)."""
     k = rng.integers(nnz_lo, nnz_hi + 1, n)          # non-zeros per row
-    rows, cols = [], []
-    # candidate offsets -bw..bw without 0; draw k-1 distinct per row
     cand = np.concatenate([np.arange(-bw, 0), np.arange(1, bw + 1)])
-    keys = rng.random((n, cand.size))
-    order = np.argsort(keys, axis=1)
-    for i in range(n):
-        sel = cand[order[i]]
-        sel = sel[(i + sel >= 0) & (i + sel < n)][: k[i] - 1]
-        cols.append(np.sort(np.concatenate([sel + i, [i]])))
-    counts = np.array([len(c) for c in cols], dtype=np.int64)
+    rows_out, cols_out = [], []
+    step = max(1, (1 << 22) // cand.size)             # bound the temporary arrays
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        i = np.arange(r0, r1)
+        order = np.argsort(rng.random((r1 - r0, cand.size)), axis=1)
+        off = cand[order]
+        valid = (i[:, None] + off >= 0) & (i[:, None] + off < n)
+        rank = np.cumsum(valid, axis=1) - 1
+        keep = valid & (rank < (k[r0:r1] - 1)[:, None])
+        rr = np.repeat(i, keep.sum(axis=1))
+        rows_out += [rr, i]
+        cols_out += [(i[:, None] + off)[keep], i]
+    rix = np.concatenate(rows_out)
+    col = np.concatenate(cols_out)
+    o = np.lexsort((col, rix))
+    rix, col = rix[o], col[o].astype(np.int32)
+    counts = np.bincount(rix, minlength=n)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
-    col = np.concatenate(cols).astype(np.int32)
     val = rng.standard_normal(col.size)
-    rix = np.repeat(np.arange(n), counts)
     isd = col == rix
     offsum = np.bincount(rix, weights=np.where(isd, 0.0, np.abs(val)), minlength=n)
     dscale = rng.uniform(1.05, 2.0, n)
-    dval = np.maximum(offsum, 1.0) * dscale
-    val[isd] = dval
+    val[isd] = np.maximum(offsum, 1.0) * dscale
     s = System(n, rowptr.astype(np.int32), col, val, np.zeros(n), f"banded_{n}")
     xt = rng.standard_normal(n)
     s.b = s.matvec(xt)

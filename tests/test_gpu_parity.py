@@ -187,3 +187,75 @@ def test_batched_equals_solo(L, orc):
         np.testing.assert_array_equal(reps[k]["relres_hist"], ro.relres_hist)
     for sv in xs:
         sv.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fp64_gmres_comparison_solver(L, orc, prec):
+    """The FP64 GMRES(m) comparison solver (params.inner = 1) converges like
+    the oracle's FP64 GMRES: same refinement count, relres < 1e-10 and the
+    same solution to rounding (its sums are ordered differently)."""
+    s = W.small_cd3d(12, seed=52) if prec else W.config0()
+    P = L.params_default(prec, 30)
+    P.inner = 1
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P), inner=1)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert rep["status"] == "ok" and rep["relres"] < 1e-10
+    assert abs(rep["refinements"] - ro.refinements) <= 1
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    solver.close()
+
+
+def test_server_results_equal_solo(L, orc):
+    """Continuous batching: requests submitted while others are running are
+    admitted into later rounds; every served result is bit-identical to the
+    same system solved alone (and to the oracle)."""
+    import time
+    rng = np.random.default_rng(60)
+    systems = [W.small_cd3d(int(N), seed=int(60 + N)) for N in (8, 11, 6, 13, 9)]
+    systems += [W.small_cd2d(int(N), seed=int(70 + N)) for N in (20, 35)]
+    P_ilu, P_none = L.params_default(1, 20), L.params_default(0, 20)
+    params = [P_ilu] * 5 + [P_none] * 2
+    srv = L.Server(budget_bytes=1 << 30, m=20)
+    ids = []
+    for k, (s, P) in enumerate(zip(systems, params)):
+        ids.append(srv.submit(s.rowptr, s.col, s.val, s.b, P))
+        if k == 2:
+            time.sleep(0.05)   # later arrivals join while the first run
+    outs = [srv.poll(i, wait_ms=60000) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(systems) and st["failed"] == 0
+    for (done, x, rep, lat), s, P in zip(outs, systems, params):
+        assert done and rep["status"] == "ok" and rep["relres"] < 1e-10
+        solo = L.Solver(s.rowptr, s.col, s.val, P)
+        xs, rs = solo.ir_solve(s.b)
+        solo.close()
+        np.testing.assert_array_equal(x, xs)
+        assert rep["refinements"] == rs["refinements"]
+        xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+        np.testing.assert_array_equal(x, xo)
+
+
+def test_server_budget_admission(L):
+    """With a budget that fits about one system at a time, requests are served
+    one after another and all complete; a request larger than the whole
+    budget is refused at submission."""
+    systems = [W.small_cd2d(24, seed=80 + k) for k in range(4)]
+    P = L.params_default(0, 10)
+    one = 0
+    sv = L.Solver(systems[0].rowptr, systems[0].col, systems[0].val, P)
+    one = sv.device_bytes()
+    sv.close()
+    srv = L.Server(budget_bytes=int(one * 1.5), m=10)
+    ids = [srv.submit(s.rowptr, s.col, s.val, s.b, P) for s in systems]
+    res = [srv.poll(i, wait_ms=60000) for i in ids]
+    st = srv.stats()
+    assert all(r[0] and r[2]["status"] == "ok" for r in res)
+    assert st["peak_bytes"] <= int(one * 1.5)
+    big = W.small_cd2d(120, seed=90)
+    with pytest.raises(L.IGMError) as e:
+        srv.submit(big.rowptr, big.col, big.val, big.b, P)
+    assert e.value.name == "eoom"
+    srv.close()
