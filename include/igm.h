@@ -154,6 +154,17 @@ igm_status int_gmres_get_state(igm_handle h, long long *V, long long *H,
                                long long *cs, long long *sn, long long *g,
                                int *jeff, double *nu);
 
+/* The reproducible FP64 2-norm used by the test of Fig. 1: with
+ * e = ilogb(max|x_i|), each (x_i 2^-e)^2 is formed exactly (product plus its
+ * FMA error), both parts are truncated to multiples of 2^-96 and summed
+ * exactly in integers, the total is rounded once to double, scaled back and
+ * square-rooted.  The result does not depend on the order of the elements or
+ * of the reduction, and is within one ulp of the exact norm.  x: n doubles
+ * (device or host); out: one double (device or host).  Device scratch is
+ * taken from a library-owned workspace, allocated on the first call for the
+ * largest n seen.  Errors: IGM_EINVAL, IGM_EOOM, IGM_ECUDA. */
+igm_status igm_norm2(const double *x, int n, double *out, void *stream);
+
 /* Kernels that igm_time_kernels can time (one launch each, on the handle's
  * current state, in the launch configuration of the solver). */
 enum {

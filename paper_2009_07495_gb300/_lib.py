@@ -94,6 +94,7 @@ def _declare(lib):
         "int_gmres_device_bytes": (C.c_longlong, [_VP]),
         "igm_time_kernels": (_I, [_VP, _I, C.POINTER(C.c_double), _VP]),
         "igm_kernel_launches": (C.c_longlong, []),
+        "igm_norm2": (_I, [_VP, _I, _VP, _VP]),
         "int_gmres_destroy": (None, [_VP]),
         "igm_server_create": (_I, [C.POINTER(ServerConfig), C.POINTER(_VP)]),
         "igm_server_submit": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, C.POINTER(Params),
@@ -331,6 +332,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def norm2(x, stream=None) -> float:
+    """The reproducible 2-norm of Fig. 1's test (igm_norm2)."""
+    b = _Buf(x, np.float64)
+    out = C.c_double(0)
+    _check(load().igm_norm2(b.ptr, b.len, C.addressof(out), _stream_ptr(stream, b)))
+    return out.value
 
 
 def version() -> str:

@@ -61,7 +61,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
     snt[s] = nt;
     sp[s] = h->d_sys;
     int cfirst = (int)ctiles.size();
-    for (int c = 0; c < h->hs.lnchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
+    for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
+    b->max_chunk = std::max(b->max_chunk, h->hs.chunk);
   }
   int CT = (int)ctiles.size();
   Tile *d_ctiles = nullptr;
@@ -114,21 +115,21 @@ namespace {
 void enqueue_inner(Batch *b, cudaStream_t st) {
   const BatchDev &B = b->bd;
   if (b->inner == 1) {
-    launch_fp64_inner(B, b->m, b->any_ilu, st);
+    launch_fp64_inner(B, b->m, b->any_ilu, b->max_chunk, st);
     return;
   }
-  if (b->any_ilu) {
-    launch_trsv_fp(B, 1, st);
-    launch_trsv_fp(B, 0, st);
+  if (b->any_ilu) {  // line 1'
+    launch_trsv_lv(B, 1, 1, 0, b->max_chunk, st);
+    launch_trsv_lv(B, 1, 0, 0, b->max_chunk, st);
   }
   launch_max(B, VEC_R, 2, st);
   launch_norm(B, VEC_R, ACT_NU, 2, st);
   launch_cast_v1(B, st);
   for (int j = 0; j < b->m; ++j) {
     launch_spmv(B, j, st);
-    if (b->any_ilu) {
-      launch_trsv_chunk(B, 1, st);
-      launch_trsv_chunk(B, 0, st);
+    if (b->any_ilu) {  // line 5'
+      launch_trsv_lv(B, 0, 1, 1, b->max_chunk, st);
+      launch_trsv_lv(B, 0, 0, 1, b->max_chunk, st);
     }
     launch_mgs_step(B, j, st);
   }
@@ -164,15 +165,25 @@ igm_status capture_graphs(Batch *b) {
   return IGM_OK;
 }
 
-// rows per substitution chunk: about one chunk per SM, a multiple of 1024
-int auto_chunk(int n) {
+// Rows per substitution chunk.  A multiple of the bandwidth of the
+// triangular factors makes every chunk depend on its predecessor only (for a
+// natural-order stencil: whole grid planes, so consecutive chunks' local
+// levels line up); at least 1024 rows; with a bandwidth too large for that
+// (fewer than 8 chunks), about one chunk per SM.
+int auto_chunk(int n, int bw) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long r = ((long long)n + sms - 1) / sms;
-  r = (r + 1023) / 1024 * 1024;
+  long long r;
+  if (bw >= 1 && (long long)bw * 8 <= n) {
+    r = bw;
+    while (r < 1024) r += bw;
+  } else {
+    r = ((long long)n + sms - 1) / sms;
+    r = (r + 1023) / 1024 * 1024;
+  }
   if (r < 1024) r = 1024;
-  if (r > (1 << 20)) r = 1 << 20;
+  if (r > (1 << 22)) r = 1 << 22;
   return (int)r;
 }
 
@@ -268,14 +279,10 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   h->prm = *params;
   const int m = params->m, ilu = params->precond;
   SysDev &d = h->hs;
-  int *rp, *cl, *dp, *lord = nullptr, *uord = nullptr, *lfl = nullptr, *ufl = nullptr;
-  int *llev = nullptr, *ulev = nullptr, *llptr = nullptr, *ulptr = nullptr;
-  int *llevb = nullptr, *ulevb = nullptr, *chmax = nullptr, *cnt = nullptr;
-  u64 *lprog = nullptr, *uprog = nullptr;
-  int R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n);
-  int nch = (n + R - 1) / R;
+  int *rp, *cl, *dp, *lfl = nullptr, *ufl = nullptr;
   double *ahat, *a, *dd, *f = nullptr, *b, *bh, *xt, *r, *t, *xk, *yfp;
   i64 *abar, *fac = nullptr, *ld = nullptr, *ud = nullptr, *w, *yv, *V, *H, *cs, *sn, *g;
+  int *bwd = nullptr;
   size_t nz = nnz > 0 ? nnz : 1;
   Arena &A = h->arena;
   A.want(&rp, n + 1);
@@ -290,20 +297,9 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     A.want(&fac, nz);
     A.want(&ld, n);
     A.want(&ud, n);
-    A.want(&lord, n);
-    A.want(&uord, n);
     A.want(&lfl, n);
     A.want(&ufl, n);
-    A.want(&llev, n);
-    A.want(&ulev, n);
-    A.want(&llptr, n + 1);
-    A.want(&ulptr, n + 1);
-    A.want(&llevb, nch + 1);
-    A.want(&ulevb, nch + 1);
-    A.want(&lprog, nch);
-    A.want(&uprog, nch);
-    A.want(&chmax, nch);
-    A.want(&cnt, n + 1);
+    A.want(&bwd, 4);
   }
   A.want(&b, n);
   A.want(&bh, n);
@@ -354,10 +350,17 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   }
   unsigned *err = h->d_err;
   launch_validate(n, nnz, rp, cl, dp, err, s);
+  unsigned herr = 0;
+  CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CKH(cudaStreamSynchronize(s));
+  if (herr) {  // a malformed CSR goes no further
+    igm_status e = err_status(herr);
+    int_gmres_destroy(h);
+    return e;
+  }
   launch_scale(n, rp, ahat, params->alpha_a, a, dd, err, s);
   launch_cast(nnz, a, abar, err, s);
   CKH(cudaGetLastError());
-  unsigned herr = 0;
   CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKH(cudaStreamSynchronize(s));
   if (herr) {
@@ -365,6 +368,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     int_gmres_destroy(h);
     return e;
   }
+  int R = 0, nch = 0, single = 0;
   if (ilu) {
     // a stored diagonal is required by ILU(0)
     std::vector<int> hdp(n);
@@ -374,35 +378,93 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
         int_gmres_destroy(h);
         return fail(IGM_EZERO_PIVOT, "row %d has no stored diagonal (ILU(0))", i);
       }
-    // chunked level schedules of the two factors (L: chunks from the top,
-    // U: from the bottom; levels local to each chunk)
+    // bandwidths and longest strict rows of the two triangles
+    int hbw[4] = {0, 0, 0, 0};
+    CKH(cudaMemsetAsync(bwd, 0, 4 * sizeof(int), s));
+    launch_bandwidth(n, rp, cl, bwd, s);
+    CKH(cudaMemcpyAsync(hbw, bwd, sizeof(hbw), cudaMemcpyDeviceToHost, s));
+    CKH(cudaStreamSynchronize(s));
+    const int bw = std::max(hbw[0], hbw[1]);
+    R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n, bw);
+    nch = (n + R - 1) / R;
+    single = R >= bw ? 1 : 0;
+    // the schedules and level-packed rows of L (t = 0) and U (t = 1)
+    const int fp = params->inner == 1;
+    Arena &A2 = h->arena2;
+    int *ord[2], *lptr[2], *levb[2], *lev[2], *need[2], *pcol[2], *chmax, *cnt;
+    i64 *pfac[2], *pdiag[2];
+    double *pfacd[2] = {nullptr, nullptr}, *pdiagd[2] = {nullptr, nullptr};
+    u64 *prog[2];
+    for (int tr = 0; tr < 2; ++tr) {
+      const size_t K = std::max(1, hbw[2 + tr]);
+      A2.want(&ord[tr], n);
+      A2.want(&lptr[tr], n + 1);
+      A2.want(&levb[tr], nch + 1);
+      A2.want(&lev[tr], n);
+      A2.want(&need[tr], n + 1);
+      A2.want(&pcol[tr], K * n);
+      A2.want(&pfac[tr], K * n);
+      A2.want(&pdiag[tr], n);
+      A2.want(&prog[tr], nch);
+      if (fp) {
+        A2.want(&pfacd[tr], K * n);
+        A2.want(&pdiagd[tr], n);
+      }
+    }
+    A2.want(&chmax, nch);
+    A2.want(&cnt, n + 1);
+    if (A2.commit() != cudaSuccess) {
+      cudaGetLastError();
+      size_t need2 = A2.total();
+      int_gmres_destroy(h);
+      return fail(IGM_EOOM, "device allocation of %zu bytes failed", need2);
+    }
+    // chunk-local levels and (chunk, level) orders of the two factors
     unsigned *tick = (unsigned *)(h->d_err + 1);
-    int *ords[2] = {lord, uord}, *flg[2] = {lfl, ufl}, *levs[2] = {llev, ulev};
-    int *lptrs[2] = {llptr, ulptr}, *levbs[2] = {llevb, ulevb};
+    int *flg[2] = {lfl, ufl};
     std::vector<int> hmax(nch), hlevb(nch + 1);
-    for (int lower = 1; lower >= 0; --lower) {
-      int f = 1 - lower;
-      CKH(cudaMemsetAsync(flg[f], 0, sizeof(int) * n, s));
+    for (int tr = 0; tr < 2; ++tr) {
+      const int lower = tr == 0;
+      CKH(cudaMemsetAsync(flg[tr], 0, sizeof(int) * n, s));
       CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
       CKH(cudaMemsetAsync(chmax, 0, sizeof(int) * nch, s));
-      launch_levels(n, rp, cl, dp, lower, R, levs[f], flg[f], 1, tick, chmax, err, s);
+      launch_levels(n, rp, cl, dp, lower, R, lev[tr], flg[tr], 1, tick, chmax, err, s);
       CKH(cudaMemcpyAsync(hmax.data(), chmax, sizeof(int) * nch, cudaMemcpyDeviceToHost, s));
       CKH(cudaStreamSynchronize(s));
       hlevb[0] = 0;
       for (int c = 0; c < nch; ++c) hlevb[c + 1] = hlevb[c] + hmax[c] + 1;
-      int L = hlevb[nch];
-      CKH(cudaMemcpyAsync(levbs[f], hlevb.data(), sizeof(int) * (nch + 1),
+      const int L = hlevb[nch];
+      CKH(cudaMemcpyAsync(levb[tr], hlevb.data(), sizeof(int) * (nch + 1),
                           cudaMemcpyHostToDevice, s));
       CKH(cudaMemsetAsync(cnt, 0, sizeof(int) * (L + 1), s));
-      launch_level_order(n, lower, R, L, levs[f], levbs[f], cnt, lptrs[f], ords[f], s);
+      launch_level_order(n, lower, R, L, lev[tr], levb[tr], cnt, lptr[tr], ord[tr], s);
+      CKH(cudaMemsetAsync(need[tr], 0, sizeof(int) * (L + 1), s));
+      launch_need(n, rp, cl, dp, lower, R, ord[tr], levb[tr], lev[tr], need[tr], s);
+      CKH(cudaMemsetAsync(prog[tr], 0, sizeof(u64) * nch, s));
       CKH(cudaStreamSynchronize(s));
+      Tri &T = d.tri[tr];
+      T.ord = ord[tr];
+      T.lptr = lptr[tr];
+      T.levb = levb[tr];
+      T.lev = lev[tr];
+      T.need = need[tr];
+      T.pcol = pcol[tr];
+      T.pfac = pfac[tr];
+      T.pdiag = pdiag[tr];
+      T.pfacd = pfacd[tr];
+      T.pdiagd = tr == 1 ? pdiagd[tr] : nullptr;
+      T.prog = prog[tr];
+      T.nchunk = nch;
+      T.K = hbw[2 + tr];
     }
-    CKH(cudaMemsetAsync(lprog, 0, sizeof(u64) * nch, s));
-    CKH(cudaMemsetAsync(uprog, 0, sizeof(u64) * nch, s));
+    // eq. (ilu) on the L schedule (epoch 2), then the integer factors
     CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
     CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
-    launch_ilu0(n, rp, cl, dp, lord, f, lfl, 2, tick, err, s);
+    launch_ilu0_lv(n, rp, cl, dp, d.tri[0], R, single, f, tick, 2, err, s);
     launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
+    for (int tr = 0; tr < 2; ++tr)
+      launch_pack(n, rp, cl, dp, tr == 0, d.tri[tr].K, ord[tr], fac, ld, ud, f, pcol[tr], pfac[tr],
+                  pdiag[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
     CKH(cudaGetLastError());
     CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));
@@ -430,18 +492,8 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.fac = fac;
   d.ldiag = ld;
   d.udiag = ud;
-  d.lorder = lord;
-  d.uorder = uord;
-  d.llptr = llptr;
-  d.ulptr = ulptr;
-  d.llevb = llevb;
-  d.ulevb = ulevb;
   d.chunk = R;
-  d.lnchunk = d.unchunk = ilu ? nch : 0;
-  d.llev = llev;
-  d.ulev = ulev;
-  d.lprog = lprog;
-  d.uprog = uprog;
+  d.single_pred = single;
   d.lflag = lfl;
   d.uflag = ufl;
   d.b = b;
@@ -493,10 +545,13 @@ void int_gmres_destroy(igm_handle h) {
   }
   delete h->solo;
   h->arena.release();
+  h->arena2.release();
   delete h;
 }
 
-long long int_gmres_device_bytes(igm_handle h) { return h ? (long long)h->arena.size : 0; }
+long long int_gmres_device_bytes(igm_handle h) {
+  return h ? (long long)(h->arena.size + h->arena2.size) : 0;
+}
 
 }  // extern "C"
 
@@ -677,6 +732,56 @@ igm_status int_gmres_get_state(igm_handle h, long long *V, long long *H, long lo
 
 long long igm_kernel_launches(void) { return g_launches.load(); }
 
+igm_status igm_norm2(const double *x, int n, double *out, void *stream) {
+  g_err.clear();
+  if (!x || !out || n < 0) return fail(IGM_EINVAL, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  static std::mutex mu;
+  static long long *ws = nullptr;
+  static double *buf = nullptr;  // [0] max, [1] input staging of size n, ...
+  static long long ws_words = 0, buf_len = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  long long need_ws = 2LL * norm2_grid(n) + 2, need_buf = 2 + (long long)n;
+  if (need_ws > ws_words) {
+    if (ws) cudaFree(ws);
+    ws = nullptr;
+    if (cudaMalloc((void **)&ws, sizeof(long long) * need_ws) != cudaSuccess) {
+      cudaGetLastError();
+      ws_words = 0;
+      return fail(IGM_EOOM, "norm workspace");
+    }
+    CK(cudaMemset(ws, 0, sizeof(long long) * need_ws));
+    ws_words = need_ws;
+  }
+  if (need_buf > buf_len) {
+    if (buf) cudaFree(buf);
+    buf = nullptr;
+    if (cudaMalloc((void **)&buf, sizeof(double) * need_buf) != cudaSuccess) {
+      cudaGetLastError();
+      buf_len = 0;
+      return fail(IGM_EOOM, "norm workspace");
+    }
+    buf_len = need_buf;
+  }
+  // the counter words sit right after the partials of this call's grid
+  const double *xd = x;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, x) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
+      pa.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();
+    if (n > 0) CK(cudaMemcpyAsync(buf + 2, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    xd = buf + 2;
+  }
+  long long g = norm2_grid(n);
+  CK(cudaMemsetAsync(ws + 2 * g, 0, 2 * sizeof(long long), s));
+  launch_norm2(xd, n, ws, buf, buf + 1, s);
+  CKL();
+  g_launches += 2;
+  CK(cudaMemcpyAsync(out, buf + 1, sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return IGM_OK;
+}
+
 igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
   g_err.clear();
   if (!h || !ms || reps < 1) return fail(IGM_EINVAL, "bad arguments");
@@ -705,12 +810,12 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
     float tot = 0.f;
     for (int r = 0; r < reps; ++r) {
       if (k == IGM_K_TRSV_L || k == IGM_K_TRSV_U) launch_spmv(B, m / 2, s);  // arms flags
-      if (k == IGM_K_TRSV_U) launch_trsv_chunk(B, 1, s);
+      if (k == IGM_K_TRSV_U) launch_trsv_lv(B, 0, 1, 1, b->max_chunk, s);
       CK(cudaEventRecord(e0, s));
       switch (k) {
         case IGM_K_SPMV: launch_spmv(B, m / 2, s); break;
-        case IGM_K_TRSV_L: launch_trsv_chunk(B, 1, s); break;
-        case IGM_K_TRSV_U: launch_trsv_chunk(B, 0, s); break;
+        case IGM_K_TRSV_L: launch_trsv_lv(B, 0, 1, 1, b->max_chunk, s); break;
+        case IGM_K_TRSV_U: launch_trsv_lv(B, 0, 0, 1, b->max_chunk, s); break;
         case IGM_K_ARNOLDI: launch_mgs_step(B, m - 1, s); break;
         case IGM_K_RESID: launch_resid(B, 0, s); break;
       }

@@ -141,6 +141,14 @@ __device__ __forceinline__ i128 shfl_down_i128(i128 v, int o) {
   return (i128)(((u128)hi << 64) | (u128)lo);
 }
 
+// shuffle down within groups of `width` lanes
+__device__ __forceinline__ i128 shfl_down_i128_w(i128 v, int o, int width) {
+  u128 u = (u128)v;
+  u64 lo = __shfl_down_sync(0xffffffffu, (u64)u, o, width);
+  u64 hi = __shfl_down_sync(0xffffffffu, (u64)(u >> 64), o, width);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
 __device__ __forceinline__ i128 warp_sum_i128(i128 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += shfl_down_i128(v, o);
@@ -271,6 +279,20 @@ __device__ __forceinline__ bool last_tile(unsigned *cnt, int ntiles) {
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
+}
+
+// v * 2^-sh as a double, built with integer operations (exact for
+// |v| < 2^53 and results in the normal range): the same value as
+// scalbn((double)v, -sh) without the FP64 pipe
+__device__ __forceinline__ double i2d_scaled(i64 v, int sh) {
+  if (v == 0) return 0.0;
+  u64 sgn = (u64)v & 0x8000000000000000ull;
+  u64 a = v < 0 ? (u64)(-v) : (u64)v;
+  int lz = __clzll((long long)a);
+  int e = 63 - lz;                        // position of the leading one
+  u64 man = (a << lz) << 1 >> 12;         // the 52 bits below it
+  u64 bits = sgn | ((u64)(1023 + e - sh) << 52) | man;
+  return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ i128 load_part(const long long *part, int t) {

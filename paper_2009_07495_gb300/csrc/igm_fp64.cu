@@ -22,90 +22,6 @@ __device__ __forceinline__ double *Hd(const SysDev *s) { return reinterpret_cast
 __device__ __forceinline__ double *Wd(const SysDev *s) { return reinterpret_cast<double *>(s->w); }
 __device__ __forceinline__ double *Yd(const SysDev *s) { return reinterpret_cast<double *>(s->yv); }
 
-__device__ __forceinline__ int f_ticket(unsigned *ctr) {
-  __shared__ int s_t;
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(ctr, 1u);
-  __syncthreads();
-  return s_t;
-}
-
-// M^-1 with the FP64 factors: lower: y = L^-1 in (unit diagonal);
-// upper: out = U^-1 y.  which: 0 -> r (line 1), 1 -> w (line 5)
-__global__ void f_trsv(BatchDev B, int lower, int which) {
-  int ti = f_ticket(&B.ticket[lower ? (which ? 2 : 0) : (which ? 3 : 1)]);
-  Tile tl = B.tiles[ti];
-  const SysDev *s = B.sys[tl.sys];
-  SysScal *sc = s->sc;
-  if (!f_step(sc) || !s->p.precond) return;
-  const int *ord = lower ? s->lorder : s->uorder;
-  int *flag = lower ? s->lflag : s->uflag;
-  double *vec = which ? Wd(s) : s->r;
-  const double *in = lower ? vec : s->t;
-  double *out = lower ? s->t : vec;
-  int ep = sc->seq;
-  TILE_LOOP(p) {
-    int i = ord[p];
-    double acc = in[i];
-    int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
-    int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      int j = s->col[k];
-      wait_flag(flag + j, ep, &sc->err);
-      acc = __dsub_rn(acc, __dmul_rn(s->f[k], __ldcg(out + j)));
-    }
-    out[i] = lower ? acc : __ddiv_rn(acc, s->f[s->diagpos[i]]);
-    st_release(flag + i, ep);
-  }
-}
-
-// line 5 preconditioner by chunks (same schedule as the integer k_trsv_chunk)
-__global__ void __launch_bounds__(256) f_trsv_chunk(BatchDev B, int lower) {
-  __shared__ int s_t;
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(&B.ticket[lower ? 2 : 3], 1u);
-  __syncthreads();
-  Tile ct = B.ctiles[s_t];
-  const SysDev *s = B.sys[ct.sys];
-  SysScal *sc = s->sc;
-  if (!f_step(sc) || !s->p.precond) return;
-  const int c = ct.row0, n = s->n, R = s->chunk;
-  const int first = c * R;
-  const int *ord = lower ? s->lorder : s->uorder;
-  const int *lptr = lower ? s->llptr : s->ulptr;
-  const int *levb = lower ? s->llevb : s->ulevb;
-  const int *lev = lower ? s->llev : s->ulev;
-  u64 *prog = lower ? s->lprog : s->uprog;
-  const double *in = lower ? Wd(s) : s->t;
-  double *out = lower ? s->t : Wd(s);
-  const u64 ep = (u64)(unsigned)sc->seq << 32;
-  const int g0 = levb[c], g1 = levb[c + 1];
-  for (int g = g0; g < g1; ++g) {
-    for (int p = lptr[g] + threadIdx.x; p < lptr[g + 1]; p += blockDim.x) {
-      int i = ord[p];
-      double acc = in[i];
-      int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
-      int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        int j = s->col[k];
-        int pj = lower ? j : n - 1 - j;
-        double yj;
-        if (pj >= first) {
-          yj = out[j];
-        } else {
-          wait_prog(prog + pj / R, ep | (u64)(lev[j] + 1), &sc->err);
-          yj = __ldcg(out + j);
-        }
-        acc = __dsub_rn(acc, __dmul_rn(s->f[k], yj));
-      }
-      out[i] = lower ? acc : __ddiv_rn(acc, s->f[s->diagpos[i]]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release64(prog + c, ep | (u64)(g - g0 + 1));
-    }
-  }
-}
-
 // v_1 = r0 / ||r0||, g = (||r0||, 0, ...)
 __global__ void f_v1(BatchDev B) {
   Tile tl = B.tiles[blockIdx.x];
@@ -192,20 +108,20 @@ __global__ void f_resid_guess(BatchDev B) {
   }
 }
 
-void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, cudaStream_t st) {
+void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, int max_chunk, cudaStream_t st) {
   const int T = B.ntiles;
-  if (any_ilu) {
-    f_trsv<<<T, IGM_BLOCK, 0, st>>>(B, 1, 0);
-    f_trsv<<<T, IGM_BLOCK, 0, st>>>(B, 0, 0);
+  if (any_ilu) {  // line 1' with the FP64 factors
+    launch_trsv_lv(B, 2, 1, 0, max_chunk, st);
+    launch_trsv_lv(B, 2, 0, 0, max_chunk, st);
   }
   launch_max(B, VEC_R, 2, st);
   launch_norm(B, VEC_R, ACT_NU, 2, st);
   f_v1<<<T, IGM_BLOCK, 0, st>>>(B);
   for (int j = 0; j < m; ++j) {
     f_spmv<<<T, IGM_BLOCK, 0, st>>>(B, j);
-    if (any_ilu && B.nctiles > 0) {
-      f_trsv_chunk<<<B.nctiles, 256, 0, st>>>(B, 1);
-      f_trsv_chunk<<<B.nctiles, 256, 0, st>>>(B, 0);
+    if (any_ilu) {  // line 5' with the FP64 factors
+      launch_trsv_lv(B, 2, 1, 1, max_chunk, st);
+      launch_trsv_lv(B, 2, 0, 1, max_chunk, st);
     }
     launch_fp64_mgs_step(B, j, st);
   }

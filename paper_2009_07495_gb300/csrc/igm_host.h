@@ -64,7 +64,7 @@ struct Batch;
 struct igm_handle_s {
   int n = 0, nnz = 0;
   igm_params prm{};
-  Arena arena;
+  Arena arena, arena2;   // system data; substitution schedules
   SysDev hs{};           // host copy of the descriptor (device pointers)
   SysDev *d_sys = nullptr;
   SysScal *d_sc = nullptr;
@@ -75,7 +75,7 @@ struct igm_handle_s {
 struct Batch {
   std::vector<igm_handle> hs;
   long long nodes_check = 0, nodes_cycle = 0;
-  int m = 0, any_ilu = 0, inner = 0;
+  int m = 0, any_ilu = 0, inner = 0, max_chunk = 0;
   Arena arena;
   BatchDev bd{};
   int *h_nact = nullptr;  // pinned

@@ -55,6 +55,24 @@ struct SysScal {
   double gamma_hist[64];
 };
 
+// Schedule and level-packed data of one triangular factor.  Positions
+// p = 0..n-1 run in dependency order (L: row p, U: row n-1-p), are cut into
+// chunks of `chunk` positions, and inside each chunk grouped by local level
+// (dependency depth counted inside the chunk).  ord[p] is the row at
+// position p; group g = (chunk, level) covers positions lptr[g]..lptr[g+1];
+// levb[c] is the first group of chunk c.  The strict part of the row at
+// position p is packed dependency-major: pcol[q*n + p], pfac[q*n + p]
+// (q < K, col -1 past the row's end), with its diagonal pdiag[p]; pfacd,
+// pdiagd: the same from the FP64 factors (FP64 comparison solver only).
+// need[g]: progress the previous chunk must reach before group g runs.
+struct Tri {
+  const int *ord, *lptr, *levb, *lev, *need, *pcol;
+  const i64 *pfac, *pdiag;
+  const double *pfacd, *pdiagd;
+  u64 *prog;                    // per chunk: (epoch << 32) | levels done
+  int nchunk, K;
+};
+
 struct SysDev {
   int n, nnz, ld;          // ld = m + 1
   int pad;
@@ -64,14 +82,12 @@ struct SysDev {
   const i64 *abar;
   const double *f;                       // FP64 ILU(0) factors
   const i64 *fac, *ldiag, *udiag;        // integer factors
-  // substitution schedules: rows in chunk order, each chunk in local-level
-  // order (L: chunks from the top, U: from the bottom); lptr: start of each
-  // (chunk, level) group in the order; levb: first group of each chunk
-  const int *lorder, *uorder, *llptr, *ulptr, *llevb, *ulevb;
-  int chunk, lnchunk, unchunk;  // rows per chunk, chunks of L and U
-  const int *llev, *ulev;       // local level of every row in its chunk
-  u64 *lprog, *uprog;           // per chunk: (epoch << 32) | levels done
-  int *lflag, *uflag;
+  // substitution schedules of the two factors, tri[0] = L, tri[1] = U
+  Tri tri[2];
+  int chunk;                    // rows per chunk (both factors)
+  int single_pred;              // chunk >= bandwidth: every dependency
+                                // outside a chunk lies in the previous one
+  int *lflag, *uflag;           // per-row ready flags (set-up, line 1' none)
   double *b, *bh, *xt, *r, *t, *xk;
   i64 *w, *yv, *V;
   i64 *H, *cs, *sn, *g;

@@ -10,6 +10,7 @@ namespace igm {
 // set-up (one system)
 void launch_validate(int n, int nnz, const int *rowptr, const int *col, int *diagpos,
                      unsigned *err, cudaStream_t st);
+void launch_bandwidth(int n, const int *rowptr, const int *col, int *bw, cudaStream_t st);
 void launch_scale(int n, const int *rowptr, const double *ahat, int alpha, double *a,
                   double *d, unsigned *err, cudaStream_t st);
 void launch_cast(long long nnz, const double *a, i64 *abar, unsigned *err, cudaStream_t st);
@@ -18,10 +19,19 @@ void launch_levels(int n, const int *rowptr, const int *col, const int *diagpos,
                    unsigned *err, cudaStream_t st);
 void launch_level_order(int n, int lower, int R, int L, const int *level, const int *levb,
                         int *cnt, int *lptr, int *order, cudaStream_t st);
-void launch_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
-                 const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
-                 unsigned *err, cudaStream_t st);
-void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
+void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos, const Tri &T,
+                    int R, int single, double *f, unsigned *ticket, int epoch, unsigned *err,
+                    cudaStream_t st);
+void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
+                 const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
+                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pfacd,
+                 double *pdiagd, cudaStream_t st);
+void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
+                 const int *ord, const int *levb, const int *lev, int *need, cudaStream_t st);
+// substitutions: kind 0 integer (line 5'), 1 FP64 on the integer factors
+// (line 1'), 2 FP64 factors (comparison solver); which 0 line 1', 1 line 5'
+void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
+                    cudaStream_t st);void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,
                     cudaStream_t st);
 
@@ -34,8 +44,6 @@ void launch_resid(const BatchDev &B, int hat, cudaStream_t st);
 void launch_resid_int(const BatchDev &B, cudaStream_t st);
 void launch_rhs(const BatchDev &B, cudaStream_t st);
 void launch_arm(const BatchDev &B, cudaStream_t st);
-void launch_trsv_fp(const BatchDev &B, int lower, cudaStream_t st);
-void launch_trsv_chunk(const BatchDev &B, int lower, cudaStream_t st);
 void launch_cast_v1(const BatchDev &B, cudaStream_t st);
 void launch_spmv(const BatchDev &B, int j, cudaStream_t st);
 // lines 6-19 of step j: persistent MGS + norm + line 11, then Givens
@@ -44,10 +52,13 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 int persistent_grid(int ntiles);  // CTAs of the persistent kernels
 void launch_backsub(const BatchDev &B, cudaStream_t st);
 void launch_update(const BatchDev &B, cudaStream_t st);
+int norm2_grid(int n);
+void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out,
+                  cudaStream_t st);
 void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st);
 
 // FP64 GMRES(m) comparison solver (lines 1-23 after line 1's residual)
-void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, cudaStream_t st);
+void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, int max_chunk, cudaStream_t st);
 void launch_fp64_resid_guess(const BatchDev &B, cudaStream_t st);
 
 }  // namespace igm

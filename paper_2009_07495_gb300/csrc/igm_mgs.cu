@@ -79,24 +79,41 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
         a[0] = 0;
         a[1] = 0;
       }
-    for (int t = blockIdx.x; t < B.ntiles; t += G) {
-      Tile tl = B.tiles[t];
+    // a CTA's tiles of one system are consecutive: their partial sums are
+    // combined in registers and published once per system
+    int cur = -1;
+    i128 part = 0;
+    unsigned evA = 0, evB = 0;
+    i64 hs = 0;
+    for (int t = blockIdx.x;; t += G) {
+      const bool end = t >= B.ntiles;
+      Tile tl = end ? Tile{-1, 0, 0, 0} : B.tiles[t];
+      if (tl.sys != cur && cur >= 0) {
+        SysScal *csc = B.sys[cur]->sc;
+        flush_ev(evB, &csc->ev[IGM_EV_L8]);
+        flush_ev(evA, &csc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+        part = block_sum_i128(part);
+        if (threadIdx.x == 0) acc_add(acc_slot(B, slot, cur), part);
+        part = 0;
+        evA = evB = 0;
+        cur = -1;
+      }
+      if (end) break;
       const SysDev *s = B.sys[tl.sys];
       if (!m_step(s, j)) continue;
       const SysParams &P = s->p;
       const int n = s->n, df = P.df;
-      SysScal *sc = s->sc;
-      // h_{i-1,j} from the previous pass's exact sum
-      i64 hs = 0;
-      if (i > 0) {
-        i128 tot = acc_load(acc_slot(B, (i - 1) % 3, tl.sys));
-        i64 h = shr(wrap(tot), df - P.b7);
-        hs = shr(h, P.b8);
+      if (cur != tl.sys) {
+        cur = tl.sys;
+        // h_{i-1,j} from the previous pass's exact sum
+        hs = 0;
+        if (i > 0) {
+          i128 tot = acc_load(acc_slot(B, (i - 1) % 3, tl.sys));
+          hs = shr(shr(wrap(tot), df - P.b7), P.b8);
+        }
       }
       const i64 *vp = s->V + (size_t)(i > 0 ? i - 1 : 0) * n;
       const i64 *vi = s->V + (size_t)(i <= j ? i : 0) * n;
-      unsigned evA = 0, evB = 0;
-      i128 part = 0;
       for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
         i64 wl = s->w[l];
         if (i > 0) {
@@ -113,10 +130,6 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
           part += (i128)mulw(a, a, evA);
         }
       }
-      flush_ev(evB, &sc->ev[IGM_EV_L8]);
-      flush_ev(evA, &sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
-      part = block_sum_i128(part);
-      if (threadIdx.x == 0) acc_add(acc_slot(B, slot, tl.sys), part);
     }
     if (!grid_sync(B.bar, err0)) return;
     // one thread records h_{i,j} (and the total's overflow event) per system

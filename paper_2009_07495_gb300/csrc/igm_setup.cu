@@ -30,6 +30,31 @@ __global__ void s_validate(int n, int nnz, const int *rowptr, const int *col, in
   }
 }
 
+// bandwidths of the strict triangles, max (i - j) below and (j - i) above,
+// and the largest number of entries of a row below / above the diagonal
+// (bw[0..3]); columns are ascending, rows well formed (checked before)
+__global__ void s_bandwidth(int n, const int *rowptr, const int *col, int *bw) {
+  int lo = 0, hi = 0, kl = 0, ku = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int k0 = rowptr[i], k1 = rowptr[i + 1];
+    if (k1 > k0) {
+      lo = max(lo, i - col[k0]);
+      hi = max(hi, col[k1 - 1] - i);
+    }
+    int nl = 0, nu = 0;
+    for (int k = k0; k < k1; ++k) {
+      nl += col[k] < i;
+      nu += col[k] > i;
+    }
+    kl = max(kl, nl);
+    ku = max(ku, nu);
+  }
+  atomicMax(bw, lo);
+  atomicMax(bw + 1, hi);
+  atomicMax(bw + 2, kl);
+  atomicMax(bw + 3, ku);
+}
+
 // eq. (3): d_i = max_j |ahat_ij| 2^-alpha_a; eq. (1): a_ij = ahat_ij / d_i
 __global__ void s_scale(int n, const int *rowptr, const double *ahat, int alpha,
                         double *a, double *d, unsigned *err) {
@@ -136,41 +161,6 @@ __global__ void s_scatter(int n, int lower, int R, const int *level, const int *
   }
 }
 
-// eq. (ilu): ILU(0), IKJ row variant on the pattern of A (Saad, Alg. 10.4):
-// for row i, k ascending over its strict lower part: l_ik = a_ik / u_kk,
-// then a_ij -= l_ik u_kj for the j > k of row i present in row k.  Rows in
-// level order, synchronisation-free as in the substitutions.
-__global__ void s_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
-                       const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
-                       unsigned *err) {
-  __shared__ int s_t;
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(ticket, 1u);
-  __syncthreads();
-  int p = s_t * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  int i = lorder[p];
-  int end = rowptr[i + 1];
-  for (int kk = rowptr[i]; kk < diagpos[i]; ++kk) {
-    int k = col[kk];
-    wait_flag(flag + k, epoch, err);
-    double ukk = __ldcg(f + diagpos[k]);
-    if (ukk == 0.0) {
-      atomicOr(err, ERR_ZERO_PIVOT);
-      break;
-    }
-    double lik = __ddiv_rn(f[kk], ukk);
-    f[kk] = lik;
-    int q = diagpos[k] + 1, qe = rowptr[k + 1];
-    for (int jj = kk + 1; jj < end; ++jj) {
-      int jc = col[jj];
-      while (q < qe && col[q] < jc) ++q;
-      if (q < qe && col[q] == jc) f[jj] = __dsub_rn(f[jj], __dmul_rn(lik, __ldcg(f + q)));
-    }
-  }
-  if (f[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
-  st_release(flag + i, epoch);
-}
-
 // eq. (dl), (dl2), (l1), (u1), (ilu2): D_l = |d|^1/2, D_u = sgn(d)|d|^1/2,
 // Lbar = trunc(L D_l), Ubar = trunc(D_u U') with U' = D^-1 U
 __global__ void s_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
@@ -214,6 +204,9 @@ void launch_validate(int n, int nnz, const int *rowptr, const int *col, int *dia
                      unsigned *err, cudaStream_t st) {
   s_validate<<<grid_for(n, 256), 256, 0, st>>>(n, nnz, rowptr, col, diagpos, err);
 }
+void launch_bandwidth(int n, const int *rowptr, const int *col, int *bw, cudaStream_t st) {
+  s_bandwidth<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, bw);
+}
 void launch_scale(int n, const int *rowptr, const double *ahat, int alpha, double *a,
                   double *d, unsigned *err, cudaStream_t st) {
   s_scale<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, ahat, alpha, a, d, err);
@@ -233,12 +226,6 @@ void launch_level_order(int n, int lower, int R, int L, const int *level, const 
   s_scan<<<1, 1024, 0, st>>>(L, cnt, lptr);
   cudaMemcpyAsync(cnt, lptr, sizeof(int) * L, cudaMemcpyDeviceToDevice, st);
   s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt, order);
-}
-void launch_ilu0(int n, const int *rowptr, const int *col, const int *diagpos,
-                 const int *lorder, double *f, int *flag, int epoch, unsigned *ticket,
-                 unsigned *err, cudaStream_t st) {
-  s_ilu0<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, diagpos, lorder, f, flag, epoch,
-                                           ticket, err);
 }
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,

@@ -21,6 +21,21 @@ __device__ __forceinline__ bool g_step(const SysScal *sc) {
   return sc->cyc != 0 && sc->early == 0;
 }
 
+// the last CTA of a system combines all its tile partials, every thread
+// taking a strided share (result in thread 0)
+__device__ __forceinline__ double tiles_max(const BatchDev &B, const Tile &tl) {
+  double m = 0.0;
+  for (int t = threadIdx.x; t < B.sys_ntiles[tl.sys]; t += blockDim.x)
+    m = fmax(m, __ldcg(B.partd + tl.first + t));
+  return block_max(m);
+}
+__device__ __forceinline__ i128 tiles_sum(const BatchDev &B, const Tile &tl) {
+  i128 v = 0;
+  for (int t = threadIdx.x; t < B.sys_ntiles[tl.sys]; t += blockDim.x)
+    v += load_part(B.part, tl.first + t);
+  return block_sum_i128(v);
+}
+
 __device__ __forceinline__ const double *vec_of(const SysDev *s, int which) {
   return which == VEC_B ? s->b : which == VEC_R ? s->r : s->bh;
 }
@@ -76,11 +91,8 @@ __global__ void k_max(BatchDev B, int which, int gate) {
   m = block_max(m);
   if (threadIdx.x == 0) B.partd[blockIdx.x] = m;
   if (last_tile(&sc->cnt[0], B.sys_ntiles[tl.sys])) {
-    if (threadIdx.x == 0) {
-      double mx = 0.0;
-      for (int t = 0; t < B.sys_ntiles[tl.sys]; ++t) mx = fmax(mx, __ldcg(B.partd + tl.first + t));
-      sc->maxabs = mx;
-    }
+    double mx = tiles_max(B, tl);
+    if (threadIdx.x == 0) sc->maxabs = mx;
   }
 }
 
@@ -142,9 +154,8 @@ __global__ void k_norm(BatchDev B, int which, int act, int gate) {
   acc = block_sum_i128(acc);
   if (threadIdx.x == 0) store_part(B.part, blockIdx.x, acc);
   if (last_tile(&sc->cnt[0], B.sys_ntiles[tl.sys])) {
+    i128 tot = tiles_sum(B, tl);
     if (threadIdx.x == 0) {
-      i128 tot = 0;
-      for (int t = 0; t < B.sys_ntiles[tl.sys]; ++t) tot += load_part(B.part, tl.first + t);
       double nrm = mx > 0.0 ? norm_from_acc(tot, e) : 0.0;
       norm_action(B, s, sc, act, nrm);
     }
@@ -175,11 +186,8 @@ __global__ void k_resid(BatchDev B, int hat) {
   m = block_max(m);
   if (threadIdx.x == 0) B.partd[blockIdx.x] = m;
   if (last_tile(&sc->cnt[0], B.sys_ntiles[tl.sys])) {
-    if (threadIdx.x == 0) {
-      double mx = 0.0;
-      for (int t = 0; t < B.sys_ntiles[tl.sys]; ++t) mx = fmax(mx, __ldcg(B.partd + tl.first + t));
-      sc->maxabs = mx;
-    }
+    double mx = tiles_max(B, tl);
+    if (threadIdx.x == 0) sc->maxabs = mx;
   }
 }
 
@@ -225,108 +233,6 @@ __global__ void k_arm(BatchDev B) {
 }
 
 // ---------------------------------------------------------------------------
-// Sparse triangular substitutions, synchronisation-free: rows are visited in
-// level order (dependencies always sit at earlier positions of the same
-// system), CTAs take tiles by a dynamic ticket so that every row waited on
-// belongs to a CTA that is already running; each row waits (bounded) on
-// the ready flags of the rows it reads, then publishes its value with a
-// release store of the current epoch.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int take_ticket(unsigned *ctr) {
-  __shared__ int s_t;
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(ctr, 1u);
-  __syncthreads();
-  return s_t;
-}
-
-// line 1': y = Lbar^-1 z (lower = 1) or w = Ubar^-1 y (lower = 0), FP64 on the
-// integer factors; z = r -> t (lower) and t -> r (upper)
-__global__ void k_trsv_fp(BatchDev B, int lower) {
-  int ti = take_ticket(&B.ticket[lower ? 0 : 1]);
-  Tile tl = B.tiles[ti];
-  const SysDev *s = B.sys[tl.sys];
-  SysScal *sc = s->sc;
-  if (!(g_cyc(sc) && sc->early == 0) || !s->p.precond) return;
-  const int *ord = lower ? s->lorder : s->uorder;
-  int *flag = lower ? s->lflag : s->uflag;
-  const double *in = lower ? s->r : s->t;
-  double *out = lower ? s->t : s->r;
-  int ep = sc->seq;
-  TILE_LOOP(p) {
-    int i = ord[p];
-    double acc = in[i];
-    int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
-    int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      int j = s->col[k];
-      wait_flag(flag + j, ep, &sc->err);
-      acc = __dsub_rn(acc, __dmul_rn((double)s->fac[k], __ldcg(out + j)));
-    }
-    out[i] = __ddiv_rn(acc, (double)(lower ? s->ldiag[i] : s->udiag[i]));
-    st_release(flag + i, ep);
-  }
-}
-
-// line 5' by chunks: each CTA takes (by ticket, in dependency order) one
-// chunk of consecutive rows and walks its local levels, separated by CTA
-// barriers; a dependency inside the chunk was computed at an earlier local
-// level of the same CTA, a dependency in an earlier chunk is waited for on
-// that chunk's progress word, which the chunk publishes once per level.
-// Integer arithmetic as k_trsv_int (exact int128 numerator, truncating
-// division).
-#define IGM_TRSV_BLOCK 256
-__global__ void __launch_bounds__(IGM_TRSV_BLOCK) k_trsv_chunk(BatchDev B, int lower) {
-  __shared__ int s_t;
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(&B.ticket[lower ? 2 : 3], 1u);
-  __syncthreads();
-  Tile ct = B.ctiles[s_t];
-  const SysDev *s = B.sys[ct.sys];
-  SysScal *sc = s->sc;
-  if (!g_step(sc) || !s->p.precond) return;
-  const int c = ct.row0, n = s->n, R = s->chunk;
-  const int first = c * R;
-  const int *ord = lower ? s->lorder : s->uorder;
-  const int *lptr = lower ? s->llptr : s->ulptr;
-  const int *levb = lower ? s->llevb : s->ulevb;
-  const int *lev = lower ? s->llev : s->ulev;
-  u64 *prog = lower ? s->lprog : s->uprog;
-  const i64 *dg = lower ? s->ldiag : s->udiag;
-  const i64 *in = lower ? s->w : s->yv;
-  i64 *out = lower ? s->yv : s->w;
-  const u64 ep = (u64)(unsigned)sc->seq << 32;
-  const int g0 = levb[c], g1 = levb[c + 1];
-  unsigned ev = 0;
-  for (int g = g0; g < g1; ++g) {
-    for (int p = lptr[g] + threadIdx.x; p < lptr[g + 1]; p += blockDim.x) {
-      int i = ord[p];
-      i128 acc = in[i];
-      int k0 = lower ? s->rowptr[i] : s->diagpos[i] + 1;
-      int k1 = lower ? s->diagpos[i] : s->rowptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        int j = s->col[k];
-        int pj = lower ? j : n - 1 - j;
-        i64 yj;
-        if (pj >= first) {
-          yj = out[j];
-        } else {
-          wait_prog(prog + pj / R, ep | (u64)(lev[j] + 1), &sc->err);
-          yj = (i64)__ldcg((const long long *)out + j);
-        }
-        acc -= (i128)mulw(s->fac[k], yj, ev);
-      }
-      ev += out64(acc);
-      out[i] = divt(wrap(acc), dg[i], ev);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release64(prog + c, ep | (u64)(g - g0 + 1));
-    }
-  }
-  flush_ev(ev, &sc->ev[IGM_EV_L5P]);
-}
-
-// ---------------------------------------------------------------------------
 // line 1 end and lines 2-3: v1 = r0 / ||r0||, cast to Q(df); g = (2^df, 0..)
 // ---------------------------------------------------------------------------
 __global__ void k_cast_v1(BatchDev B) {
@@ -352,9 +258,11 @@ __global__ void k_cast_v1(BatchDev B) {
 }
 
 // ---------------------------------------------------------------------------
-// line 5: w = Abar_0 v_j (exact int128 row sums; Table 3 line 5)
+// line 5: w = Abar_0 v_j (exact int128 row sums; Table 3 line 5), one thread
+// per row (consecutive threads read consecutive rows' entries, which share
+// cache lines)
 // ---------------------------------------------------------------------------
-__global__ void k_spmv(BatchDev B, int j) {
+__global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     B.ticket[2] = 0;
     B.ticket[3] = 0;
@@ -409,13 +317,67 @@ __global__ void k_update(BatchDev B) {
   const int jeff = sc->jeff, n = s->n, df = s->p.df;
   const bool ir = sc->mode == 0;
   double gam = sc->gamma;
+  // y_i (v_il 2^-df): the scaled basis entry is exact, built with integer
+  // operations (GB300's FP64 rate is low)
   TILE_LOOP(l) {
     double acc = ir ? 0.0 : s->xk[l];
     for (int i = 0; i < jeff; ++i)
-      acc = __dadd_rn(acc, __dmul_rn(s->yfp[i], scalbn((double)s->V[(size_t)i * n + l], -df)));
+      acc = __dadd_rn(acc, __dmul_rn(s->yfp[i], i2d_scaled(s->V[(size_t)i * n + l], df)));
     if (ir) s->xt[l] = __dadd_rn(s->xt[l], __dmul_rn(gam, acc));
     else s->xk[l] = acc;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Reproducible 2-norm of one vector (the norm of Fig. 1's test), standalone:
+// pass 1 max |x_i|, pass 2 the exact sum of the truncated squares; each pass
+// finishes in its last CTA.  ws: scratch of 2*grid int64 partials + 2 words.
+// ---------------------------------------------------------------------------
+__global__ void k_vmax(const double *x, int n, long long *ws, double *mx_out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  m = block_max(m);
+  double *pd = reinterpret_cast<double *>(ws);
+  unsigned *cnt = reinterpret_cast<unsigned *>(ws + 2 * gridDim.x);
+  if (threadIdx.x == 0) pd[blockIdx.x] = m;
+  if (last_tile(cnt, gridDim.x) && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t = fmax(t, __ldcg(pd + b));
+    *mx_out = t;
+  }
+}
+
+__global__ void k_vnorm(const double *x, int n, long long *ws, const double *mx, double *out) {
+  double m = *mx;
+  int e = m > 0.0 ? ilogb(m) : 0;
+  i128 acc = 0;
+  if (m > 0.0)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      acc += sq_term(x[i], e);
+  acc = block_sum_i128(acc);
+  unsigned *cnt = reinterpret_cast<unsigned *>(ws + 2 * gridDim.x);
+  if (threadIdx.x == 0) store_part(ws, blockIdx.x, acc);
+  if (last_tile(cnt, gridDim.x) && threadIdx.x == 0) {
+    i128 tot = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) tot += load_part(ws, b);
+    *out = m > 0.0 ? norm_from_acc(tot, e) : 0.0;
+  }
+}
+
+int norm2_grid(int n) {
+  int g = (n + IGM_BLOCK * 4 - 1) / (IGM_BLOCK * 4);
+  if (g > 1024) g = 1024;
+  return g < 1 ? 1 : g;
+}
+
+// ws: 2*norm2_grid(n) + 2 int64 words whose last two start at zero (the
+// kernels leave them at zero); mx: one double of scratch
+void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out,
+                  cudaStream_t st) {
+  int g = norm2_grid(n);
+  k_vmax<<<g, IGM_BLOCK, 0, st>>>(x, n, ws, mx);
+  k_vnorm<<<g, IGM_BLOCK, 0, st>>>(x, n, ws, mx, out);
 }
 
 // per-system {active, status, error bits, refinements} for the host
@@ -454,12 +416,6 @@ void launch_rhs(const BatchDev &B, cudaStream_t st) {
 }
 void launch_arm(const BatchDev &B, cudaStream_t st) {
   k_arm<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);
-}
-void launch_trsv_fp(const BatchDev &B, int lower, cudaStream_t st) {
-  k_trsv_fp<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, lower);
-}
-void launch_trsv_chunk(const BatchDev &B, int lower, cudaStream_t st) {
-  if (B.nctiles > 0) k_trsv_chunk<<<B.nctiles, IGM_TRSV_BLOCK, 0, st>>>(B, lower);
 }
 void launch_cast_v1(const BatchDev &B, cudaStream_t st) {
   k_cast_v1<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);

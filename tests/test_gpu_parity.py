@@ -259,3 +259,73 @@ def test_server_budget_admission(L):
         srv.submit(big.rowptr, big.col, big.val, big.b, P)
     assert e.value.name == "eoom"
     srv.close()
+
+
+@pytest.mark.parametrize("n", [1, 7, 1000, 262144 + 13])
+@pytest.mark.parametrize("scale", [1e-150, 1.0, 1e200])
+def test_norm2_bit_exact(L, orc, n, scale):
+    """igm_norm2 (device and host input) equals the oracle's reproducible
+    norm bit for bit, and is independent of the element order."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) * scale
+    ref = orc.norm2(x)
+    assert L.norm2(_dev(x)) == ref
+    assert L.norm2(x) == ref
+    assert L.norm2(_dev(rng.permutation(x))) == ref
+    assert L.norm2(np.zeros(5)) == 0.0
+
+
+@pytest.mark.parametrize("chunk", [100, 1000, 1024, 1500, 4096, 1 << 20])
+def test_chunk_schedule_does_not_change_results(L, orc, chunk):
+    """Line 5' runs over chunked level schedules; any chunk size (several
+    ragged chunks, one chunk for the whole system) gives the oracle's result
+    bit for bit."""
+    s = W.small_cd3d(16, seed=44)
+    P = L.params_default(1, 30)
+    P.trsv_chunk = chunk
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    solver.close()
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return W.config1()
+
+
+def test_full_size_config1_inner_solve_bit_exact(L, orc, cfg1):
+    """Config 1 at full size (128^3, n = 2,097,152, ILU(0), m = 50), in the
+    launch configuration of the benchmark: one whole inner solve (Fig. 2) is
+    bit-identical to the oracle's -- basis, Hessenberg matrix, rotations, g,
+    correction and overflow counts."""
+    s = cfg1
+    P = L.params_default(1, 50)
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    bk = d["b"] / np.abs(d["b"]).max()
+    o = orc.int_gmres(_oparams(orc, P), d, bk)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(np.zeros(s.n))
+    rep = solver.inner_solve(_dev(bk), xk)
+    st = solver.state()
+    _compare_inner(st, o, s.n, 50)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    solver.close()
+
+
+def test_full_size_config1_refinement(L, cfg1):
+    """The full refinement solve of config 1 reaches 1e-10 in 6 refinements,
+    the count of the oracle's own full solve of this system (measured once;
+    the two paths agree bit for bit), with no overflow event (Sec. VII-C:
+    ILU with zero shifts) and a decreasing gamma (Sec. IV-A)."""
+    s = cfg1
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), L.params_default(1, 50))
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert rep["status"] == "ok" and rep["relres"] < 1e-10
+    assert rep["refinements"] == 6
+    assert np.all(rep["ev"] == 0)
+    assert np.all(np.diff(rep["gamma_hist"]) < 0)
+    solver.close()
