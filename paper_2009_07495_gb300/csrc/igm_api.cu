@@ -42,7 +42,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   Batch *b = new Batch();
   b->hs = hs;
   int ns = (int)hs.size();
-  std::vector<Tile> tiles, ctiles;
+  std::vector<Tile> tiles, ctiles, stiles;
   std::vector<int> snt(ns);
   std::vector<SysDev *> sp(ns);
   b->m = hs[0]->prm.m;
@@ -60,12 +60,14 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
       tiles.push_back(Tile{s, t * IGM_TILE, std::min(IGM_TILE, h->n - t * IGM_TILE), first});
     snt[s] = nt;
     sp[s] = h->d_sys;
+    for (int r0 = 0; r0 < h->n; r0 += IGM_STILE)
+      stiles.push_back(Tile{s, r0, std::min(IGM_STILE, h->n - r0), 0});
     int cfirst = (int)ctiles.size();
     for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
     b->max_chunk = std::max(b->max_chunk, h->hs.chunk);
   }
-  int CT = (int)ctiles.size();
-  Tile *d_ctiles = nullptr;
+  int CT = (int)ctiles.size(), ST = (int)stiles.size();
+  Tile *d_ctiles = nullptr, *d_stiles = nullptr;
   int T = (int)tiles.size();
   Tile *d_tiles;
   int *d_snt, *d_nact;
@@ -75,9 +77,10 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   unsigned *d_ticket, *d_bar;
   u64 *d_acc;
   double *d_cpart;
-  int maxg = persistent_grid(T);
+  int maxg = persistent_grid(ST);
   b->arena.want(&d_tiles, T);
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
+  b->arena.want(&d_stiles, ST);
   b->arena.want(&d_bar, 2);
   b->arena.want(&d_acc, 6 * (size_t)ns);
   b->arena.want(&d_cpart, 3 * (size_t)maxg * ns);
@@ -94,14 +97,16 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   }
   CK(cudaMemcpy(d_tiles, tiles.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice));
   if (CT > 0) CK(cudaMemcpy(d_ctiles, ctiles.data(), sizeof(Tile) * CT, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_stiles, stiles.data(), sizeof(Tile) * ST, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_snt, snt.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sp, sp.data(), sizeof(SysDev *) * ns, cudaMemcpyHostToDevice));
   CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
   CK(cudaMemset(d_nact, 0, sizeof(int)));
   CK(cudaMemset(d_bar, 0, 2 * sizeof(unsigned)));
   CK(cudaMemset(d_acc, 0, 6 * sizeof(u64) * ns));
-  b->bd = BatchDev{ns,       T,      CT,    d_ctiles, d_sp,    d_tiles, d_snt,
-                   d_part,   d_partd, d_ticket, d_nact, d_bar, d_acc,   d_cpart, maxg};
+  b->bd = BatchDev{ns,    T,        ST,      d_stiles, CT,     d_ctiles, d_sp,  d_tiles,
+                   d_snt, d_part,   d_partd, d_ticket, d_nact, d_bar,    d_acc, d_cpart,
+                   maxg};
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;

@@ -102,8 +102,12 @@ struct Tile {
   int first;   // index of the system's first tile
 };
 
+#define IGM_STILE 4096     // rows of a super-tile of the persistent kernels
+
 struct BatchDev {
   int nsys, ntiles;
+  int nstiles;             // super-tiles (IGM_STILE rows, one system each)
+  const Tile *stiles;
   int nctiles;             // substitution chunks over all systems
   const Tile *ctiles;      // {sys, chunk index, -, first chunk tile}
   SysDev *const *sys;      // device pointers to each system's SysDev

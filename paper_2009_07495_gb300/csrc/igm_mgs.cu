@@ -67,6 +67,8 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
   return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
 }
 
+#define IGM_RPT (IGM_STILE / IGM_MGS_BLOCK)  // rows per thread in a super-tile
+
 __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j) {
   const int G = gridDim.x;
   unsigned *err0 = &B.sys[0]->sc->err;
@@ -79,15 +81,15 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
         a[0] = 0;
         a[1] = 0;
       }
-    // a CTA's tiles of one system are consecutive: their partial sums are
-    // combined in registers and published once per system
+    // a CTA's super-tiles of one system are consecutive: their partial sums
+    // are combined in registers and published once per system
     int cur = -1;
     i128 part = 0;
     unsigned evA = 0, evB = 0;
     i64 hs = 0;
     for (int t = blockIdx.x;; t += G) {
-      const bool end = t >= B.ntiles;
-      Tile tl = end ? Tile{-1, 0, 0, 0} : B.tiles[t];
+      const bool end = t >= B.nstiles;
+      Tile tl = end ? Tile{-1, 0, 0, 0} : B.stiles[t];
       if (tl.sys != cur && cur >= 0) {
         SysScal *csc = B.sys[cur]->sc;
         flush_ev(evB, &csc->ev[IGM_EV_L8]);
@@ -114,17 +116,32 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
       }
       const i64 *vp = s->V + (size_t)(i > 0 ? i - 1 : 0) * n;
       const i64 *vi = s->V + (size_t)(i <= j ? i : 0) * n;
-      for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
-        i64 wl = s->w[l];
+      i64 *w = s->w;
+      // all loads of the thread's rows first (memory-level parallelism)
+      i64 wv[IGM_RPT], pv[IGM_RPT], qv[IGM_RPT];
+#pragma unroll
+      for (int u = 0; u < IGM_RPT; ++u) {
+        const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
+        const int l = tl.row0 + lr;
+        const bool ok = lr < tl.nrows;
+        wv[u] = ok ? w[l] : 0;
+        pv[u] = (ok && i > 0) ? vp[l] : 0;
+        qv[u] = (ok && i <= j) ? vi[l] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < IGM_RPT; ++u) {
+        const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
+        if (lr >= tl.nrows) continue;
+        i64 wl = wv[u];
         if (i > 0) {
-          i64 p = shr(mulw(hs, vp[l], evB), df - P.b8);
+          i64 p = shr(mulw(hs, pv[u], evB), df - P.b8);
           i128 d = (i128)wl - (i128)p;
           evB += out64(d);
           wl = wrap(d);
-          s->w[l] = wl;
+          w[tl.row0 + lr] = wl;
         }
         if (i <= j) {
-          part += (i128)mulw(shr(wl, P.b7), vi[l], evA);
+          part += (i128)mulw(shr(wl, P.b7), qv[u], evA);
         } else {
           i64 a = shr(wl, P.b10);
           part += (i128)mulw(a, a, evA);
@@ -151,8 +168,8 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
   }
   // line 11 for every system whose divisor is non-zero
   const int slot = (j + 1) % 3;
-  for (int t = blockIdx.x; t < B.ntiles; t += G) {
-    Tile tl = B.tiles[t];
+  for (int t = blockIdx.x; t < B.nstiles; t += G) {
+    Tile tl = B.stiles[t];
     const SysDev *s = B.sys[tl.sys];
     if (!m_step(s, j)) continue;
     const SysParams &P = s->p;
@@ -160,10 +177,19 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
     i64 hn = fx_sqrt(wrap(acc_load(acc_slot(B, slot, tl.sys))), 2 * P.df - 2 * P.b10, P.df, e10);
     if (shr(hn, P.b11b) == 0) continue;
     i64 *vn = s->V + (size_t)(j + 1) * s->n;
-    for (int l = tl.row0 + threadIdx.x; l < tl.row0 + tl.nrows; l += blockDim.x) {
-      i64 q = fx_div(s->w[l], hn, P.b11a, P.b11b, P.df, ev);
+    i64 wv[IGM_RPT];
+#pragma unroll
+    for (int u = 0; u < IGM_RPT; ++u) {
+      const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
+      wv[u] = lr < tl.nrows ? s->w[tl.row0 + lr] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < IGM_RPT; ++u) {
+      const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
+      if (lr >= tl.nrows) continue;
+      i64 q = fx_div(wv[u], hn, P.b11a, P.b11b, P.df, ev);
       evr += (q < INT32_MIN || q > INT32_MAX);
-      vn[l] = q;
+      vn[tl.row0 + lr] = q;
     }
     flush_ev(ev, &s->sc->ev[IGM_EV_L11]);
     flush_ev(evr, &s->sc->ev[IGM_EV_VRANGE]);
@@ -220,8 +246,8 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) f_mgs_step(BatchDev B, int j
     // this CTA's partials of every system start at zero
     for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) *cpart_at(B, slot, blockIdx.x, s) = 0.0;
     __syncthreads();
-    for (int t = blockIdx.x; t < B.ntiles; t += G) {
-      Tile tl = B.tiles[t];
+    for (int t = blockIdx.x; t < B.nstiles; t += G) {
+      Tile tl = B.stiles[t];
       const SysDev *s = B.sys[tl.sys];
       if (!m_step(s, j)) continue;
       const int n = s->n;
@@ -257,8 +283,8 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) f_mgs_step(BatchDev B, int j
       }
   }
   const int slot = (j + 1) % 3;
-  for (int t = blockIdx.x; t < B.ntiles; t += G) {
-    Tile tl = B.tiles[t];
+  for (int t = blockIdx.x; t < B.nstiles; t += G) {
+    Tile tl = B.stiles[t];
     const SysDev *s = B.sys[tl.sys];
     if (!m_step(s, j)) continue;
     __syncthreads();
@@ -330,7 +356,7 @@ int persistent_grid(int ntiles) {
 }
 
 void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
-  int G = persistent_grid(B.ntiles);
+  int G = persistent_grid(B.nstiles);
   BatchDev b = B;
   void *args[] = {&b, &j};
   cudaLaunchCooperativeKernel((const void *)f_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);
@@ -338,7 +364,7 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
 }
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
-  int G = persistent_grid(B.ntiles);
+  int G = persistent_grid(B.nstiles);
   BatchDev b = B;
   void *args[] = {&b, &j};
   cudaLaunchCooperativeKernel((const void *)k_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);

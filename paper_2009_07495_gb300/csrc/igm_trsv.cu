@@ -228,13 +228,15 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
         y = (V)__ddiv_rn((double)acc, (double)rr.diag);
       }
       out[rr.i] = y;
-      if (use_smem) sv[p - first] = y;
+      // shared slots are indexed by the row's natural position in the chunk
+      // (the order inside a level group is arbitrary)
+      if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
     }
+    // every writer orders its stores at GPU scope before the CTA barrier, so
+    // that the progress word released after it covers the whole level
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
-    }
+    if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
   }
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
 }
@@ -265,8 +267,12 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
       int end = rowptr[i + 1];
       for (int kk = rowptr[i]; kk < diagpos[i]; ++kk) {
         int k = col[kk];
-        if (!single && k < first) wait_prog(T.prog + k / R, ep | (u64)(T.lev[k] + 1), err);
-        double ukk = __ldcg(f + diagpos[k]);
+        // row k: finished at an earlier level of this CTA (ordinary loads,
+        // visible after the CTA barrier) or in an earlier chunk (L2 loads
+        // after the acquire of its progress word)
+        const bool ext = k < first;
+        if (!single && ext) wait_prog(T.prog + k / R, ep | (u64)(T.lev[k] + 1), err);
+        double ukk = ext ? __ldcg(f + diagpos[k]) : f[diagpos[k]];
         if (ukk == 0.0) {
           atomicOr(err, ERR_ZERO_PIVOT);
           break;
@@ -277,16 +283,15 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
         for (int jj = kk + 1; jj < end; ++jj) {
           int jc = col[jj];
           while (q < qe && col[q] < jc) ++q;
-          if (q < qe && col[q] == jc) f[jj] = __dsub_rn(f[jj], __dmul_rn(lik, __ldcg(f + q)));
+          if (q < qe && col[q] == jc)
+            f[jj] = __dsub_rn(f[jj], __dmul_rn(lik, ext ? __ldcg(f + q) : f[q]));
         }
       }
       if (f[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
     }
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
-    }
+    if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
   }
 }
 
