@@ -338,7 +338,8 @@ def norm2(x, stream=None) -> float:
     """The reproducible 2-norm of Fig. 1's test (igm_norm2)."""
     b = _Buf(x, np.float64)
     out = C.c_double(0)
-    _check(load().igm_norm2(b.ptr, b.len, C.addressof(out), _stream_ptr(stream, b)))
+    _check(load().igm_norm2(b.ptr if b.len else None, b.len, C.addressof(out),
+                            _stream_ptr(stream, b)))
     return out.value
 
 

@@ -398,6 +398,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     Arena &A2 = h->arena2;
     int *ord[2], *lptr[2], *levb[2], *lev[2], *need[2], *pcol[2], *chmax, *cnt;
     i64 *pfac[2], *pdiag[2];
+    double *pdinv[2];
     double *pfacd[2] = {nullptr, nullptr}, *pdiagd[2] = {nullptr, nullptr};
     u64 *prog[2];
     for (int tr = 0; tr < 2; ++tr) {
@@ -410,6 +411,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       A2.want(&pcol[tr], K * n);
       A2.want(&pfac[tr], K * n);
       A2.want(&pdiag[tr], n);
+      A2.want(&pdinv[tr], n);
       A2.want(&prog[tr], nch);
       if (fp) {
         A2.want(&pfacd[tr], K * n);
@@ -456,6 +458,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       T.pcol = pcol[tr];
       T.pfac = pfac[tr];
       T.pdiag = pdiag[tr];
+      T.pdinv = pdinv[tr];
       T.pfacd = pfacd[tr];
       T.pdiagd = tr == 1 ? pdiagd[tr] : nullptr;
       T.prog = prog[tr];
@@ -469,7 +472,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
     for (int tr = 0; tr < 2; ++tr)
       launch_pack(n, rp, cl, dp, tr == 0, d.tri[tr].K, ord[tr], fac, ld, ud, f, pcol[tr], pfac[tr],
-                  pdiag[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
+                  pdiag[tr], pdinv[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
     CKH(cudaGetLastError());
     CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));
@@ -739,7 +742,7 @@ long long igm_kernel_launches(void) { return g_launches.load(); }
 
 igm_status igm_norm2(const double *x, int n, double *out, void *stream) {
   g_err.clear();
-  if (!x || !out || n < 0) return fail(IGM_EINVAL, "bad arguments");
+  if (!out || n < 0 || (n > 0 && !x)) return fail(IGM_EINVAL, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   static std::mutex mu;
   static long long *ws = nullptr;
@@ -771,8 +774,10 @@ igm_status igm_norm2(const double *x, int n, double *out, void *stream) {
   // the counter words sit right after the partials of this call's grid
   const double *xd = x;
   cudaPointerAttributes pa;
-  if (cudaPointerGetAttributes(&pa, x) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
-      pa.type == cudaMemoryTypeUnregistered) {
+  if (n == 0) {
+    xd = buf + 2;
+  } else if (cudaPointerGetAttributes(&pa, x) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
+             pa.type == cudaMemoryTypeUnregistered) {
     cudaGetLastError();
     if (n > 0) CK(cudaMemcpyAsync(buf + 2, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     xd = buf + 2;

@@ -60,6 +60,27 @@ __device__ __forceinline__ i64 divt(i64 a, i64 b, unsigned &ev) {
   return a / b;
 }
 
+// a / d truncated toward zero, exactly, for d != 0, from an FP64 estimate
+// a * dinv (dinv = 1/d) corrected with the exact int128 remainder.  The
+// estimate's relative error is below 2^-51, so for |a/d| < 2^50 it is within
+// one of the quotient; larger quotients take the integer division.  Same
+// result and events as divt.
+__device__ __forceinline__ i64 divt_rcp(i64 a, i64 d, double dinv, unsigned &ev) {
+  const double qe = __dmul_rn((double)a, dinv);
+  if (!(fabs(qe) < 1125899906842624.0)) return divt(a, d, ev);  // 2^50
+  i64 q = __double2ll_rz(qe);
+  i128 r = (i128)a - (i128)q * (i128)d;
+  const i64 ad = d < 0 ? -d : d, sd = d < 0 ? -1 : 1;
+  if (a >= 0) {
+    while (r < 0) { q -= sd; r += ad; }
+    while (r >= ad) { q += sd; r -= ad; }
+  } else {
+    while (r > 0) { q += sd; r -= ad; }
+    while (-r >= ad) { q -= sd; r += ad; }
+  }
+  return q;
+}
+
 // floor(sqrt(s)) for s >= 0 (0 for s <= 0): FP64 estimate, then exact
 // integer correction.
 __device__ __forceinline__ i64 isqrt64(i64 s) {

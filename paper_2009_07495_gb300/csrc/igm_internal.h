@@ -68,6 +68,7 @@ struct SysScal {
 struct Tri {
   const int *ord, *lptr, *levb, *lev, *need, *pcol;
   const i64 *pfac, *pdiag;
+  const double *pdinv;          // 1 / pdiag (FP64 estimate of the divisions)
   const double *pfacd, *pdiagd;
   u64 *prog;                    // per chunk: (epoch << 32) | levels done
   int nchunk, K;

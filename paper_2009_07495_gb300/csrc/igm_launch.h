@@ -24,8 +24,8 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
                     cudaStream_t st);
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
                  const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pfacd,
-                 double *pdiagd, cudaStream_t st);
+                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                 double *pfacd, double *pdiagd, cudaStream_t st);
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
                  const int *ord, const int *levb, const int *lev, int *need, cudaStream_t st);
 // substitutions: kind 0 integer (line 5'), 1 FP64 on the integer factors
@@ -55,6 +55,9 @@ void launch_update(const BatchDev &B, cudaStream_t st);
 int norm2_grid(int n);
 void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out,
                   cudaStream_t st);
+// the same with an explicit grid (ws: 2*g partial words + 2 counter words)
+void launch_norm2_grid(const double *x, int n, int g, long long *ws, double *mx, double *out,
+                       cudaStream_t st);
 void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st);
 
 // FP64 GMRES(m) comparison solver (lines 1-23 after line 1's residual)

@@ -373,11 +373,15 @@ int norm2_grid(int n) {
 
 // ws: 2*norm2_grid(n) + 2 int64 words whose last two start at zero (the
 // kernels leave them at zero); mx: one double of scratch
-void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out,
-                  cudaStream_t st) {
-  int g = norm2_grid(n);
+void launch_norm2_grid(const double *x, int n, int g, long long *ws, double *mx, double *out,
+                       cudaStream_t st) {
   k_vmax<<<g, IGM_BLOCK, 0, st>>>(x, n, ws, mx);
   k_vnorm<<<g, IGM_BLOCK, 0, st>>>(x, n, ws, mx, out);
+}
+
+void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out,
+                  cudaStream_t st) {
+  launch_norm2_grid(x, n, norm2_grid(n), ws, mx, out, st);
 }
 
 // per-system {active, status, error bits, refinements} for the host

@@ -39,8 +39,8 @@ __global__ void s_maxdeps(int n, const int *rowptr, const int *diagpos, int lowe
 // packs the strict part of the row at each position, dependency-major
 __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
                        int K, const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                       const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pfacd,
-                       double *pdiagd) {
+                       const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                       double *pfacd, double *pdiagd) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     int i = ord[p];
     int k0 = lower ? rowptr[i] : diagpos[i] + 1;
@@ -53,6 +53,7 @@ __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diag
       if (pfacd) pfacd[(size_t)q * n + p] = in ? f[k] : 0.0;
     }
     pdiag[p] = lower ? ldiag[i] : udiag[i];
+    pdinv[p] = 1.0 / (double)pdiag[p];
     if (pdiagd) pdiagd[p] = f[diagpos[i]];
   }
 }
@@ -104,12 +105,13 @@ struct RowPre {
   V fac[IGM_TRSV_KC];
   V diag;
   V rhs;
+  double dinv;
 };
 
 template <int KIND>
-__device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, int p,
+__device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, int p, int row,
                                          const typename TrsvT<KIND>::V *in) {
-  r.i = T.ord[p];
+  r.i = row;
 #pragma unroll
   for (int q = 0; q < IGM_TRSV_KC; ++q) {
     if (q < T.K) {
@@ -121,8 +123,10 @@ __device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, i
       r.col[q] = -1;
     }
   }
-  if (KIND == TK_INT) r.diag = T.pdiag[p];
-  else if (KIND == TK_FPI) r.diag = (double)T.pdiag[p];
+  if (KIND == TK_INT) {
+    r.diag = T.pdiag[p];
+    r.dinv = T.pdinv[p];
+  } else if (KIND == TK_FPI) r.diag = (double)T.pdiag[p];
   else r.diag = T.pdiagd ? T.pdiagd[p] : 1.0;
   r.rhs = in[r.i];
 }
@@ -133,6 +137,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
   typedef typename TrsvT<KIND>::V V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *sv = reinterpret_cast<V *>(smem_raw);
+  int *sord = reinterpret_cast<int *>(smem_raw + (size_t)smem_rows * sizeof(V));
   __shared__ int s_t;
   const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
   if (threadIdx.x == 0) s_t = (int)atomicAdd(&B.ticket[tk], 1u);
@@ -163,10 +168,17 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
   const bool single = s->single_pred != 0;
   unsigned ev = 0;
 
+  // the chunk's rows in level order, staged once so that prefetching a row
+  // never waits on the order array
+  if (use_smem)
+    for (int q = threadIdx.x; q < last - first; q += blockDim.x) sord[q] = T.ord[first + q];
+  __syncthreads();
+#define ROW_OF(pp) (use_smem ? sord[(pp) - first] : T.ord[pp])
+
   RowPre<KIND> cur, nxt;
   int pn = T.lptr[g0] + threadIdx.x;
   bool has_nxt = pn < T.lptr[g0 + 1];
-  if (has_nxt) row_load<KIND>(nxt, T, n, pn, in);
+  if (has_nxt) row_load<KIND>(nxt, T, n, pn, ROW_OF(pn), in);
 
   for (int g = g0; g < g1; ++g) {
     const int p0 = T.lptr[g], p1 = T.lptr[g + 1];
@@ -176,7 +188,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
     if (g + 1 < g1) {
       pn = T.lptr[g + 1] + threadIdx.x;
       has_nxt = pn < T.lptr[g + 2];
-      if (has_nxt) row_load<KIND>(nxt, T, n, pn, in);
+      if (has_nxt) row_load<KIND>(nxt, T, n, pn, ROW_OF(pn), in);
     } else {
       has_nxt = false;
     }
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
       RowPre<KIND> rr;
       if (p == p0 + (int)threadIdx.x && has_cur) rr = cur;
-      else row_load<KIND>(rr, T, n, p, in);
+      else row_load<KIND>(rr, T, n, p, ROW_OF(p), in);
       typedef typename std::conditional<KIND == TK_INT, i128, double>::type A;
       A acc = (A)rr.rhs;
       for (int q = 0; q < T.K; ++q) {
@@ -221,7 +233,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
       V y;
       if (KIND == TK_INT) {
         ev += out64((i128)acc);
-        y = (V)divt(wrap((i128)acc), (i64)rr.diag, ev);
+        y = (V)divt_rcp(wrap((i128)acc), (i64)rr.diag, rr.dinv, ev);
       } else if (KIND == TK_FP && lower) {
         y = (V)acc;  // unit lower factor
       } else {
@@ -232,13 +244,13 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
       // (the order inside a level group is arbitrary)
       if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
     }
-    // every writer orders its stores at GPU scope before the CTA barrier, so
-    // that the progress word released after it covers the whole level
-    __threadfence();
+    // the release by one thread after the CTA barrier covers every thread's
+    // stores of the level (release is cumulative over the barrier)
     __syncthreads();
     if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
   }
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
+#undef ROW_OF
 }
 
 // ---------------------------------------------------------------------------
@@ -289,7 +301,6 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
       }
       if (f[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
   }
@@ -309,10 +320,10 @@ void launch_maxdeps(int n, const int *rowptr, const int *diagpos, int lower, int
 
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
                  const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pfacd,
-                 double *pdiagd, cudaStream_t st) {
+                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                 double *pfacd, double *pdiagd, cudaStream_t st) {
   s_pack<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, K, ord, fac, ldiag, udiag, f,
-                                     pcol, pfac, pdiag, pfacd, pdiagd);
+                                     pcol, pfac, pdiag, pdinv, pfacd, pdiagd);
 }
 
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
@@ -327,20 +338,21 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
                                                  epoch, err);
 }
 
-// shared memory for a chunk's values: the chunk if it fits in 160 KB
-static int smem_rows_for(int bytes_per) { return (160 * 1024) / bytes_per; }
+// shared memory for a chunk's values and order: the chunk if it fits in
+// 200 KB
+static int smem_rows_for(int bytes_per) { return (200 * 1024) / bytes_per; }
 
 template <int KIND>
 static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cudaStream_t st) {
   if (B.nctiles <= 0) return;
-  const int bper = 8;
+  const int bper = 8 + 4;  // a value and an order entry per row
   int rows = smem_rows_for(bper);
   if (rows > max_chunk) rows = max_chunk;
   size_t sm = (size_t)rows * bper;
   static bool attr_set[3] = {false, false, false};
   if (!attr_set[KIND]) {
     cudaFuncSetAttribute(k_trsv_lv<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         160 * 1024);
+                         200 * 1024);
     attr_set[KIND] = true;
   }
   k_trsv_lv<KIND><<<B.nctiles, IGM_TRSV_BLOCK, sm, st>>>(B, lower, which, rows);
