@@ -165,6 +165,21 @@ igm_status int_gmres_get_state(igm_handle h, long long *V, long long *H,
  * largest n seen.  Errors: IGM_EINVAL, IGM_EOOM, IGM_ECUDA. */
 igm_status igm_norm2(const double *x, int n, double *out, void *stream);
 
+/* igm_norm2 for callers that cannot allocate device memory (a stream being
+ * captured into a CUDA graph, a process whose device memory belongs to
+ * another allocator, a latency-critical loop).  The paper has no
+ * counterpart: this is an operational variant of the same computation.
+ * Scratch (per-CTA partial sums and counters, 32 KB) lives in a static
+ * device array held by every GPU that loads the library until the process
+ * exits; the call allocates nothing.  x: n doubles and out: one double,
+ * both already in device (or managed) memory; 0 <= n <= 8,388,608, larger n
+ * is rejected with IGM_EINVAL.  The first call on each device resolves the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams
+ * or threads on the same device) race; calls on one stream are ordered.
+ * The result is written on `stream` (no synchronisation). */
+igm_status igm_norm2_noalloc(const double *x, int n, double *out, void *stream);
+
 /* Kernels that igm_time_kernels can time (one launch each, on the handle's
  * current state, in the launch configuration of the solver). */
 enum {

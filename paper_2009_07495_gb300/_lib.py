@@ -95,6 +95,7 @@ def _declare(lib):
         "igm_time_kernels": (_I, [_VP, _I, C.POINTER(C.c_double), _VP]),
         "igm_kernel_launches": (C.c_longlong, []),
         "igm_norm2": (_I, [_VP, _I, _VP, _VP]),
+        "igm_norm2_noalloc": (_I, [_VP, _I, _VP, _VP]),
         "int_gmres_destroy": (None, [_VP]),
         "igm_server_create": (_I, [C.POINTER(ServerConfig), C.POINTER(_VP)]),
         "igm_server_submit": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, C.POINTER(Params),
