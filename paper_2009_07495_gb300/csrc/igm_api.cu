@@ -78,6 +78,16 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   u64 *d_acc;
   double *d_cpart;
   int maxg = persistent_grid(ST);
+  std::vector<int> sysn(ns);
+  for (int s = 0; s < ns; ++s) sysn[s] = hs[s]->n;
+  int mgs_g = 1, mgs_wrows = 0;
+  std::vector<int> mptr;
+  std::vector<Tile> mseg;
+  mgs_plan(sysn, persistent_grid(1 << 30), mgs_g, mptr, mseg, mgs_wrows);
+  const int MS = (int)mseg.size();
+  int *d_mptr;
+  Tile *d_mseg;
+  long long *d_mh;
   b->arena.want(&d_tiles, T);
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
   b->arena.want(&d_stiles, ST);
@@ -90,6 +100,9 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   b->arena.want(&d_partd, T);
   b->arena.want(&d_ticket, 4);
   b->arena.want(&d_nact, 1);
+  b->arena.want(&d_mptr, mgs_g + 1);
+  b->arena.want(&d_mseg, MS > 0 ? MS : 1);
+  b->arena.want(&d_mh, MS > 0 ? MS : 1);
   if (b->arena.commit() != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -104,9 +117,32 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   CK(cudaMemset(d_nact, 0, sizeof(int)));
   CK(cudaMemset(d_bar, 0, 2 * sizeof(unsigned)));
   CK(cudaMemset(d_acc, 0, 6 * sizeof(u64) * ns));
-  b->bd = BatchDev{ns,    T,        ST,      d_stiles, CT,     d_ctiles, d_sp,  d_tiles,
-                   d_snt, d_part,   d_partd, d_ticket, d_nact, d_bar,    d_acc, d_cpart,
-                   maxg};
+  CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (mgs_g + 1), cudaMemcpyHostToDevice));
+  if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
+  BatchDev &B = b->bd;
+  B = BatchDev{};
+  B.nsys = ns;
+  B.ntiles = T;
+  B.nstiles = ST;
+  B.stiles = d_stiles;
+  B.nctiles = CT;
+  B.ctiles = d_ctiles;
+  B.sys = d_sp;
+  B.tiles = d_tiles;
+  B.sys_ntiles = d_snt;
+  B.part = d_part;
+  B.partd = d_partd;
+  B.ticket = d_ticket;
+  B.nact = d_nact;
+  B.bar = d_bar;
+  B.acc = d_acc;
+  B.cpart = d_cpart;
+  B.maxg = maxg;
+  B.mgs_g = mgs_g;
+  B.mseg_ptr = d_mptr;
+  B.mseg = d_mseg;
+  B.mseg_h = d_mh;
+  B.mgs_wrows = mgs_wrows;
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;

@@ -27,11 +27,25 @@ __device__ __forceinline__ i64 shr(i64 x, int s) {
   return x >> s;
 }
 
+// wrapped product of two words; an event when the exact product leaves
+// int64, i.e. when its high word is not the sign extension of the low one
 __device__ __forceinline__ i64 mulw(i64 a, i64 b, unsigned &ev) {
-  i128 p = (i128)a * (i128)b;
-  ev += out64(p);
-  return wrap(p);
+  const i64 lo = (i64)((u64)a * (u64)b);
+  const i64 hi = __mul64hi(a, b);
+  ev += (hi != (lo >> 63));
+  return lo;
 }
+
+// wrapped a - b; an event when the exact difference leaves int64
+__device__ __forceinline__ i64 subw(i64 a, i64 b, unsigned &ev) {
+  const i64 d = (i64)((u64)a - (u64)b);
+  ev += (((a ^ b) & (a ^ d)) < 0);
+  return d;
+}
+
+// a right-shift amount clamped to [0, 63]: x >> shc(s) is floor(x / 2^s)
+// for every s >= 0 (and |x| < 2^63)
+__device__ __forceinline__ int shc(int s) { return s < 0 ? 0 : (s > 63 ? 63 : s); }
 
 __device__ __forceinline__ i64 negw(i64 a, unsigned &ev) {
   ev += (a == INT64_MIN);

@@ -122,6 +122,14 @@ struct BatchDev {
   u64 *acc;                // 3 slots x nsys x {lo, hi}: exact int128 sums
   double *cpart;           // 3 slots x maxG x nsys FP64 per-CTA partials
   int maxg;                // CTAs of the persistent kernels
+  // integer Arnoldi step: CTA c sweeps the segments
+  // mseg[mseg_ptr[c] .. mseg_ptr[c+1]), contiguous row ranges of one system
+  // each ({sys, row0, nrows, offset of the rows in the CTA's copy of w})
+  int mgs_g;               // its CTAs
+  const int *mseg_ptr;
+  const Tile *mseg;
+  i64 *mseg_h;             // per segment: the coefficient of the next pass
+  int mgs_wrows;           // rows of w each CTA keeps in shared memory (0: global)
 };
 
 // vector selectors for the generic max / norm kernels

@@ -1,5 +1,6 @@
 // igm_launch.h -- host-side launchers of the device kernels (internal).
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/igm.h"
@@ -50,6 +51,9 @@ void launch_spmv(const BatchDev &B, int j, cudaStream_t st);
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 int persistent_grid(int ntiles);  // CTAs of the persistent kernels
+// the row partition of the integer Arnoldi step over systems of sizes n
+void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> &ptr,
+              std::vector<Tile> &seg, int &wrows);
 void launch_backsub(const BatchDev &B, cudaStream_t st);
 void launch_update(const BatchDev &B, cudaStream_t st);
 int norm2_grid(int n);

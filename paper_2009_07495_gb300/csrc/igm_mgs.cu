@@ -7,6 +7,8 @@
 // and the line-7 inner product with v_i; pass j+1 fuses the last update with
 // the line-10 norm; then line 11 and (one thread per system) lines 12-19.
 // The basis streams from HBM once per pass; w stays in L2.
+#include <algorithm>
+
 #include "igm_dev.cuh"
 #include "igm_launch.h"
 
@@ -67,13 +69,80 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
   return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
 }
 
-#define IGM_RPT (IGM_STILE / IGM_MGS_BLOCK)  // rows per thread in a super-tile
+#define IGM_RPT 4           // rows in flight per thread
+#define IGM_MSEG_CACHE 64   // segment descriptors a CTA keeps in shared memory
+#define IGM_MGS_WMAX 20480  // rows of w a CTA may keep in shared memory (160 KB)
 
+// a segment as the step kernel sees it: its system's arrays and shifts
+struct MSegC {
+  i64 *V;  // basis of the system
+  i64 *w;        // the segment's first row of w
+  i64 *H;
+  SysScal *sc;
+  int n, row0, nrows, off, sys, ld;
+  int df, b7, b8, b10, b11a, b11b;
+  int first;   // holds row 0 of its system: records h_{i,j} and its events
+  int active;  // the system takes this step
+};
+
+__device__ __forceinline__ void mseg_make(const BatchDev &B, int g, int j, MSegC &c) {
+  const Tile t = B.mseg[g];
+  const SysDev *s = B.sys[t.sys];
+  const SysParams &P = s->p;
+  c.V = s->V;
+  c.w = s->w + t.row0;
+  c.H = s->H;
+  c.sc = s->sc;
+  c.n = s->n;
+  c.row0 = t.row0;
+  c.nrows = t.nrows;
+  c.off = t.first;
+  c.sys = t.sys;
+  c.ld = s->ld;
+  c.df = P.df;
+  c.b7 = P.b7;
+  c.b8 = P.b8;
+  c.b10 = P.b10;
+  c.b11a = P.b11a;
+  c.b11b = P.b11b;
+  c.first = t.row0 == 0;
+  c.active = m_step(s, j);
+}
+
+// after the barrier of pass i: the exact total of the pass; h_{i,j} (line 7)
+// or h_{j+1,j} (line 10), recorded once per system with the total's event;
+// returns the coefficient pass i+1 needs (line 8) or h_{j+1,j}
+__device__ __forceinline__ i64 mseg_total(const BatchDev &B, const MSegC &c, int i, int j) {
+  const i128 tot = acc_load(acc_slot(B, i % 3, c.sys));
+  unsigned e = out64(tot);
+  if (i <= j) {
+    const i64 h = shr(wrap(tot), c.df - c.b7);
+    if (c.first) {
+      c.H[i + j * c.ld] = h;
+      if (e) atomicAdd(&c.sc->ev[IGM_EV_L7], (u64)e);
+    }
+    return shr(h, c.b8);
+  }
+  const i64 h = fx_sqrt(wrap(tot), 2 * c.df - 2 * c.b10, c.df, e);
+  if (c.first && e) atomicAdd(&c.sc->ev[IGM_EV_L10], (u64)e);
+  return h;
+}
+
+// Every CTA owns the same rows in every pass (a balanced partition of all
+// systems' rows, planned on the host); when they fit, its rows of w stay in
+// shared memory from pass 0 to line 11, so a pass reads only the two basis
+// vectors it needs (v_i from HBM, v_{i-1} mostly from L2).
 __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j) {
-  const int G = gridDim.x;
+  extern __shared__ i64 sw[];  // this CTA's rows of w (B.mgs_wrows > 0)
+  __shared__ MSegC s_seg[IGM_MSEG_CACHE + 1];
+  __shared__ i64 s_h[IGM_MSEG_CACHE];
   unsigned *err0 = &B.sys[0]->sc->err;
+  const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
+  const bool wsm = B.mgs_wrows > 0;
+  for (int k = threadIdx.x; k < ns && k < IGM_MSEG_CACHE; k += blockDim.x)
+    mseg_make(B, g0 + k, j, s_seg[k]);
+  __syncthreads();
   for (int i = 0; i <= j + 1; ++i) {
-    const int slot = i % 3;
     // slot (i+1)%3 was last read right after barrier i-2, before barrier i-1
     if (blockIdx.x == 0)
       for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
@@ -81,118 +150,98 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
         a[0] = 0;
         a[1] = 0;
       }
-    // a CTA's super-tiles of one system are consecutive: their partial sums
-    // are combined in registers and published once per system
-    int cur = -1;
-    i128 part = 0;
-    unsigned evA = 0, evB = 0;
-    i64 hs = 0;
-    for (int t = blockIdx.x;; t += G) {
-      const bool end = t >= B.nstiles;
-      Tile tl = end ? Tile{-1, 0, 0, 0} : B.stiles[t];
-      if (tl.sys != cur && cur >= 0) {
-        SysScal *csc = B.sys[cur]->sc;
-        flush_ev(evB, &csc->ev[IGM_EV_L8]);
-        flush_ev(evA, &csc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
-        part = block_sum_i128(part);
-        if (threadIdx.x == 0) acc_add(acc_slot(B, slot, cur), part);
-        part = 0;
-        evA = evB = 0;
-        cur = -1;
+    for (int k = 0; k < ns; ++k) {
+      if (k >= IGM_MSEG_CACHE) {  // descriptor beyond the cache: one spare slot
+        __syncthreads();
+        if (threadIdx.x == 0) mseg_make(B, g0 + k, j, s_seg[IGM_MSEG_CACHE]);
+        __syncthreads();
       }
-      if (end) break;
-      const SysDev *s = B.sys[tl.sys];
-      if (!m_step(s, j)) continue;
-      const SysParams &P = s->p;
-      const int n = s->n, df = P.df;
-      if (cur != tl.sys) {
-        cur = tl.sys;
-        // h_{i-1,j} from the previous pass's exact sum
-        hs = 0;
-        if (i > 0) {
-          i128 tot = acc_load(acc_slot(B, (i - 1) % 3, tl.sys));
-          hs = shr(shr(wrap(tot), df - P.b7), P.b8);
-        }
-      }
-      const i64 *vp = s->V + (size_t)(i > 0 ? i - 1 : 0) * n;
-      const i64 *vi = s->V + (size_t)(i <= j ? i : 0) * n;
-      i64 *w = s->w;
-      // all loads of the thread's rows first (memory-level parallelism)
-      i64 wv[IGM_RPT], pv[IGM_RPT], qv[IGM_RPT];
+      const MSegC &c = s_seg[k < IGM_MSEG_CACHE ? k : IGM_MSEG_CACHE];
+      if (!c.active) continue;
+      const i64 hs = i == 0 ? 0 : (k < IGM_MSEG_CACHE ? s_h[k] : B.mseg_h[g0 + k]);
+      const int nr = c.nrows;
+      const i64 *vp = c.V + (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
+      const i64 *vi = c.V + (size_t)(i <= j ? i : 0) * c.n + c.row0;
+      i64 *wg = c.w, *ws = sw + c.off;
+      const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
+      i128 part = 0;
+      unsigned evA = 0, evB = 0;
+      for (int q0 = threadIdx.x; q0 < nr; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+        // all loads of the thread's rows first (memory-level parallelism)
+        i64 wv[IGM_RPT], pv[IGM_RPT], qv[IGM_RPT];
 #pragma unroll
-      for (int u = 0; u < IGM_RPT; ++u) {
-        const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
-        const int l = tl.row0 + lr;
-        const bool ok = lr < tl.nrows;
-        wv[u] = ok ? w[l] : 0;
-        pv[u] = (ok && i > 0) ? vp[l] : 0;
-        qv[u] = (ok && i <= j) ? vi[l] : 0;
-      }
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * IGM_MGS_BLOCK;
+          const bool ok = q < nr;
+          wv[u] = ok ? ((wsm && i > 0) ? ws[q] : wg[q]) : 0;
+          pv[u] = (ok && i > 0) ? vp[q] : 0;
+          qv[u] = (ok && i <= j) ? vi[q] : 0;
+        }
 #pragma unroll
-      for (int u = 0; u < IGM_RPT; ++u) {
-        const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
-        if (lr >= tl.nrows) continue;
-        i64 wl = wv[u];
-        if (i > 0) {
-          i64 p = shr(mulw(hs, pv[u], evB), df - P.b8);
-          i128 d = (i128)wl - (i128)p;
-          evB += out64(d);
-          wl = wrap(d);
-          w[tl.row0 + lr] = wl;
-        }
-        if (i <= j) {
-          part += (i128)mulw(shr(wl, P.b7), qv[u], evA);
-        } else {
-          i64 a = shr(wl, P.b10);
-          part += (i128)mulw(a, a, evA);
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * IGM_MGS_BLOCK;
+          if (q >= nr) continue;
+          i64 wl = wv[u];
+          if (i > 0) wl = subw(wl, mulw(hs, pv[u], evB) >> s8, evB);
+          if (wsm) ws[q] = wl;
+          else if (i > 0) wg[q] = wl;
+          if (i <= j) {
+            part += (i128)mulw(wl >> s7, qv[u], evA);
+          } else {
+            const i64 a = wl >> s10;
+            part += (i128)mulw(a, a, evA);
+          }
         }
       }
+      flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
+      flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+      part = block_sum_i128(part);
+      if (threadIdx.x == 0) acc_add(acc_slot(B, i % 3, c.sys), part);
     }
     if (!grid_sync(B.bar, err0)) return;
-    // one thread records h_{i,j} (and the total's overflow event) per system
-    if (blockIdx.x == 0)
-      for (int sidx = threadIdx.x; sidx < B.nsys; sidx += blockDim.x) {
-        const SysDev *s = B.sys[sidx];
-        if (!m_step(s, j)) continue;
-        const SysParams &P = s->p;
-        i128 tot = acc_load(acc_slot(B, slot, sidx));
-        unsigned e = out64(tot);
-        if (i <= j) {
-          s->H[i + j * s->ld] = shr(wrap(tot), P.df - P.b7);
-          if (e) atomicAdd(&s->sc->ev[IGM_EV_L7], (u64)e);
-        } else {
-          (void)fx_sqrt(wrap(tot), 2 * P.df - 2 * P.b10, P.df, e);
-          if (e) atomicAdd(&s->sc->ev[IGM_EV_L10], (u64)e);
-        }
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      if (k < IGM_MSEG_CACHE) {
+        if (s_seg[k].active) s_h[k] = mseg_total(B, s_seg[k], i, j);
+      } else {
+        MSegC c;
+        mseg_make(B, g0 + k, j, c);
+        if (c.active) B.mseg_h[g0 + k] = mseg_total(B, c, i, j);
       }
+    }
+    __syncthreads();
   }
   // line 11 for every system whose divisor is non-zero
-  const int slot = (j + 1) % 3;
-  for (int t = blockIdx.x; t < B.nstiles; t += G) {
-    Tile tl = B.stiles[t];
-    const SysDev *s = B.sys[tl.sys];
-    if (!m_step(s, j)) continue;
-    const SysParams &P = s->p;
-    unsigned e10 = 0, ev = 0, evr = 0;
-    i64 hn = fx_sqrt(wrap(acc_load(acc_slot(B, slot, tl.sys))), 2 * P.df - 2 * P.b10, P.df, e10);
-    if (shr(hn, P.b11b) == 0) continue;
-    i64 *vn = s->V + (size_t)(j + 1) * s->n;
-    i64 wv[IGM_RPT];
-#pragma unroll
-    for (int u = 0; u < IGM_RPT; ++u) {
-      const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
-      wv[u] = lr < tl.nrows ? s->w[tl.row0 + lr] : 0;
+  for (int k = 0; k < ns; ++k) {
+    if (k >= IGM_MSEG_CACHE) {
+      __syncthreads();
+      if (threadIdx.x == 0) mseg_make(B, g0 + k, j, s_seg[IGM_MSEG_CACHE]);
+      __syncthreads();
     }
+    const MSegC &c = s_seg[k < IGM_MSEG_CACHE ? k : IGM_MSEG_CACHE];
+    if (!c.active) continue;
+    const i64 hn = k < IGM_MSEG_CACHE ? s_h[k] : B.mseg_h[g0 + k];
+    if (shr(hn, c.b11b) == 0) continue;
+    i64 *vn = c.V + (size_t)(j + 1) * c.n + c.row0;
+    const i64 *wg = c.w, *ws = sw + c.off;
+    unsigned ev = 0, evr = 0;
+    for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+      i64 wv[IGM_RPT];
 #pragma unroll
-    for (int u = 0; u < IGM_RPT; ++u) {
-      const int lr = threadIdx.x + u * IGM_MGS_BLOCK;
-      if (lr >= tl.nrows) continue;
-      i64 q = fx_div(wv[u], hn, P.b11a, P.b11b, P.df, ev);
-      evr += (q < INT32_MIN || q > INT32_MAX);
-      vn[tl.row0 + lr] = q;
+      for (int u = 0; u < IGM_RPT; ++u) {
+        const int q = q0 + u * IGM_MGS_BLOCK;
+        wv[u] = q < c.nrows ? (wsm ? ws[q] : wg[q]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < IGM_RPT; ++u) {
+        const int q = q0 + u * IGM_MGS_BLOCK;
+        if (q >= c.nrows) continue;
+        const i64 v = fx_div(wv[u], hn, c.b11a, c.b11b, c.df, ev);
+        evr += (v < INT32_MIN || v > INT32_MAX);
+        vn[q] = v;
+      }
     }
-    flush_ev(ev, &s->sc->ev[IGM_EV_L11]);
-    flush_ev(evr, &s->sc->ev[IGM_EV_VRANGE]);
+    flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
+    flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
   }
 }
 
@@ -363,11 +412,46 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   f_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j, G);
 }
 
+void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> &ptr,
+              std::vector<Tile> &seg, int &wrows) {
+  long long N = 0;
+  for (int v : n) N += v;
+  long long g = (N + IGM_MGS_BLOCK - 1) / IGM_MGS_BLOCK;
+  if (g > max_ctas) g = max_ctas;
+  G = (int)(g < 1 ? 1 : g);
+  ptr.assign(G + 1, 0);
+  seg.clear();
+  int s = 0, maxrows = 0;
+  long long base = 0;  // first global row of system s
+  for (int c = 0; c < G; ++c) {
+    const long long lo = N * c / G, hi = N * (c + 1) / G;
+    ptr[c] = (int)seg.size();
+    int off = 0;
+    for (long long r = lo; r < hi;) {
+      while (r >= base + n[s]) base += n[s++];
+      const long long e = std::min(hi, base + n[s]);
+      seg.push_back(Tile{s, (int)(r - base), (int)(e - r), off});
+      off += (int)(e - r);
+      r = e;
+    }
+    maxrows = std::max(maxrows, off);
+  }
+  ptr[G] = (int)seg.size();
+  wrows = maxrows <= IGM_MGS_WMAX ? maxrows : 0;
+}
+
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
-  int G = persistent_grid(B.nstiles);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mgs_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IGM_MGS_WMAX * (int)sizeof(i64));
+    attr = true;
+  }
+  int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};
-  cudaLaunchCooperativeKernel((const void *)k_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);
+  cudaLaunchCooperativeKernel((const void *)k_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args,
+                              (size_t)B.mgs_wrows * sizeof(i64), st);
   k_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j);
   k_acc_clear<<<(B.nsys + 255) / 256, 256, 0, st>>>(B);
 }
