@@ -47,6 +47,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   std::vector<SysDev *> sp(ns);
   b->m = hs[0]->prm.m;
   b->inner = hs[0]->prm.inner;
+  int maxlev = 1, maxw = 1, maxk = 0;
   for (int s = 0; s < ns; ++s) {
     igm_handle h = hs[s];
     if (h->prm.m != b->m || h->prm.inner != b->inner) {
@@ -65,6 +66,13 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
     int cfirst = (int)ctiles.size();
     for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
     b->max_chunk = std::max(b->max_chunk, h->hs.chunk);
+    if (h->prm.precond) {
+      for (int tr = 0; tr < 2; ++tr) {
+        maxlev = std::max(maxlev, h->hs.tri[tr].maxlev);
+        maxw = std::max(maxw, h->hs.tri[tr].maxw);
+        maxk = std::max(maxk, h->hs.tri[tr].K);
+      }
+    }
   }
   int CT = (int)ctiles.size(), ST = (int)stiles.size();
   Tile *d_ctiles = nullptr, *d_stiles = nullptr;
@@ -143,6 +151,9 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.mseg = d_mseg;
   B.mseg_h = d_mh;
   B.mgs_wrows = mgs_wrows;
+  B.trsv_maxlev = maxlev;
+  B.trsv_maxw = maxw;
+  B.trsv_maxk = maxk;
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;
@@ -434,7 +445,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     Arena &A2 = h->arena2;
     int *ord[2], *lptr[2], *levb[2], *lev[2], *need[2], *pcol[2], *chmax, *cnt;
     i64 *pfac[2], *pdiag[2];
-    double *pdinv[2];
+    u64 *pdm[2];
     double *pfacd[2] = {nullptr, nullptr}, *pdiagd[2] = {nullptr, nullptr};
     u64 *prog[2];
     for (int tr = 0; tr < 2; ++tr) {
@@ -447,8 +458,8 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       A2.want(&pcol[tr], K * n);
       A2.want(&pfac[tr], K * n);
       A2.want(&pdiag[tr], n);
-      A2.want(&pdinv[tr], n);
-      A2.want(&prog[tr], nch);
+      A2.want(&pdm[tr], n);
+      A2.want(&prog[tr], (size_t)nch * IGM_PROG_STRIDE);
       if (fp) {
         A2.want(&pfacd[tr], K * n);
         A2.want(&pdiagd[tr], n);
@@ -481,9 +492,14 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
                           cudaMemcpyHostToDevice, s));
       CKH(cudaMemsetAsync(cnt, 0, sizeof(int) * (L + 1), s));
       launch_level_order(n, lower, R, L, lev[tr], levb[tr], cnt, lptr[tr], ord[tr], s);
+      int hmaxw = 0;
+      CKH(cudaMemsetAsync(chmax, 0, sizeof(int), s));
+      launch_maxw(L, lptr[tr], chmax, s);
+      CKH(cudaMemcpyAsync(&hmaxw, chmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CKH(cudaStreamSynchronize(s));
       CKH(cudaMemsetAsync(need[tr], 0, sizeof(int) * (L + 1), s));
       launch_need(n, rp, cl, dp, lower, R, ord[tr], levb[tr], lev[tr], need[tr], s);
-      CKH(cudaMemsetAsync(prog[tr], 0, sizeof(u64) * nch, s));
+      CKH(cudaMemsetAsync(prog[tr], 0, sizeof(u64) * nch * IGM_PROG_STRIDE, s));
       CKH(cudaStreamSynchronize(s));
       Tri &T = d.tri[tr];
       T.ord = ord[tr];
@@ -494,12 +510,14 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       T.pcol = pcol[tr];
       T.pfac = pfac[tr];
       T.pdiag = pdiag[tr];
-      T.pdinv = pdinv[tr];
+      T.pdm = pdm[tr];
       T.pfacd = pfacd[tr];
       T.pdiagd = tr == 1 ? pdiagd[tr] : nullptr;
       T.prog = prog[tr];
       T.nchunk = nch;
       T.K = hbw[2 + tr];
+      T.maxlev = 1 + *std::max_element(hmax.begin(), hmax.end());
+      T.maxw = hmaxw;
     }
     // eq. (ilu) on the L schedule (epoch 2), then the integer factors
     CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
@@ -508,7 +526,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
     for (int tr = 0; tr < 2; ++tr)
       launch_pack(n, rp, cl, dp, tr == 0, d.tri[tr].K, ord[tr], fac, ld, ud, f, pcol[tr], pfac[tr],
-                  pdiag[tr], pdinv[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
+                  pdiag[tr], pdm[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
     CKH(cudaGetLastError());
     CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));

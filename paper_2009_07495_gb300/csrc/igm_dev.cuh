@@ -74,25 +74,35 @@ __device__ __forceinline__ i64 divt(i64 a, i64 b, unsigned &ev) {
   return a / b;
 }
 
-// a / d truncated toward zero, exactly, for d != 0, from an FP64 estimate
-// a * dinv (dinv = 1/d) corrected with the exact int128 remainder.  The
-// estimate's relative error is below 2^-51, so for |a/d| < 2^50 it is within
-// one of the quotient; larger quotients take the integer division.  Same
-// result and events as divt.
-__device__ __forceinline__ i64 divt_rcp(i64 a, i64 d, double dinv, unsigned &ev) {
-  const double qe = __dmul_rn((double)a, dinv);
-  if (!(fabs(qe) < 1125899906842624.0)) return divt(a, d, ev);  // 2^50
-  i64 q = __double2ll_rz(qe);
-  i128 r = (i128)a - (i128)q * (i128)d;
-  const i64 ad = d < 0 ? -d : d, sd = d < 0 ? -1 : 1;
-  if (a >= 0) {
-    while (r < 0) { q -= sd; r += ad; }
-    while (r >= ad) { q += sd; r -= ad; }
-  } else {
-    while (r > 0) { q += sd; r -= ad; }
-    while (-r >= ad) { q -= sd; r += ad; }
-  }
-  return q;
+// Division by a run-time invariant divisor without a divide instruction
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, the unsigned N-bit method of their Sec. 4):
+// for 1 <= d < 2^64 with l = ceil(log2 d) and m = floor(2^64 (2^l - d) / d)
+// + 1 (which fits in 64 bits), every 0 <= n < 2^64 has
+// floor(n / d) = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n).
+__device__ __forceinline__ int ceil_log2_u64(u64 d) { return d <= 1 ? 0 : 64 - __clzll(d - 1); }
+
+// m for the divisor d >= 1 (set-up only: a 128-bit division)
+__device__ __forceinline__ u64 magic_u64(u64 d) {
+  const int l = ceil_log2_u64(d);
+  const u128 num = ((u128)1 << 64) * (((u128)1 << l) - (u128)d);
+  return (u64)(num / (u128)d) + 1;
+}
+
+__device__ __forceinline__ u64 udiv_magic(u64 n, u64 d, u64 m) {
+  const int l = ceil_log2_u64(d);
+  const u64 t = __umul64hi(m, n);
+  return (t + ((n - t) >> (l < 1 ? l : 1))) >> (l > 1 ? l - 1 : 0);
+}
+
+// a / d truncated toward zero for d != 0, m = magic_u64(|d|): the same result
+// and events as divt
+__device__ __forceinline__ i64 divt_magic(i64 a, i64 d, u64 m, unsigned &ev) {
+  ev += (a == INT64_MIN && d == -1);
+  const u64 ua = a < 0 ? 0ull - (u64)a : (u64)a;
+  const u64 ud = d < 0 ? 0ull - (u64)d : (u64)d;
+  const u64 uq = udiv_magic(ua, ud, m);
+  return (i64)(((a < 0) != (d < 0)) ? 0ull - uq : uq);
 }
 
 // floor(sqrt(s)) for s >= 0 (0 for s <= 0): FP64 estimate, then exact

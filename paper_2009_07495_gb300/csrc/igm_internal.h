@@ -65,13 +65,19 @@ struct SysScal {
 // (q < K, col -1 past the row's end), with its diagonal pdiag[p]; pfacd,
 // pdiagd: the same from the FP64 factors (FP64 comparison solver only).
 // need[g]: progress the previous chunk must reach before group g runs.
+// progress words one 128-byte line apart (pollers of different chunks do not
+// share a line)
+#define IGM_PROG_STRIDE 16
+
 struct Tri {
   const int *ord, *lptr, *levb, *lev, *need, *pcol;
   const i64 *pfac, *pdiag;
-  const double *pdinv;          // 1 / pdiag (FP64 estimate of the divisions)
+  const u64 *pdm;               // magic multipliers of |pdiag| (exact divisions)
   const double *pfacd, *pdiagd;
-  u64 *prog;                    // per chunk: (epoch << 32) | levels done
+  u64 *prog;                    // per chunk (IGM_PROG_STRIDE apart): (epoch << 32) | levels done
   int nchunk, K;
+  int maxlev;                   // most local levels of one chunk
+  int maxw;                     // most rows of one level group
 };
 
 struct SysDev {
@@ -130,6 +136,9 @@ struct BatchDev {
   const Tile *mseg;
   i64 *mseg_h;             // per segment: the coefficient of the next pass
   int mgs_wrows;           // rows of w each CTA keeps in shared memory (0: global)
+  int trsv_maxlev;         // most local levels of a substitution chunk
+  int trsv_maxw;           // most rows of one level group
+  int trsv_maxk;           // most strict entries of one factor row
 };
 
 // vector selectors for the generic max / norm kernels

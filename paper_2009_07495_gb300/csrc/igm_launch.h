@@ -25,14 +25,16 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
                     cudaStream_t st);
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
                  const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
                  double *pfacd, double *pdiagd, cudaStream_t st);
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
                  const int *ord, const int *levb, const int *lev, int *need, cudaStream_t st);
 // substitutions: kind 0 integer (line 5'), 1 FP64 on the integer factors
 // (line 1'), 2 FP64 factors (comparison solver); which 0 line 1', 1 line 5'
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
-                    cudaStream_t st);void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
+                    cudaStream_t st);
+void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st);
+void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,
                     cudaStream_t st);
 

@@ -161,6 +161,14 @@ __global__ void s_scatter(int n, int lower, int R, const int *level, const int *
   }
 }
 
+// the most rows of one level group, max over g of lptr[g+1] - lptr[g]
+__global__ void s_maxw(int L, const int *lptr, int *out) {
+  int w = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < L; g += gridDim.x * blockDim.x)
+    w = max(w, lptr[g + 1] - lptr[g]);
+  atomicMax(out, w);
+}
+
 // eq. (dl), (dl2), (l1), (u1), (ilu2): D_l = |d|^1/2, D_u = sgn(d)|d|^1/2,
 // Lbar = trunc(L D_l), Ubar = trunc(D_u U') with U' = D^-1 U
 __global__ void s_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
@@ -226,6 +234,9 @@ void launch_level_order(int n, int lower, int R, int L, const int *level, const 
   s_scan<<<1, 1024, 0, st>>>(L, cnt, lptr);
   cudaMemcpyAsync(cnt, lptr, sizeof(int) * L, cudaMemcpyDeviceToDevice, st);
   s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt, order);
+}
+void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st) {
+  s_maxw<<<grid_for(L, 256), 256, 0, st>>>(L, lptr, out);
 }
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,

@@ -39,7 +39,7 @@ __global__ void s_maxdeps(int n, const int *rowptr, const int *diagpos, int lowe
 // packs the strict part of the row at each position, dependency-major
 __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
                        int K, const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                       const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                       const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
                        double *pfacd, double *pdiagd) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     int i = ord[p];
@@ -53,7 +53,8 @@ __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diag
       if (pfacd) pfacd[(size_t)q * n + p] = in ? f[k] : 0.0;
     }
     pdiag[p] = lower ? ldiag[i] : udiag[i];
-    pdinv[p] = 1.0 / (double)pdiag[p];
+    const i64 dg = pdiag[p];
+    pdm[p] = dg == 0 ? 0 : magic_u64(dg < 0 ? 0ull - (u64)dg : (u64)dg);
     if (pdiagd) pdiagd[p] = f[diagpos[i]];
   }
 }
@@ -105,8 +106,31 @@ struct RowPre {
   V fac[IGM_TRSV_KC];
   V diag;
   V rhs;
-  double dinv;
+  u64 dm;  // magic multiplier of |diag| (integer kind)
 };
+
+// read-only loads issued where they are written (a prefetch must not be
+// moved next to its use)
+__device__ __forceinline__ int ldnc(const int *p) {
+  int v;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ long long ldnc(const long long *p) {
+  long long v;
+  asm volatile("ld.global.nc.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ldnc(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.global.nc.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ldnc(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
 
 template <int KIND>
 __device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, int p, int row,
@@ -115,38 +139,220 @@ __device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, i
 #pragma unroll
   for (int q = 0; q < IGM_TRSV_KC; ++q) {
     if (q < T.K) {
-      r.col[q] = T.pcol[(size_t)q * n + p];
-      if (KIND == TK_INT) r.fac[q] = T.pfac[(size_t)q * n + p];
-      else if (KIND == TK_FPI) r.fac[q] = (double)T.pfac[(size_t)q * n + p];
-      else r.fac[q] = T.pfacd[(size_t)q * n + p];
+      r.col[q] = ldnc(T.pcol + (size_t)q * n + p);
+      if (KIND == TK_INT) r.fac[q] = ldnc(T.pfac + (size_t)q * n + p);
+      else if (KIND == TK_FPI) r.fac[q] = (double)ldnc(T.pfac + (size_t)q * n + p);
+      else r.fac[q] = ldnc(T.pfacd + (size_t)q * n + p);
     } else {
       r.col[q] = -1;
+      r.fac[q] = 0;
     }
   }
   if (KIND == TK_INT) {
-    r.diag = T.pdiag[p];
-    r.dinv = T.pdinv[p];
-  } else if (KIND == TK_FPI) r.diag = (double)T.pdiag[p];
-  else r.diag = T.pdiagd ? T.pdiagd[p] : 1.0;
-  r.rhs = in[r.i];
+    r.diag = ldnc(T.pdiag + p);
+    r.dm = ldnc(T.pdm + p);
+  } else if (KIND == TK_FPI) {
+    r.diag = (double)ldnc(T.pdiag + p);
+    r.dm = 0;
+  } else {
+    r.diag = T.pdiagd ? ldnc(T.pdiagd + p) : 1.0;
+    r.dm = 0;
+  }
+  r.rhs = ldnc(in + r.i);
 }
 
+// asynchronous global -> shared copies (no register scoreboard is held while
+// they are in flight; a thread waits for its own groups)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until at most n of this thread's groups are pending (n <= 3)
+__device__ __forceinline__ void cp_async_wait(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+
+// One row of a level: y_i = (rhs_i - sum_q fac_q y_(col_q)) / diag_i.  FAST
+// when every dependency outside the chunk lies in the previous chunk (already
+// waited for) and the chunk's values are in shared memory: the register-held
+// dependencies are then fetched and multiplied without branches (padding
+// entries have factor 0).  Integer numerators are exact (int128); FP64 ones
+// subtract in the packed (CSR) order.
+template <int KIND, bool FAST>
+__device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
+    const RowPre<KIND> &rr, int p, const Tri &T, int n, int lower, int first, int R,
+    bool use_smem, bool single, u64 ep, const typename TrsvT<KIND>::V *sv,
+    const typename TrsvT<KIND>::V *out, unsigned *err, unsigned &ev) {
+  typedef typename TrsvT<KIND>::V V;
+  V yv[IGM_TRSV_KC];
+#pragma unroll
+  for (int q = 0; q < IGM_TRSV_KC; ++q) {
+    const int j = rr.col[q];
+    const int pj = lower ? j : n - 1 - j;
+    if (FAST) {
+      const bool ext = j >= 0 && pj < first;
+      const int si = (j >= 0 && !ext) ? pj - first : 0;
+      yv[q] = ext ? (V)__ldcg(out + j) : sv[si];
+    } else {
+      V y = 0;
+      if (j >= 0) {
+        if (pj >= first) {
+          y = use_smem ? sv[pj - first] : (V)__ldcg(out + j);
+        } else {
+          if (!single) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (pj / R), ep | (u64)(T.lev[j] + 1), err);
+          y = (V)__ldcg(out + j);
+        }
+      }
+      yv[q] = y;
+    }
+  }
+  typedef typename std::conditional<KIND == TK_INT, i128, double>::type A;
+  A acc = (A)rr.rhs;
+  if (KIND == TK_INT) {
+    i128 sum = 0;
+#pragma unroll
+    for (int q = 0; q < IGM_TRSV_KC; ++q) sum += (i128)mulw((i64)rr.fac[q], (i64)yv[q], ev);
+    acc -= (A)sum;
+  } else {
+#pragma unroll
+    for (int q = 0; q < IGM_TRSV_KC; ++q)
+      if (rr.col[q] >= 0) acc = __dsub_rn((double)acc, __dmul_rn((double)rr.fac[q], (double)yv[q]));
+  }
+  // rows with more dependencies than the registers hold
+  for (int q = IGM_TRSV_KC; q < T.K; ++q) {
+    const int j = T.pcol[(size_t)q * n + p];
+    if (j < 0) break;
+    V a;
+    if (KIND == TK_INT) a = T.pfac[(size_t)q * n + p];
+    else if (KIND == TK_FPI) a = (double)T.pfac[(size_t)q * n + p];
+    else a = T.pfacd[(size_t)q * n + p];
+    const int pj = lower ? j : n - 1 - j;
+    V yj;
+    if (pj >= first) {
+      yj = use_smem ? sv[pj - first] : (V)__ldcg(out + j);
+    } else {
+      if (!single) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (pj / R), ep | (u64)(T.lev[j] + 1), err);
+      yj = (V)__ldcg(out + j);
+    }
+    if (KIND == TK_INT) acc -= (A)mulw((i64)a, (i64)yj, ev);
+    else acc = __dsub_rn((double)acc, __dmul_rn((double)a, (double)yj));
+  }
+  if (KIND == TK_INT) {
+    ev += out64((i128)acc);
+    return (V)divt_magic(wrap((i128)acc), (i64)rr.diag, rr.dm, ev);
+  }
+  if (KIND == TK_FP && lower) return (V)acc;  // unit lower factor
+  return (V)__ddiv_rn((double)acc, (double)rr.diag);
+}
+
+// CTA-scope release / acquire on shared-memory counters
+__device__ __forceinline__ void red_release_cta(unsigned *p, unsigned v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(p)),
+               "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void st_release_cta(unsigned *p, unsigned v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(p)),
+               "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cta(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];"
+               : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ u64 gtimer() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The three waits of a substitution CTA are bounded in time, nested so that
+// a wait never expires while the wait it depends on can still succeed: the
+// waiter gives up after IGM_WAIT_NS, the compute warps (who wait on the
+// waiter) after twice that, the publisher (who waits on them) after four
+// times.  An iteration cap backs up each bound.
+#define IGM_WAIT_NS 1000000000ull
+#define IGM_WAIT_ITERS (1 << 28)
+
+// spin until the shared counter *p reaches at least v; false if the bound
+// expired or another wait of the system already timed out
+__device__ __forceinline__ bool wait_cta(const unsigned *p, unsigned v, unsigned *err,
+                                         u64 limit_ns) {
+  if (ld_acquire_cta(p) >= v) return true;
+  const u64 t0 = gtimer();
+  for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+    if (ld_acquire_cta(p) >= v) return true;
+    if (it > 64) __nanosleep(32);
+    if ((it & 255) == 255 &&
+        ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > limit_ns))
+      break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+// Roles in a substitution CTA: IGM_TRSV_CW compute warps walk the levels;
+// the waiter warp acquires the previous chunk's progress word and joins the
+// compute warps in one named barrier per level, which both lets a level start
+// once its inputs are there and makes the previous level's shared values
+// visible; the publisher warp turns the compute warps' count of finished
+// levels into this chunk's progress word with a GPU-scope release, off the
+// compute warps' path.
+#define IGM_TRSV_CW 8
+#define IGM_TRSV_NC (IGM_TRSV_CW * 32)
+#define IGM_TRSV_THREADS (IGM_TRSV_NC + 64)
+
 template <int KIND>
-__global__ void __launch_bounds__(IGM_TRSV_BLOCK)
-    k_trsv_lv(BatchDev B, int lower, int which, int smem_rows) {
+__global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
+    k_trsv_lv(BatchDev B, int lower, int which, int smem_rows, int smem_lev, int rmax, int pf,
+              int kr) {
   typedef typename TrsvT<KIND>::V V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // [values: smem_rows][ring words: (pf+1) x (kr+3) x rmax][order: smem_rows]
+  // [ring columns: (pf+1) x kr x rmax][level pointers: smem_lev+1][needs: smem_lev]
+  const int S = pf + 1;
   V *sv = reinterpret_cast<V *>(smem_raw);
-  int *sord = reinterpret_cast<int *>(smem_raw + (size_t)smem_rows * sizeof(V));
+  long long *ring64 = reinterpret_cast<long long *>(sv + smem_rows);
+  int *sord = reinterpret_cast<int *>(ring64 + (pf > 0 ? (size_t)S * (kr + 3) * rmax : 0));
+  int *ring32 = sord + smem_rows;
+  int *slptr = ring32 + (pf > 0 ? (size_t)S * kr * rmax : 0);  // level pointers (smem_lev + 1)
+  int *sneed = slptr + smem_lev + 1;  // their requirements on the previous chunk
   __shared__ int s_t;
+  __shared__ unsigned s_done;
   const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
-  if (threadIdx.x == 0) s_t = (int)atomicAdd(&B.ticket[tk], 1u);
+  if (threadIdx.x == 0) {
+    s_t = (int)atomicAdd(&B.ticket[tk], 1u);
+    s_done = 0;
+  }
   __syncthreads();
-  Tile ct = B.ctiles[s_t];
+  const Tile ct = B.ctiles[s_t];
   const SysDev *s = B.sys[ct.sys];
   SysScal *sc = s->sc;
   if (!(sc->cyc != 0 && sc->early == 0) || !s->p.precond) return;
-  const Tri &T = s->tri[lower ? 0 : 1];
+  const Tri T = s->tri[lower ? 0 : 1];
   const int c = ct.row0, n = s->n, R = s->chunk;
   const int first = c * R, last = min(n, first + R);  // positions of the chunk
   const bool use_smem = (last - first) <= smem_rows;
@@ -164,93 +370,155 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
     out = reinterpret_cast<V *>(lower ? s->t : reinterpret_cast<double *>(s->w));
   }
   const u64 ep = (u64)(unsigned)sc->seq << 32;
-  const int g0 = T.levb[c], g1 = T.levb[c + 1];
+  const int g0 = T.levb[c], nlev = T.levb[c + 1] - g0;
   const bool single = s->single_pred != 0;
-  unsigned ev = 0;
+  const bool lev_smem = nlev <= smem_lev;
+  unsigned *err = &sc->err;
 
-  // the chunk's rows in level order, staged once so that prefetching a row
-  // never waits on the order array
+  // stage the chunk's order and level data once
   if (use_smem)
     for (int q = threadIdx.x; q < last - first; q += blockDim.x) sord[q] = T.ord[first + q];
+  if (lev_smem) {
+    for (int q = threadIdx.x; q <= nlev; q += blockDim.x) slptr[q] = T.lptr[g0 + q];
+    for (int q = threadIdx.x; q < nlev; q += blockDim.x) sneed[q] = T.need[g0 + q];
+  }
   __syncthreads();
 #define ROW_OF(pp) (use_smem ? sord[(pp) - first] : T.ord[pp])
+#define LPTR(l) (lev_smem ? slptr[l] : T.lptr[g0 + (l)])
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  RowPre<KIND> cur, nxt;
-  int pn = T.lptr[g0] + threadIdx.x;
-  bool has_nxt = pn < T.lptr[g0 + 1];
-  if (has_nxt) row_load<KIND>(nxt, T, n, pn, ROW_OF(pn), in);
+  if (wid == IGM_TRSV_CW) {  // waiter: one barrier per level with the compute warps
+    u64 seen = 0;  // levels of the previous chunk known to be done
+    bool dead = false;
+    for (int l = 0; l < nlev; ++l) {
+      const int nd = (single && c > 0) ? (lev_smem ? sneed[l] : T.need[g0 + l]) : 0;
+      if (lane == 0 && !dead && (u64)nd > seen) {
+        const u64 want = ep | (u64)nd;
+        u64 v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
+        if (v < want) {
+          const u64 t0 = gtimer();
+          for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+            if (it > 32) __nanosleep(16);
+            v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
+            if (v >= want) break;
+            if ((it & 255) == 255 &&
+                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > IGM_WAIT_NS))
+              break;
+          }
+        }
+        if (v < want) {  // expired: the compute warps finish unchecked, the result is flagged
+          atomicOr(err, ERR_TIMEOUT);
+          dead = true;
+        } else {
+          seen = v - ep;
+        }
+      }
+      __syncwarp();
+      asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
+    }
+    return;
+  }
+  if (wid == IGM_TRSV_CW + 1) {  // publisher
+    if (lane == 0) {
+      for (unsigned pub = 0; pub < (unsigned)nlev;) {
+        // levels every compute warp has finished
+        if (!wait_cta(&s_done, (pub + 1) * IGM_TRSV_CW, err, 4 * IGM_WAIT_NS)) break;
+        pub = ld_acquire_cta(&s_done) / IGM_TRSV_CW;
+        st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
+      }
+    }
+    return;
+  }
 
-  for (int g = g0; g < g1; ++g) {
-    const int p0 = T.lptr[g], p1 = T.lptr[g + 1];
-    const bool has_cur = has_nxt;
-    cur = nxt;
-    // prefetch this thread's first row of the next level
-    if (g + 1 < g1) {
-      pn = T.lptr[g + 1] + threadIdx.x;
-      has_nxt = pn < T.lptr[g + 2];
-      if (has_nxt) row_load<KIND>(nxt, T, n, pn, ROW_OF(pn), in);
-    } else {
-      has_nxt = false;
-    }
-    // the previous chunk must have reached the level this group reads
-    if (single && c > 0) {
-      if (threadIdx.x == 0) {
-        int nd = T.need[g];
-        if (nd) wait_prog(T.prog + c - 1, ep | (u64)nd, &sc->err);
-      }
-      __syncthreads();
-    }
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-      RowPre<KIND> rr;
-      if (p == p0 + (int)threadIdx.x && has_cur) rr = cur;
-      else row_load<KIND>(rr, T, n, p, ROW_OF(p), in);
-      typedef typename std::conditional<KIND == TK_INT, i128, double>::type A;
-      A acc = (A)rr.rhs;
-      for (int q = 0; q < T.K; ++q) {
-        int j;
-        V a;
-        if (q < IGM_TRSV_KC) {
-          j = rr.col[q];
-          a = rr.fac[q];
-        } else {
-          j = T.pcol[(size_t)q * n + p];
-          if (KIND == TK_INT) a = T.pfac[(size_t)q * n + p];
-          else if (KIND == TK_FPI) a = (double)T.pfac[(size_t)q * n + p];
-          else a = T.pfacd[(size_t)q * n + p];
+  // compute warps.  A thread's first row of a level (threads below rmax) is
+  // copied into a shared-memory ring pf levels ahead with asynchronous
+  // copies; other rows are loaded when they are computed.
+  const int tid = threadIdx.x;
+  const bool fast = single && use_smem;
+  const int kk = T.K < kr ? T.K : kr;  // dependencies this system keeps in the ring
+  unsigned ev = 0;
+  auto issue = [&](int lv) {
+    if (pf == 0) return;
+    if (lv < nlev && tid < rmax) {
+      const int pn = LPTR(lv) + tid;
+      if (pn < LPTR(lv + 1)) {
+        const int sl = lv % S;
+        long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
+        int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
+        for (int q = 0; q < kk; ++q) {
+          cp_async4(r32 + q * rmax, T.pcol + (size_t)q * n + pn);
+          if (KIND == TK_FP) cp_async8(r64 + q * rmax, T.pfacd + (size_t)q * n + pn);
+          else cp_async8(r64 + q * rmax, T.pfac + (size_t)q * n + pn);
         }
-        if (j < 0) break;
-        const int pj = lower ? j : n - 1 - j;
-        V yj;
-        if (pj >= first) {
-          yj = use_smem ? sv[pj - first] : out[j];
-        } else {
-          if (!single) wait_prog(T.prog + pj / R, ep | (u64)(T.lev[j] + 1), &sc->err);
-          yj = (V)__ldcg(out + j);
-        }
-        if (KIND == TK_INT) acc -= (A)mulw((i64)a, (i64)yj, ev);
-        else acc = __dsub_rn((double)acc, __dmul_rn((double)a, (double)yj));
+        if (KIND != TK_FP) cp_async8(r64 + kr * rmax, T.pdiag + pn);
+        else if (T.pdiagd) cp_async8(r64 + kr * rmax, T.pdiagd + pn);
+        if (KIND == TK_INT) cp_async8(r64 + (kr + 1) * rmax, T.pdm + pn);
+        cp_async8(r64 + (kr + 2) * rmax, in + ROW_OF(pn));
       }
-      V y;
-      if (KIND == TK_INT) {
-        ev += out64((i128)acc);
-        y = (V)divt_rcp(wrap((i128)acc), (i64)rr.diag, rr.dinv, ev);
-      } else if (KIND == TK_FP && lower) {
-        y = (V)acc;  // unit lower factor
+    }
+    cp_async_commit();
+  };
+  auto ring_row = [&](int lv, int p, RowPre<KIND> &r) {
+    const int sl = lv % S;
+    const long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
+    const int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
+    r.i = ROW_OF(p);
+#pragma unroll
+    for (int q = 0; q < IGM_TRSV_KC; ++q) {
+      if (q < kk) {
+        r.col[q] = r32[q * rmax];
+        const long long w = r64[q * rmax];
+        if (KIND == TK_INT) r.fac[q] = (V)w;
+        else if (KIND == TK_FPI) r.fac[q] = (V)(double)w;
+        else r.fac[q] = (V)__longlong_as_double(w);
       } else {
-        y = (V)__ddiv_rn((double)acc, (double)rr.diag);
+        r.col[q] = -1;
+        r.fac[q] = 0;
       }
+    }
+    const long long dw = r64[kr * rmax], rw = r64[(kr + 2) * rmax];
+    if (KIND == TK_INT) {
+      r.diag = (V)dw;
+      r.dm = (u64)r64[(kr + 1) * rmax];
+      r.rhs = (V)rw;
+    } else {
+      if (KIND == TK_FPI) r.diag = (V)(double)dw;
+      else r.diag = (V)(T.pdiagd ? __longlong_as_double(dw) : 1.0);
+      r.dm = 0;
+      r.rhs = (V)__longlong_as_double(rw);
+    }
+  };
+  for (int l = 0; l < pf; ++l) issue(l);
+  for (int l = 0; l < nlev; ++l) {
+    const int p0 = LPTR(l), p1 = LPTR(l + 1);
+    issue(l + pf);
+    // the waiter has seen the previous chunk reach what this level reads;
+    // the previous level's shared values are visible
+    __syncwarp();
+    asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
+    if (pf > 0) cp_async_wait(pf);  // this thread's copies of level l have landed
+    for (int p = p0 + tid; p < p1; p += IGM_TRSV_NC) {
+      RowPre<KIND> rr;
+      if (pf > 0 && p == p0 + tid && tid < rmax) ring_row(l, p, rr);
+      else row_load<KIND>(rr, T, n, p, ROW_OF(p), in);
+      const V y = fast ? trsv_row<KIND, true>(rr, p, T, n, lower, first, R, use_smem, single, ep,
+                                              sv, out, err, ev)
+                       : trsv_row<KIND, false>(rr, p, T, n, lower, first, R, use_smem, single,
+                                               ep, sv, out, err, ev);
       out[rr.i] = y;
       // shared slots are indexed by the row's natural position in the chunk
       // (the order inside a level group is arbitrary)
       if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
     }
-    // the release by one thread after the CTA barrier covers every thread's
-    // stores of the level (release is cumulative over the barrier)
-    __syncthreads();
-    if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
+    // the warp's stores of the level, then one count per warp for the
+    // publisher
+    __syncwarp();
+    if (lane == 0) red_release_cta(&s_done, 1u);
   }
+  if (pf > 0) cp_async_wait(0);
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
 #undef ROW_OF
+#undef LPTR
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +539,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
   const int g0 = T.levb[c], g1 = T.levb[c + 1];
   for (int g = g0; g < g1; ++g) {
     if (single && c > 0) {
-      if (threadIdx.x == 0 && T.need[g]) wait_prog(T.prog + c - 1, ep | (u64)T.need[g], err);
+      if (threadIdx.x == 0 && T.need[g]) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1), ep | (u64)T.need[g], err);
       __syncthreads();
     }
     for (int p = T.lptr[g] + threadIdx.x; p < T.lptr[g + 1]; p += blockDim.x) {
@@ -283,7 +551,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
         // visible after the CTA barrier) or in an earlier chunk (L2 loads
         // after the acquire of its progress word)
         const bool ext = k < first;
-        if (!single && ext) wait_prog(T.prog + k / R, ep | (u64)(T.lev[k] + 1), err);
+        if (!single && ext) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (k / R), ep | (u64)(T.lev[k] + 1), err);
         double ukk = ext ? __ldcg(f + diagpos[k]) : f[diagpos[k]];
         if (ukk == 0.0) {
           atomicOr(err, ERR_ZERO_PIVOT);
@@ -302,7 +570,7 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
       if (f[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
     }
     __syncthreads();
-    if (threadIdx.x == 0) st_release64(T.prog + c, ep | (u64)(g - g0 + 1));
+    if (threadIdx.x == 0) st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)(g - g0 + 1));
   }
 }
 
@@ -320,10 +588,10 @@ void launch_maxdeps(int n, const int *rowptr, const int *diagpos, int lower, int
 
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
                  const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, double *pdinv,
+                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
                  double *pfacd, double *pdiagd, cudaStream_t st) {
   s_pack<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, K, ord, fac, ldiag, udiag, f,
-                                     pcol, pfac, pdiag, pdinv, pfacd, pdiagd);
+                                     pcol, pfac, pdiag, pdm, pfacd, pdiagd);
 }
 
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
@@ -338,9 +606,11 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
                                                  epoch, err);
 }
 
-// shared memory for a chunk's values and order: the chunk if it fits in
-// 200 KB
+// shared memory: a chunk's values and order if the chunk fits in 200 KB,
+// its level pointers and requirements if they fit in the rest, then as deep
+// a ring of prefetched rows (up to three levels ahead) as the remainder holds
 static int smem_rows_for(int bytes_per) { return (200 * 1024) / bytes_per; }
+#define IGM_TRSV_SMEM_MAX (226 * 1024)
 
 template <int KIND>
 static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cudaStream_t st) {
@@ -349,13 +619,27 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
   int rows = smem_rows_for(bper);
   if (rows > max_chunk) rows = max_chunk;
   size_t sm = (size_t)rows * bper;
+  int lev = B.trsv_maxlev;
+  if (sm + (size_t)(2 * lev + 1) * sizeof(int) > IGM_TRSV_SMEM_MAX) lev = 0;
+  sm += (size_t)(2 * lev + 1) * sizeof(int);
+  const int kr = B.trsv_maxk < IGM_TRSV_KC ? (B.trsv_maxk > 0 ? B.trsv_maxk : 1) : IGM_TRSV_KC;
+  const int rmax = B.trsv_maxw < IGM_TRSV_NC ? B.trsv_maxw : IGM_TRSV_NC;
+  const size_t per_slot = (size_t)rmax * ((kr + 3) * 8 + kr * 4);
+  int pf = 0;
+  for (int d = 3; d >= 1; --d)
+    if (sm + (size_t)(d + 1) * per_slot <= IGM_TRSV_SMEM_MAX) {
+      pf = d;
+      break;
+    }
+  if (pf > 0) sm += (size_t)(pf + 1) * per_slot;
   static bool attr_set[3] = {false, false, false};
   if (!attr_set[KIND]) {
     cudaFuncSetAttribute(k_trsv_lv<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+                         IGM_TRSV_SMEM_MAX);
     attr_set[KIND] = true;
   }
-  k_trsv_lv<KIND><<<B.nctiles, IGM_TRSV_BLOCK, sm, st>>>(B, lower, which, rows);
+  k_trsv_lv<KIND><<<B.nctiles, IGM_TRSV_THREADS, sm, st>>>(B, lower, which, rows, lev, rmax, pf,
+                                                          kr);
 }
 
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
