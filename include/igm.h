@@ -84,7 +84,10 @@ typedef struct {
   int max_refine;/* maximum inner solves in Fig. 1                           */
   int inner;     /* 0: int-GMRES (Fig. 2); 1: FP64 GMRES(m) ("Double")       */
   int trsv_chunk;/* rows per chunk of the line-5' substitutions (0: automatic)*/
-  int reserved[5];
+  int trsv_cluster;/* chunks per thread-block cluster of the substitutions:
+                    0 automatic, 1 none, 2, 4 or 8 (results do not depend
+                    on it)                                               */
+  int reserved[4];
 } igm_params;
 
 #define IGM_MAX_M 128

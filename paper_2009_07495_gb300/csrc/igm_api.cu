@@ -154,6 +154,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.trsv_maxlev = maxlev;
   B.trsv_maxw = maxw;
   B.trsv_maxk = maxk;
+  B.trsv_cluster = hs[0]->prm.trsv_cluster;
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;
@@ -253,6 +254,9 @@ igm_status check_params(const igm_params *p) {
   if (!(p->tol >= 0.0)) return fail(IGM_EINVAL, "tol must be >= 0");
   if (p->inner != 0 && p->inner != 1) return fail(IGM_EINVAL, "inner must be 0 or 1");
   if (p->trsv_chunk < 0) return fail(IGM_EINVAL, "trsv_chunk must be >= 0");
+  if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
+        p->trsv_cluster == 4 || p->trsv_cluster == 8))
+    return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
   return IGM_OK;
 }
 

@@ -139,6 +139,7 @@ struct BatchDev {
   int trsv_maxlev;         // most local levels of a substitution chunk
   int trsv_maxw;           // most rows of one level group
   int trsv_maxk;           // most strict entries of one factor row
+  int trsv_cluster;        // CTAs per cluster of the substitutions (0 automatic)
 };
 
 // vector selectors for the generic max / norm kernels

@@ -14,12 +14,15 @@
 // group needs (precomputed); otherwise each row waits for its own
 // dependencies.  A chunk publishes its progress after every level.  Each
 // thread prefetches its row of the next level while computing the current.
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "igm_dev.cuh"
 #include "igm_launch.h"
 
 namespace igm {
+
+namespace cg = cooperative_groups;
 
 #define IGM_TRSV_BLOCK 256
 #define IGM_TRSV_KC 4  // dependencies prefetched into registers per row
@@ -198,7 +201,8 @@ template <int KIND, bool FAST>
 __device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
     const RowPre<KIND> &rr, int p, const Tri &T, int n, int lower, int first, int R,
     bool use_smem, bool single, u64 ep, const typename TrsvT<KIND>::V *sv,
-    const typename TrsvT<KIND>::V *out, unsigned *err, unsigned &ev) {
+    const typename TrsvT<KIND>::V *psv, const typename TrsvT<KIND>::V *out, unsigned *err,
+    unsigned &ev) {
   typedef typename TrsvT<KIND>::V V;
   V yv[IGM_TRSV_KC];
 #pragma unroll
@@ -208,7 +212,9 @@ __device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
     if (FAST) {
       const bool ext = j >= 0 && pj < first;
       const int si = (j >= 0 && !ext) ? pj - first : 0;
-      yv[q] = ext ? (V)__ldcg(out + j) : sv[si];
+      // the previous chunk's values: its CTA's shared memory when it is in
+      // this cluster, else global memory
+      yv[q] = ext ? (psv ? psv[pj - first + R] : (V)__ldcg(out + j)) : sv[si];
     } else {
       V y = 0;
       if (j >= 0) {
@@ -325,10 +331,31 @@ __device__ __forceinline__ bool wait_cta(const unsigned *p, unsigned v, unsigned
 #define IGM_TRSV_NC (IGM_TRSV_CW * 32)
 #define IGM_TRSV_THREADS (IGM_TRSV_NC + 64)
 
+// cluster-scope signalling between the CTAs of a cluster
+__device__ __forceinline__ void st_release_cluster_remote(unsigned *local_ptr, int rank,
+                                                          unsigned v) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(local_ptr), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cluster_local(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];"
+               : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+
+// One chunk (ctile t) of a substitution.  rank/cl: the CTA's place in its
+// cluster (cl = 1: no cluster).  s_done counts finished levels x warps;
+// s_pred receives the previous chunk's finished levels when that chunk runs
+// in the same cluster.
 template <int KIND>
-__global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
-    k_trsv_lv(BatchDev B, int lower, int which, int smem_rows, int smem_lev, int rmax, int pf,
-              int kr) {
+__device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, int cl, int lower,
+                                           int which, int smem_rows, int smem_lev, int rmax,
+                                           int pf, int kr, unsigned *s_done_p,
+                                           unsigned *s_pred_p) {
   typedef typename TrsvT<KIND>::V V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // [values: smem_rows][ring words: (pf+1) x (kr+3) x rmax][order: smem_rows]
@@ -340,15 +367,9 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   int *ring32 = sord + smem_rows;
   int *slptr = ring32 + (pf > 0 ? (size_t)S * kr * rmax : 0);  // level pointers (smem_lev + 1)
   int *sneed = slptr + smem_lev + 1;  // their requirements on the previous chunk
-  __shared__ int s_t;
-  __shared__ unsigned s_done;
-  const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
-  if (threadIdx.x == 0) {
-    s_t = (int)atomicAdd(&B.ticket[tk], 1u);
-    s_done = 0;
-  }
-  __syncthreads();
-  const Tile ct = B.ctiles[s_t];
+  unsigned &s_done = *s_done_p;
+  if (t >= B.nctiles) return;
+  const Tile ct = B.ctiles[t];
   const SysDev *s = B.sys[ct.sys];
   SysScal *sc = s->sc;
   if (!(sc->cyc != 0 && sc->early == 0) || !s->p.precond) return;
@@ -374,6 +395,13 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   const bool single = s->single_pred != 0;
   const bool lev_smem = nlev <= smem_lev;
   unsigned *err = &sc->err;
+  // the previous chunk (c - 1) runs in this cluster's CTA rank - 1 and keeps
+  // its values in shared memory; the next chunk (c + 1) in rank + 1
+  const bool pred_cl = cl > 1 && rank > 0 && c > 0 && single && R <= smem_rows;
+  const bool succ_cl = cl > 1 && rank < cl - 1 && t + 1 < B.nctiles &&
+                       B.ctiles[t + 1].sys == ct.sys && single && R <= smem_rows;
+  const V *psv = nullptr;
+  if (pred_cl) psv = cg::this_cluster().map_shared_rank(sv, rank - 1);
 
   // stage the chunk's order and level data once
   if (use_smem)
@@ -392,7 +420,26 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
     bool dead = false;
     for (int l = 0; l < nlev; ++l) {
       const int nd = (single && c > 0) ? (lev_smem ? sneed[l] : T.need[g0 + l]) : 0;
-      if (lane == 0 && !dead && (u64)nd > seen) {
+      if (lane == 0 && !dead && (u64)nd > seen && pred_cl) {
+        unsigned v = ld_acquire_cluster_local(s_pred_p);
+        if (v < (unsigned)nd) {
+          const u64 t0 = gtimer();
+          for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+            if (it > 256) __nanosleep(32);
+            v = ld_acquire_cluster_local(s_pred_p);
+            if (v >= (unsigned)nd) break;
+            if ((it & 255) == 255 &&
+                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > IGM_WAIT_NS))
+              break;
+          }
+        }
+        if (v < (unsigned)nd) {
+          atomicOr(err, ERR_TIMEOUT);
+          dead = true;
+        } else {
+          seen = v;
+        }
+      } else if (lane == 0 && !dead && (u64)nd > seen) {
         const u64 want = ep | (u64)nd;
         u64 v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
         if (v < want) {
@@ -424,7 +471,8 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
         // levels every compute warp has finished
         if (!wait_cta(&s_done, (pub + 1) * IGM_TRSV_CW, err, 4 * IGM_WAIT_NS)) break;
         pub = ld_acquire_cta(&s_done) / IGM_TRSV_CW;
-        st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
+        if (succ_cl) st_release_cluster_remote(s_pred_p, rank + 1, pub);
+        else st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
       }
     }
     return;
@@ -437,6 +485,15 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   const bool fast = single && use_smem;
   const int kk = T.K < kr ? T.K : kr;  // dependencies this system keeps in the ring
   unsigned ev = 0;
+  // the packed arrays of each register-held dependency
+  const int *pcq[IGM_TRSV_KC];
+  const void *pfq[IGM_TRSV_KC];
+#pragma unroll
+  for (int q = 0; q < IGM_TRSV_KC; ++q) {
+    pcq[q] = T.pcol + (size_t)q * n;
+    if (KIND == TK_FP) pfq[q] = T.pfacd + (size_t)q * n;
+    else pfq[q] = T.pfac + (size_t)q * n;
+  }
   auto issue = [&](int lv) {
     if (pf == 0) return;
     if (lv < nlev && tid < rmax) {
@@ -445,10 +502,12 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
         const int sl = lv % S;
         long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
         int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
-        for (int q = 0; q < kk; ++q) {
-          cp_async4(r32 + q * rmax, T.pcol + (size_t)q * n + pn);
-          if (KIND == TK_FP) cp_async8(r64 + q * rmax, T.pfacd + (size_t)q * n + pn);
-          else cp_async8(r64 + q * rmax, T.pfac + (size_t)q * n + pn);
+#pragma unroll
+        for (int q = 0; q < IGM_TRSV_KC; ++q) {
+          if (q < kk) {
+            cp_async4(r32 + q * rmax, pcq[q] + pn);
+            cp_async8(r64 + q * rmax, static_cast<const long long *>(pfq[q]) + pn);
+          }
         }
         if (KIND != TK_FP) cp_async8(r64 + kr * rmax, T.pdiag + pn);
         else if (T.pdiagd) cp_async8(r64 + kr * rmax, T.pdiagd + pn);
@@ -497,28 +556,75 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
     __syncwarp();
     asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
     if (pf > 0) cp_async_wait(pf);  // this thread's copies of level l have landed
+    V yl = 0;
+    int il = 0;
     for (int p = p0 + tid; p < p1; p += IGM_TRSV_NC) {
       RowPre<KIND> rr;
       if (pf > 0 && p == p0 + tid && tid < rmax) ring_row(l, p, rr);
       else row_load<KIND>(rr, T, n, p, ROW_OF(p), in);
       const V y = fast ? trsv_row<KIND, true>(rr, p, T, n, lower, first, R, use_smem, single, ep,
-                                              sv, out, err, ev)
+                                              sv, psv, out, err, ev)
                        : trsv_row<KIND, false>(rr, p, T, n, lower, first, R, use_smem, single,
-                                               ep, sv, out, err, ev);
-      out[rr.i] = y;
+                                               ep, sv, nullptr, out, err, ev);
       // shared slots are indexed by the row's natural position in the chunk
       // (the order inside a level group is arbitrary)
       if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
+      // a successor in the cluster reads the shared values only: the global
+      // store then stays out of the publisher's release
+      if (succ_cl) { yl = y; il = rr.i; }
+      else out[rr.i] = y;
     }
     // the warp's stores of the level, then one count per warp for the
     // publisher
     __syncwarp();
     if (lane == 0) red_release_cta(&s_done, 1u);
+    if (succ_cl) {
+      for (int p = p0 + tid, k = 0; p < p1; p += IGM_TRSV_NC, ++k)
+        if (k == 0) out[il] = yl;
+        else out[ROW_OF(p)] = sv[(lower ? ROW_OF(p) : n - 1 - ROW_OF(p)) - first];
+    }
   }
   if (pf > 0) cp_async_wait(0);
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
 #undef ROW_OF
 #undef LPTR
+}
+
+// The substitution kernel.  Without clusters each CTA takes a chunk by
+// ticket; with clusters of cl CTAs, rank 0 takes a ticket for cl consecutive
+// chunks (tickets keep every chunk's predecessor started before it), and all
+// CTAs of a cluster stay resident until the last one is done, since later
+// chunks read earlier chunks' shared memory.
+template <int KIND>
+__global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
+    k_trsv_lv(BatchDev B, int lower, int which, int smem_rows, int smem_lev, int rmax, int pf,
+              int kr, int cl) {
+  __shared__ int s_t;
+  __shared__ unsigned s_done, s_pred;
+  const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
+  if (cl > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    if (threadIdx.x == 0) {
+      if (rank == 0) s_t = (int)atomicAdd(&B.ticket[tk], 1u);
+      s_done = 0;
+      s_pred = 0;
+    }
+    cluster.sync();  // rank 0's ticket and every CTA's counters are set
+    const int t = *cluster.map_shared_rank(&s_t, 0) * cl + rank;
+    trsv_chunk<KIND>(B, t, rank, cl, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
+                     &s_pred);
+    cluster.sync();  // no CTA leaves while a later chunk may read its values
+  } else {
+    if (threadIdx.x == 0) {
+      s_t = (int)atomicAdd(&B.ticket[tk], 1u);
+      s_done = 0;
+      s_pred = 0;
+    }
+    __syncthreads();
+    trsv_chunk<KIND>(B, s_t, 0, 1, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
+                     &s_pred);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -638,8 +744,45 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
                          IGM_TRSV_SMEM_MAX);
     attr_set[KIND] = true;
   }
-  k_trsv_lv<KIND><<<B.nctiles, IGM_TRSV_THREADS, sm, st>>>(B, lower, which, rows, lev, rmax, pf,
-                                                          kr);
+  // clusters of consecutive chunks when the GPU can co-schedule them (4 by
+  // default: larger clusters are harder to place and measured slower)
+  int cl = B.trsv_cluster;
+  if (cl == 0) {
+    cl = 1;
+    for (int want = 4; want >= 2; want /= 2) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(want);
+      q.blockDim = dim3(IGM_TRSV_THREADS);
+      q.dynamicSmemBytes = sm;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = want;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int nclus = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclus, k_trsv_lv<KIND>, &q) == cudaSuccess && nclus >= 1) {
+        cl = want;
+        break;
+      }
+      cudaGetLastError();
+    }
+  }
+  const int G = (B.nctiles + cl - 1) / cl * cl;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(IGM_TRSV_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = cl > 1 ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND>, B, lower, which, rows, lev, rmax, pf, kr, cl);
 }
 
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,

@@ -291,6 +291,24 @@ def test_chunk_schedule_does_not_change_results(L, orc, chunk):
     solver.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_substitution_clusters_do_not_change_results(L, orc, cluster):
+    """Chunks of the substitutions may run as thread-block clusters (the next
+    chunk reads the previous one's shared memory); with 16 chunks, clusters of
+    1, 2, 4 or 8 CTAs all give the oracle's result bit for bit."""
+    s = W.small_cd3d(16, seed=45)
+    P = L.params_default(1, 30)
+    P.trsv_chunk = 256
+    P.trsv_cluster = cluster
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    solver.close()
+
+
 @pytest.fixture(scope="module")
 def cfg1():
     return W.config1()
