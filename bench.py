@@ -40,7 +40,7 @@ from paper_2009_07495_gb300 import workloads as W  # noqa: E402
 
 METRIC = "refined solves/s @1e-10 resid (int vs FP64 GMRES, 1 GB300); SpMV GB/s; p99 ms"
 KNAMES = ["spmv", "trsv_l", "trsv_u", "arnoldi", "resid"]
-KERNEL_SYMBOL = {"spmv": "k_spmv", "trsv_l": "k_trsv_int", "trsv_u": "k_trsv_int",
+KERNEL_SYMBOL = {"spmv": "k_spmv", "trsv_l": "k_trsv_lv", "trsv_u": "k_trsv_lv",
                  "arnoldi": "k_mgs_step", "resid": "k_resid"}
 
 WORKLOADS = {
@@ -137,14 +137,14 @@ def peak_hbm():
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
                       m: int) -> float:
     """Bytes the method must move per launch (the per-unit figures of the
-    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 4n; Arnoldi step j = m-1:
-    one basis vector per MGS pass (4n each, w kept on chip) for m passes plus
-    the line-11 write (4n); one triangular solve (nnz_tri + n) 12 + 16 n;
-    FP64 residual nnz 12 + 4(n+1) + 24 n."""
+    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 16n (v_j in, w out); Arnoldi step j = m-1:
+    each of the m basis vectors once (8n each), w in and v_m out (8n each);
+    one triangular solve (nnz_tri + n) 12 + 16 n; FP64 residual
+    nnz 12 + 4(n+1) + 24 n."""
     if kind == "spmv":
-        return nnz * (val_bytes + 4) + 4 * (n + 1) + 4 * n
+        return nnz * (val_bytes + 4) + 4 * (n + 1) + 16 * n
     if kind == "arnoldi":
-        return 4.0 * n * (m + 1)
+        return 8.0 * n * (m + 2)
     if kind in ("trsv_l", "trsv_u"):
         return (nnz_l + n) * 12 + 16 * n
     if kind == "resid":
