@@ -218,19 +218,48 @@ igm_status capture_graphs(Batch *b) {
   return IGM_OK;
 }
 
-// Rows per substitution chunk.  A multiple of the bandwidth of the
-// triangular factors makes every chunk depend on its predecessor only (for a
-// natural-order stencil: whole grid planes, so consecutive chunks' local
-// levels line up); at least 1024 rows; with a bandwidth too large for that
+// Rows per substitution chunk.  At least the bandwidth of the triangular
+// factors, so that every chunk depends on its predecessor only, and a
+// multiple of the matrix's row period P (for a natural-order stencil the grid
+// plane, N^2 in 3D), so that chunks start on plane boundaries: then a chunk's
+// first rows need only early levels of the previous chunk and consecutive
+// chunks pipeline; at least 1024 rows; with a bandwidth too large for that
 // (fewer than 8 chunks), about one chunk per SM.
-int auto_chunk(int n, int bw) {
+// The row period of a banded matrix: among 64 rows spread over the middle
+// half, the one with the most dependencies farther than half the lower
+// bandwidth gives the median of those far offsets (N^2 for 7- and 27-point 3D
+// stencils in natural order, N for 2D ones).  0 if there is none.
+int row_period(int n, const int *rp, const int *cl, int bw) {
+  if (n < 2 || bw < 2) return 0;
+  std::vector<int> best;
+  for (int k = 0; k < 64; ++k) {
+    const int i = (int)(n / 4 + (long long)k * (n / 2) / 64);
+    int ext[2];
+    if (cudaMemcpy(ext, rp + i, sizeof(ext), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    std::vector<int> c(ext[1] - ext[0]);
+    if (!c.empty() &&
+        cudaMemcpy(c.data(), cl + ext[0], sizeof(int) * c.size(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+      return 0;
+    std::vector<int> far;
+    for (int j : c)
+      if (i - j > bw / 2) far.push_back(i - j);
+    if (far.size() > best.size()) best = far;
+  }
+  if (best.empty()) return 0;
+  std::sort(best.begin(), best.end());
+  return best[best.size() / 2];
+}
+
+int auto_chunk(int n, int bw, int P) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long r;
+  if (P < 1 || P > bw) P = bw;
   if (bw >= 1 && (long long)bw * 8 <= n) {
-    r = bw;
-    while (r < 1024) r += bw;
+    r = P;
+    while (r < bw || r < 1024) r += P;
   } else {
     r = ((long long)n + sms - 1) / sms;
     r = (r + 1023) / 1024 * 1024;
@@ -441,7 +470,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     CKH(cudaMemcpyAsync(hbw, bwd, sizeof(hbw), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));
     const int bw = std::max(hbw[0], hbw[1]);
-    R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n, bw);
+    R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n, bw, row_period(n, rp, cl, hbw[0]));
     nch = (n + R - 1) / R;
     single = R >= bw ? 1 : 0;
     // the schedules and level-packed rows of L (t = 0) and U (t = 1)

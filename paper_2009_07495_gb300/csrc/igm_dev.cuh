@@ -309,6 +309,45 @@ __device__ __forceinline__ bool wait_prog(const u64 *prog, u64 target, unsigned 
   return false;
 }
 
+__device__ __forceinline__ u64 gtime_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The one-time set-up kernels (level schedules, the level-scheduled ILU(0))
+// are pipelines whose later parts may legitimately wait long for earlier
+// ones on big systems: their waits are bounded by time instead.
+#define IGM_SETUP_WAIT_NS 20000000000ull
+
+__device__ __forceinline__ bool wait_flag_setup(const int *flag, int epoch, unsigned *err) {
+  if (ld_acquire(flag) >= epoch) return true;
+  const u64 t0 = gtime_ns();
+  for (long long it = 0; it < (1ll << 34); ++it) {
+    __nanosleep(64);
+    if (ld_acquire(flag) >= epoch) return true;
+    if ((it & 255) == 255 &&
+        ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtime_ns() - t0 > IGM_SETUP_WAIT_NS))
+      break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ bool wait_prog_setup(const u64 *prog, u64 target, unsigned *err) {
+  if (ld_acquire64(prog) >= target) return true;
+  const u64 t0 = gtime_ns();
+  for (long long it = 0; it < (1ll << 34); ++it) {
+    if (it > 32) __nanosleep(32);
+    if (ld_acquire64(prog) >= target) return true;
+    if ((it & 255) == 255 &&
+        ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtime_ns() - t0 > IGM_SETUP_WAIT_NS))
+      break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
 // Last-CTA detection for a per-system reduction over its tiles.  Call from
 // all threads after the tile partial is written; returns true in every
 // thread of the CTA that arrives last (counter reset for reuse).

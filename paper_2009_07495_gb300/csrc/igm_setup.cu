@@ -110,7 +110,7 @@ __global__ void s_levels(int n, const int *rowptr, const int *col, const int *di
     int j = col[k];
     int pj = lower ? j : n - 1 - j;
     if (pj < first) continue;
-    wait_flag(flag + j, epoch, err);
+    wait_flag_setup(flag + j, epoch, err);
     lv = max(lv, __ldcg(level + j) + 1);
   }
   level[i] = lv;

@@ -25,7 +25,11 @@ namespace igm {
 namespace cg = cooperative_groups;
 
 #define IGM_TRSV_BLOCK 256
-#define IGM_TRSV_KC 4  // dependencies prefetched into registers per row
+// dependencies of a row held in registers (and in the prefetch ring): 4 for
+// 5/7-point stencils, 16 for up to 27-point ones; longer rows read the rest
+// from the packed arrays
+#define IGM_TRSV_KC_SMALL 4
+#define IGM_TRSV_KC_LARGE 16
 
 // ---------------------------------------------------------------------------
 // set-up: packed rows, predecessor requirements
@@ -101,12 +105,12 @@ struct TrsvT<TK_FP> {
 };
 
 // row data of one position, loaded ahead of its level
-template <int KIND>
+template <int KIND, int KC>
 struct RowPre {
   typedef typename TrsvT<KIND>::V V;
   int i;
-  int col[IGM_TRSV_KC];
-  V fac[IGM_TRSV_KC];
+  int col[KC];
+  V fac[KC];
   V diag;
   V rhs;
   u64 dm;  // magic multiplier of |diag| (integer kind)
@@ -135,12 +139,12 @@ __device__ __forceinline__ double ldnc(const double *p) {
   return v;
 }
 
-template <int KIND>
-__device__ __forceinline__ void row_load(RowPre<KIND> &r, const Tri &T, int n, int p, int row,
+template <int KIND, int KC>
+__device__ __forceinline__ void row_load(RowPre<KIND, KC> &r, const Tri &T, int n, int p, int row,
                                          const typename TrsvT<KIND>::V *in) {
   r.i = row;
 #pragma unroll
-  for (int q = 0; q < IGM_TRSV_KC; ++q) {
+  for (int q = 0; q < KC; ++q) {
     if (q < T.K) {
       r.col[q] = ldnc(T.pcol + (size_t)q * n + p);
       if (KIND == TK_INT) r.fac[q] = ldnc(T.pfac + (size_t)q * n + p);
@@ -197,16 +201,16 @@ __device__ __forceinline__ void cp_async_wait(int n) {
 // dependencies are then fetched and multiplied without branches (padding
 // entries have factor 0).  Integer numerators are exact (int128); FP64 ones
 // subtract in the packed (CSR) order.
-template <int KIND, bool FAST>
+template <int KIND, int KC, bool FAST>
 __device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
-    const RowPre<KIND> &rr, int p, const Tri &T, int n, int lower, int first, int R,
+    const RowPre<KIND, KC> &rr, int p, const Tri &T, int n, int lower, int first, int R,
     bool use_smem, bool single, u64 ep, const typename TrsvT<KIND>::V *sv,
     const typename TrsvT<KIND>::V *psv, const typename TrsvT<KIND>::V *out, unsigned *err,
     unsigned &ev) {
   typedef typename TrsvT<KIND>::V V;
-  V yv[IGM_TRSV_KC];
+  V yv[KC];
 #pragma unroll
-  for (int q = 0; q < IGM_TRSV_KC; ++q) {
+  for (int q = 0; q < KC; ++q) {
     const int j = rr.col[q];
     const int pj = lower ? j : n - 1 - j;
     if (FAST) {
@@ -233,15 +237,15 @@ __device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
   if (KIND == TK_INT) {
     i128 sum = 0;
 #pragma unroll
-    for (int q = 0; q < IGM_TRSV_KC; ++q) sum += (i128)mulw((i64)rr.fac[q], (i64)yv[q], ev);
+    for (int q = 0; q < KC; ++q) sum += (i128)mulw((i64)rr.fac[q], (i64)yv[q], ev);
     acc -= (A)sum;
   } else {
 #pragma unroll
-    for (int q = 0; q < IGM_TRSV_KC; ++q)
+    for (int q = 0; q < KC; ++q)
       if (rr.col[q] >= 0) acc = __dsub_rn((double)acc, __dmul_rn((double)rr.fac[q], (double)yv[q]));
   }
   // rows with more dependencies than the registers hold
-  for (int q = IGM_TRSV_KC; q < T.K; ++q) {
+  for (int q = KC; q < T.K; ++q) {
     const int j = T.pcol[(size_t)q * n + p];
     if (j < 0) break;
     V a;
@@ -351,7 +355,7 @@ __device__ __forceinline__ unsigned ld_acquire_cluster_local(const unsigned *p) 
 // cluster (cl = 1: no cluster).  s_done counts finished levels x warps;
 // s_pred receives the previous chunk's finished levels when that chunk runs
 // in the same cluster.
-template <int KIND>
+template <int KIND, int KC>
 __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, int cl, int lower,
                                            int which, int smem_rows, int smem_lev, int rmax,
                                            int pf, int kr, unsigned *s_done_p,
@@ -400,6 +404,11 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
   const bool pred_cl = cl > 1 && rank > 0 && c > 0 && single && R <= smem_rows;
   const bool succ_cl = cl > 1 && rank < cl - 1 && t + 1 < B.nctiles &&
                        B.ctiles[t + 1].sys == ct.sys && single && R <= smem_rows;
+  // a successor in the cluster reads this chunk's values from shared memory,
+  // except for dependencies beyond the KC held in registers, which it reads
+  // from global memory: the global stores may follow the signal only when
+  // rows have no more than KC dependencies
+  const bool late_store = succ_cl && T.K <= KC;
   const V *psv = nullptr;
   if (pred_cl) psv = cg::this_cluster().map_shared_rank(sv, rank - 1);
 
@@ -486,10 +495,10 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
   const int kk = T.K < kr ? T.K : kr;  // dependencies this system keeps in the ring
   unsigned ev = 0;
   // the packed arrays of each register-held dependency
-  const int *pcq[IGM_TRSV_KC];
-  const void *pfq[IGM_TRSV_KC];
+  const int *pcq[KC];
+  const void *pfq[KC];
 #pragma unroll
-  for (int q = 0; q < IGM_TRSV_KC; ++q) {
+  for (int q = 0; q < KC; ++q) {
     pcq[q] = T.pcol + (size_t)q * n;
     if (KIND == TK_FP) pfq[q] = T.pfacd + (size_t)q * n;
     else pfq[q] = T.pfac + (size_t)q * n;
@@ -503,7 +512,7 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
         long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
         int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
 #pragma unroll
-        for (int q = 0; q < IGM_TRSV_KC; ++q) {
+        for (int q = 0; q < KC; ++q) {
           if (q < kk) {
             cp_async4(r32 + q * rmax, pcq[q] + pn);
             cp_async8(r64 + q * rmax, static_cast<const long long *>(pfq[q]) + pn);
@@ -517,13 +526,13 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
     }
     cp_async_commit();
   };
-  auto ring_row = [&](int lv, int p, RowPre<KIND> &r) {
+  auto ring_row = [&](int lv, int p, RowPre<KIND, KC> &r) {
     const int sl = lv % S;
     const long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
     const int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
     r.i = ROW_OF(p);
 #pragma unroll
-    for (int q = 0; q < IGM_TRSV_KC; ++q) {
+    for (int q = 0; q < KC; ++q) {
       if (q < kk) {
         r.col[q] = r32[q * rmax];
         const long long w = r64[q * rmax];
@@ -559,26 +568,25 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
     V yl = 0;
     int il = 0;
     for (int p = p0 + tid; p < p1; p += IGM_TRSV_NC) {
-      RowPre<KIND> rr;
+      RowPre<KIND, KC> rr;
       if (pf > 0 && p == p0 + tid && tid < rmax) ring_row(l, p, rr);
-      else row_load<KIND>(rr, T, n, p, ROW_OF(p), in);
-      const V y = fast ? trsv_row<KIND, true>(rr, p, T, n, lower, first, R, use_smem, single, ep,
+      else row_load<KIND, KC>(rr, T, n, p, ROW_OF(p), in);
+      const V y = fast ? trsv_row<KIND, KC, true>(rr, p, T, n, lower, first, R, use_smem, single, ep,
                                               sv, psv, out, err, ev)
-                       : trsv_row<KIND, false>(rr, p, T, n, lower, first, R, use_smem, single,
+                       : trsv_row<KIND, KC, false>(rr, p, T, n, lower, first, R, use_smem, single,
                                                ep, sv, nullptr, out, err, ev);
       // shared slots are indexed by the row's natural position in the chunk
       // (the order inside a level group is arbitrary)
       if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
-      // a successor in the cluster reads the shared values only: the global
-      // store then stays out of the publisher's release
-      if (succ_cl) { yl = y; il = rr.i; }
+      // with late_store the global store stays out of the publisher's release
+      if (late_store) { yl = y; il = rr.i; }
       else out[rr.i] = y;
     }
     // the warp's stores of the level, then one count per warp for the
     // publisher
     __syncwarp();
     if (lane == 0) red_release_cta(&s_done, 1u);
-    if (succ_cl) {
+    if (late_store) {
       for (int p = p0 + tid, k = 0; p < p1; p += IGM_TRSV_NC, ++k)
         if (k == 0) out[il] = yl;
         else out[ROW_OF(p)] = sv[(lower ? ROW_OF(p) : n - 1 - ROW_OF(p)) - first];
@@ -595,7 +603,7 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
 // chunks (tickets keep every chunk's predecessor started before it), and all
 // CTAs of a cluster stay resident until the last one is done, since later
 // chunks read earlier chunks' shared memory.
-template <int KIND>
+template <int KIND, int KC>
 __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
     k_trsv_lv(BatchDev B, int lower, int which, int smem_rows, int smem_lev, int rmax, int pf,
               int kr, int cl) {
@@ -612,7 +620,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
     }
     cluster.sync();  // rank 0's ticket and every CTA's counters are set
     const int t = *cluster.map_shared_rank(&s_t, 0) * cl + rank;
-    trsv_chunk<KIND>(B, t, rank, cl, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
+    trsv_chunk<KIND, KC>(B, t, rank, cl, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
                      &s_pred);
     cluster.sync();  // no CTA leaves while a later chunk may read its values
   } else {
@@ -622,7 +630,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
       s_pred = 0;
     }
     __syncthreads();
-    trsv_chunk<KIND>(B, s_t, 0, 1, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
+    trsv_chunk<KIND, KC>(B, s_t, 0, 1, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
                      &s_pred);
   }
 }
@@ -645,7 +653,8 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
   const int g0 = T.levb[c], g1 = T.levb[c + 1];
   for (int g = g0; g < g1; ++g) {
     if (single && c > 0) {
-      if (threadIdx.x == 0 && T.need[g]) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1), ep | (u64)T.need[g], err);
+      if (threadIdx.x == 0 && T.need[g])
+        wait_prog_setup(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1), ep | (u64)T.need[g], err);
       __syncthreads();
     }
     for (int p = T.lptr[g] + threadIdx.x; p < T.lptr[g + 1]; p += blockDim.x) {
@@ -657,7 +666,8 @@ __global__ void __launch_bounds__(IGM_TRSV_BLOCK)
         // visible after the CTA barrier) or in an earlier chunk (L2 loads
         // after the acquire of its progress word)
         const bool ext = k < first;
-        if (!single && ext) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (k / R), ep | (u64)(T.lev[k] + 1), err);
+        if (!single && ext)
+          wait_prog_setup(T.prog + (size_t)IGM_PROG_STRIDE * (k / R), ep | (u64)(T.lev[k] + 1), err);
         double ukk = ext ? __ldcg(f + diagpos[k]) : f[diagpos[k]];
         if (ukk == 0.0) {
           atomicOr(err, ERR_ZERO_PIVOT);
@@ -718,7 +728,7 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
 static int smem_rows_for(int bytes_per) { return (200 * 1024) / bytes_per; }
 #define IGM_TRSV_SMEM_MAX (226 * 1024)
 
-template <int KIND>
+template <int KIND, int KC>
 static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cudaStream_t st) {
   if (B.nctiles <= 0) return;
   const int bper = 8 + 4;  // a value and an order entry per row
@@ -728,7 +738,7 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
   int lev = B.trsv_maxlev;
   if (sm + (size_t)(2 * lev + 1) * sizeof(int) > IGM_TRSV_SMEM_MAX) lev = 0;
   sm += (size_t)(2 * lev + 1) * sizeof(int);
-  const int kr = B.trsv_maxk < IGM_TRSV_KC ? (B.trsv_maxk > 0 ? B.trsv_maxk : 1) : IGM_TRSV_KC;
+  const int kr = B.trsv_maxk < KC ? (B.trsv_maxk > 0 ? B.trsv_maxk : 1) : KC;
   const int rmax = B.trsv_maxw < IGM_TRSV_NC ? B.trsv_maxw : IGM_TRSV_NC;
   const size_t per_slot = (size_t)rmax * ((kr + 3) * 8 + kr * 4);
   int pf = 0;
@@ -738,11 +748,11 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
       break;
     }
   if (pf > 0) sm += (size_t)(pf + 1) * per_slot;
-  static bool attr_set[3] = {false, false, false};
-  if (!attr_set[KIND]) {
-    cudaFuncSetAttribute(k_trsv_lv<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_trsv_lv<KIND, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          IGM_TRSV_SMEM_MAX);
-    attr_set[KIND] = true;
+    attr_set = true;
   }
   // clusters of consecutive chunks when the GPU can co-schedule them (4 by
   // default: larger clusters are harder to place and measured slower)
@@ -762,7 +772,7 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
       q.attrs = qa;
       q.numAttrs = 1;
       int nclus = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclus, k_trsv_lv<KIND>, &q) == cudaSuccess && nclus >= 1) {
+      if (cudaOccupancyMaxActiveClusters(&nclus, k_trsv_lv<KIND, KC>, &q) == cudaSuccess && nclus >= 1) {
         cl = want;
         break;
       }
@@ -782,14 +792,20 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = cl > 1 ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND>, B, lower, which, rows, lev, rmax, pf, kr, cl);
+  cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND, KC>, B, lower, which, rows, lev, rmax, pf, kr, cl);
 }
 
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
                     cudaStream_t st) {
-  if (kind == TK_INT) launch_lv<TK_INT>(B, lower, which, max_chunk, st);
-  else if (kind == TK_FPI) launch_lv<TK_FPI>(B, lower, which, max_chunk, st);
-  else launch_lv<TK_FP>(B, lower, which, max_chunk, st);
+  if (B.trsv_maxk <= IGM_TRSV_KC_SMALL) {
+    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
+    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
+    else launch_lv<TK_FP, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
+  } else {
+    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
+    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
+    else launch_lv<TK_FP, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
+  }
 }
 
 }  // namespace igm

@@ -309,6 +309,26 @@ def test_substitution_clusters_do_not_change_results(L, orc, cluster):
     solver.close()
 
 
+@pytest.mark.parametrize("N,chunk,cluster", [(12, 0, 0), (12, 300, 1), (12, 300, 4),
+                                             (14, 0, 4)])
+def test_27_point_ilu_bit_exact(L, orc, N, chunk, cluster):
+    """27-point stencil with ILU(0): factor rows have 13 strict entries, more
+    than the substitution keeps in registers (the rest come from the packed
+    arrays, external values from global memory).  Several chunks, with and
+    without clusters: the oracle's result bit for bit."""
+    s = W.small_cd3d(N, seed=46, points=27)
+    P = L.params_default(1, 30)
+    P.trsv_chunk = chunk
+    P.trsv_cluster = cluster
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    solver.close()
+
+
 @pytest.fixture(scope="module")
 def cfg1():
     return W.config1()
