@@ -53,6 +53,10 @@ WORKLOADS = {
     "cfg2": dict(desc="batch of 512 banded random systems, n log-uniform [1k, 64k], 5-27 "
                       "nnz/row within +-64, int-GMRES(30) no preconditioning, refinement "
                       "to 1e-10, one batched launch sequence", precond=0, m=30),
+    "cfg4": dict(desc="3D heterogeneous diffusion-convection 27-pt 200^3 (n=8,000,000, "
+                      "nnz~216M), log-normal diffusion sigma 2.5, convection U[-100,100], "
+                      "ILU(0) int-GMRES(60), FP64 refinement to 1e-10",
+                 gen=lambda: W.config4(), precond=1, m=60),
     "cfg3": dict(desc="serving stream: Poisson arrivals 2k req/s, 2D 5-pt / 3D 7-pt / 3D "
                       "27-pt convection-diffusion, sides U[16,160], Peclet log-U[0.1,100], "
                       "tol 1e-8 or 1e-10, 150 GB budget, continuous batching", m=30),
