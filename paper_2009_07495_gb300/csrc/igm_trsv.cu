@@ -406,8 +406,8 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
                        B.ctiles[t + 1].sys == ct.sys && single && R <= smem_rows;
   // a successor in the cluster reads this chunk's values from shared memory,
   // except for dependencies beyond the KC held in registers, which it reads
-  // from global memory: the global stores may follow the signal only when
-  // rows have no more than KC dependencies
+  // from global memory: the global stores may wait until the chunk is done
+  // only when rows have no more than KC dependencies
   const bool late_store = succ_cl && T.K <= KC;
   const V *psv = nullptr;
   if (pred_cl) psv = cg::this_cluster().map_shared_rank(sv, rank - 1);
@@ -565,8 +565,6 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
     __syncwarp();
     asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
     if (pf > 0) cp_async_wait(pf);  // this thread's copies of level l have landed
-    V yl = 0;
-    int il = 0;
     for (int p = p0 + tid; p < p1; p += IGM_TRSV_NC) {
       RowPre<KIND, KC> rr;
       if (pf > 0 && p == p0 + tid && tid < rmax) ring_row(l, p, rr);
@@ -578,19 +576,20 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
       // shared slots are indexed by the row's natural position in the chunk
       // (the order inside a level group is arbitrary)
       if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
-      // with late_store the global store stays out of the publisher's release
-      if (late_store) { yl = y; il = rr.i; }
-      else out[rr.i] = y;
+      if (!late_store) out[rr.i] = y;
     }
     // the warp's stores of the level, then one count per warp for the
     // publisher
     __syncwarp();
     if (lane == 0) red_release_cta(&s_done, 1u);
-    if (late_store) {
-      for (int p = p0 + tid, k = 0; p < p1; p += IGM_TRSV_NC, ++k)
-        if (k == 0) out[il] = yl;
-        else out[ROW_OF(p)] = sv[(lower ? ROW_OF(p) : n - 1 - ROW_OF(p)) - first];
-    }
+  }
+  if (late_store) {
+    // the chunk's values go to global memory once, in one coalesced sweep
+    // after its last level, so the publisher's releases never wait for
+    // global stores
+    asm volatile("bar.sync 3, %0;" ::"n"(IGM_TRSV_NC) : "memory");
+    for (int q = tid; q < last - first; q += IGM_TRSV_NC)
+      out[lower ? first + q : n - 1 - (first + q)] = sv[q];
   }
   if (pf > 0) cp_async_wait(0);
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
