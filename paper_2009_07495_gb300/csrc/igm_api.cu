@@ -369,7 +369,39 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   i64 *abar, *fac = nullptr, *ld = nullptr, *ud = nullptr, *w, *yv, *V, *H, *cs, *sn, *g;
   int *bwd = nullptr;
   size_t nz = nnz > 0 ? nnz : 1;
+  // the row pointers on the host: checked here (monotone, 0 .. nnz) and used
+  // for the sizes of the SELL-32 slices
+  std::vector<int> hrp(n + 1);
+  if (cudaMemcpy(hrp.data(), rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(IGM_EINVAL, "rowptr is not readable");
+  }
+  if (hrp[0] != 0 || hrp[n] != nnz) {
+    delete h;
+    return fail(IGM_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  }
+  const int nsl = (n + 31) / 32;
+  std::vector<long long> hsp(nsl + 1, 0);
+  for (int sl = 0; sl < nsl; ++sl) {
+    int len = 0;
+    for (int r = 32 * sl; r < std::min(n, 32 * sl + 32); ++r) {
+      if (hrp[r + 1] < hrp[r]) {
+        delete h;
+        return fail(IGM_EINVAL, "rowptr must be non-decreasing");
+      }
+      len = std::max(len, hrp[r + 1] - hrp[r]);
+    }
+    hsp[sl + 1] = hsp[sl] + 32ll * len;
+  }
+  const size_t nzs = hsp[nsl] > 0 ? (size_t)hsp[nsl] : 1;
+  long long *sptr;
+  i64 *sval;
+  int *scol;
   Arena &A = h->arena;
+  A.want(&sptr, nsl + 1);
+  A.want(&sval, nzs);
+  A.want(&scol, nzs);
   A.want(&rp, n + 1);
   A.want(&cl, nz);
   A.want(&dp, n);
@@ -445,6 +477,8 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   }
   launch_scale(n, rp, ahat, params->alpha_a, a, dd, err, s);
   launch_cast(nnz, a, abar, err, s);
+  CKH(cudaMemcpyAsync(sptr, hsp.data(), sizeof(long long) * (nsl + 1), cudaMemcpyHostToDevice, s));
+  launch_sell_fill(n, nsl, rp, cl, abar, sptr, sval, scol, s);
   CKH(cudaGetLastError());
   CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKH(cudaStreamSynchronize(s));
@@ -583,6 +617,9 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.a = a;
   d.d = dd;
   d.abar = abar;
+  d.sptr = sptr;
+  d.sval = sval;
+  d.scol = scol;
   d.f = f;
   d.fac = fac;
   d.ldiag = ld;
@@ -684,6 +721,7 @@ long long handle_bytes_estimate(int n, int nnz, const igm_params *p) {
   long long N = n, Z = nnz > 0 ? nnz : 1, m = p->m, r = 0;
   r += 4 * (N + 1) + 4 * Z + 4 * N;                 // rowptr, col, diagpos
   r += 8 * Z * 3 + 8 * N;                           // ahat, a, abar, d
+  r += 12 * Z + 12 * N + N / 4 + 8;                 // SELL-32 copy of abar (estimate)
   if (p->precond) r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
   r += 8 * N * 8 + 8 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
   return r + 64 * 256 + (long long)sizeof(SysScal) + sizeof(SysDev);

@@ -87,6 +87,12 @@ struct SysDev {
   const int *rowptr, *col, *diagpos;
   const double *ahat, *a, *d;
   const i64 *abar;
+  // Ā in SELL-32 (slices of 32 rows, each padded to its longest row and
+  // stored column-major: entry k of row 32 s + l at sptr[s] + 32 k + l;
+  // padding has value 0) for the line-5 SpMV
+  const long long *sptr;
+  const i64 *sval;
+  const int *scol;
   const double *f;                       // FP64 ILU(0) factors
   const i64 *fac, *ldiag, *udiag;        // integer factors
   // substitution schedules of the two factors, tri[0] = L, tri[1] = U

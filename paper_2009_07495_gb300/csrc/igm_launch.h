@@ -34,6 +34,8 @@ void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, i
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
                     cudaStream_t st);
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st);
+void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
+                      const long long *sptr, i64 *sval, int *scol, cudaStream_t st);
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,
                     cudaStream_t st);

@@ -85,6 +85,23 @@ __global__ void s_cast(long long nnz, const double *a, i64 *abar, unsigned *err)
   }
 }
 
+// Ā in SELL-32 (see SysDev): one thread per slot row (padding rows of the
+// last slice included)
+__global__ void s_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
+                            const long long *sptr, i64 *sval, int *scol) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < 32ll * nsl;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(r >> 5), lane = (int)(r & 31);
+    const long long base = sptr[s], len = (sptr[s + 1] - base) >> 5;
+    const int k0 = r < n ? rowptr[r] : 0, cnt = r < n ? rowptr[r + 1] - k0 : 0;
+    for (int k = 0; k < len; ++k) {
+      const long long q = base + 32ll * k + lane;
+      sval[q] = k < cnt ? abar[k0 + k] : 0;
+      scol[q] = k < cnt ? col[k0 + k] : (r < n ? (int)r : 0);
+    }
+  }
+}
+
 // Chunk-local level of every row of the strict lower (lower = 1) or strict
 // upper part.  Positions p = 0..n-1 run in dependency order (row p for L,
 // row n-1-p for U) and are cut into chunks of R positions; the local level of
@@ -234,6 +251,11 @@ void launch_level_order(int n, int lower, int R, int L, const int *level, const 
   s_scan<<<1, 1024, 0, st>>>(L, cnt, lptr);
   cudaMemcpyAsync(cnt, lptr, sizeof(int) * L, cudaMemcpyDeviceToDevice, st);
   s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt, order);
+}
+void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
+                      const long long *sptr, i64 *sval, int *scol, cudaStream_t st) {
+  s_sell_fill<<<grid_for(32ll * nsl, 256), 256, 0, st>>>(n, nsl, rowptr, col, abar, sptr, sval,
+                                                         scol);
 }
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st) {
   s_maxw<<<grid_for(L, 256), 256, 0, st>>>(L, lptr, out);

@@ -273,11 +273,37 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   if (!g_step(sc) || j >= s->p.m) return;
   if (blockIdx.x == tl.first && threadIdx.x == 0) sc->seq += 1;
   const i64 *vj = s->V + (size_t)j * s->n;
+  const long long *sptr = s->sptr;
+  const i64 *sval = s->sval;
+  const int *scol = s->scol;
   unsigned ev = 0;
+  // SELL-32: the 32 rows of a slice are one warp's lanes, so every load of
+  // values and columns is one coalesced 256 / 128-byte access; padding
+  // entries have value 0 (no product, no event)
   TILE_LOOP(i) {
+    const int sl = i >> 5;
+    const long long base = sptr[sl] + (i & 31);
+    const int len = (int)((sptr[sl + 1] - sptr[sl]) >> 5);
     i128 acc = 0;
-    for (int k = s->rowptr[i]; k < s->rowptr[i + 1]; ++k)
-      acc += (i128)mulw(s->abar[k], vj[s->col[k]], ev);
+    const i64 *pv = sval + base;
+    const int *pc = scol + base;
+    // eight entries at a time: all value and column loads, then all
+    // gathers, then the products (memory-level parallelism per thread)
+    for (int k0 = 0; k0 < len; k0 += 8) {
+      i64 a[8];
+      int c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = k0 + u < len;
+        a[u] = ok ? __ldcs(pv + 32 * (k0 + u)) : 0;
+        c[u] = ok ? __ldcs(pc + 32 * (k0 + u)) : i;
+      }
+      i64 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
+    }
     ev += out64(acc);
     s->w[i] = wrap(acc);
   }
