@@ -138,6 +138,20 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+def job_throughput(local_ms: float, steps: int, dist=None, device="cpu") -> tuple:
+    """Whole-job rate of independent replicas: every rank ran `steps` solves
+    and the job took as long as its slowest rank (max over ranks).  Returns
+    (max_ms, solves/s of all ranks together)."""
+    world, ms = 1, float(local_ms)
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1000.0)
+
+
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
                       m: int) -> float:
     """Bytes the method must move per launch (the per-unit figures of the
@@ -302,11 +316,7 @@ def run_ours(args, wl):
     clk = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms, value = job_throughput(total_ms, args.steps, dist, dev)
     assert rep["status"] == "ok" and rep["relres"] < 1e-10, rep
     refinements = rep["refinements"]
 
