@@ -64,6 +64,8 @@ enum {
 };
 
 /* Parameters of the method: the paper's names (Sec. II, III, VII). */
+#define OR_MAX_S 4
+
 typedef struct {
   int df;        /* fractional bits d_f of the Q(d_m).(d_f) word        */
   int alpha_a;   /* exponent of the initial scaling, eq. (3)            */
@@ -72,6 +74,8 @@ typedef struct {
   int beta7, beta8, beta10, beta11a, beta11b, beta13, beta15, beta16a, beta16b;
   double tol;    /* epsilon of Fig. 1                                   */
   int max_refine;
+  int s;         /* correction terms of eq. (AA) used in every refinement,
+                    s(k) = s (0 ... OR_MAX_S)                          */
 } or_params;
 
 typedef struct {
@@ -247,6 +251,39 @@ int or_cast(int nnz, const double *a, i64 *abar) {
   return OR_OK;
 }
 
+/* Sec. IV-C, eq. (alpha1) and (A): Abar_0 = trunc(A); then, for l = 1 ... S,
+ * with the FP remainder A_l (A_1 = A - Abar_0), alpha_l = alpha_a -
+ * floor(log2 max |A_l|), Abar_l = trunc(A_l 2^alpha_l) and A_(l+1) =
+ * A_l - Abar_l 2^-alpha_l (every step exact in FP64).  terms holds
+ * (S+1) x nnz values (term 0 first), alphas[l] the exponents (alphas[0] =
+ * 0).  Returns the number of correction terms built: fewer than S when a
+ * remainder is zero (A is then represented exactly). */
+int or_multiterm(int nnz, const double *a, int alpha_a, int S, i64 *terms, int *alphas) {
+  double *R = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+  int built = 0;
+  alphas[0] = 0;
+  for (int k = 0; k < nnz; ++k) {
+    terms[k] = (i64)a[k];
+    R[k] = a[k] - (double)terms[k];
+  }
+  for (int l = 1; l <= S; ++l) {
+    double mx = 0.0;
+    for (int k = 0; k < nnz; ++k) mx = fmax(mx, fabs(R[k]));
+    if (mx == 0.0) break;
+    int al = alpha_a - ilogb(mx);
+    alphas[l] = al;
+    i64 *T = terms + (size_t)l * nnz;
+    for (int k = 0; k < nnz; ++k) {
+      double t = ldexp(R[k], al);
+      T[k] = (i64)t;
+      R[k] = ldexp(t - (double)T[k], -al);
+    }
+    built = l;
+  }
+  free(R);
+  return built;
+}
+
 static int find_diag(int n, const int *rowptr, const int *col, int *diagpos) {
   for (int i = 0; i < n; ++i) {
     diagpos[i] = -1;
@@ -340,6 +377,30 @@ void or_spmv_int(int n, const int *rowptr, const int *col, const i64 *abar,
   }
 }
 
+/* line 5 / eq. (matvec) with s correction terms: each Abar_l v is the
+ * product of an integer matrix program (exact row sums stored as words,
+ * events as in or_spmv_int), divided by 2^alpha_l as a right shift and
+ * added to the result; the sum of the s + 1 words is exact, stored as a
+ * word (an event when it leaves the range).  terms: (s+1) x nnz. */
+void or_spmv_int_s(int n, const int *rowptr, const int *col, int ns, const i64 *terms,
+                   const int *alphas, const i64 *v, i64 *w, i64 *ev) {
+  const int nnz = rowptr[n];
+  for (int i = 0; i < n; ++i) {
+    i128 tot = 0;
+    for (int l = 0; l <= ns; ++l) {
+      const i64 *T = terms + (size_t)l * nnz;
+      i128 acc = 0;
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+        acc += (i128)mul(T[k], v[col[k]], ev);
+      if (out64(acc)) (*ev)++;
+      i64 u = wrap64(acc);
+      tot += (i128)(l == 0 ? u : shr(u, alphas[l]));
+    }
+    if (out64(tot)) (*ev)++;
+    w[i] = wrap64(tot);
+  }
+}
+
 /* line 5', first half: y = Lbar^-1 z by forward substitution with the data
  * types of an FP program changed to integers (Sec. VI-A):
  * y_i = (z_i - sum_{j<i} Lbar_ij y_j) / Lbar_ii, division truncating. */
@@ -406,13 +467,17 @@ void or_resid_fp(int n, const int *rowptr, const int *col, const double *a,
   }
 }
 
-/* same with integer matrix values (line 1 of Fig. 2) */
-static void resid_fp_int(int n, const int *rowptr, const int *col, const i64 *abar,
-                         const double *x, const double *b, double *r) {
+/* same with the matrix of eq. (AA) (line 1 of Fig. 2): its FP64 value
+ * Abar_0 + sum_l Abar_l 2^-alpha_l is exact (a truncation of A's bits) */
+static void resid_fp_int(int n, const int *rowptr, const int *col, int ns, const i64 *terms,
+                         const int *alphas, const double *x, const double *b, double *r) {
+  const int nnz = rowptr[n];
   for (int i = 0; i < n; ++i) {
     double s = 0.0;
     for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-      double p = (double)abar[k] * x[col[k]];
+      double av = (double)terms[k];
+      for (int l = 1; l <= ns; ++l) av = av + ldexp((double)terms[(size_t)l * nnz + k], -alphas[l]);
+      double p = av * x[col[k]];
       s = s + p;
     }
     r[i] = b[i] - s;
@@ -426,8 +491,10 @@ static void resid_fp_int(int n, const int *rowptr, const int *col, const i64 *ab
 typedef struct {
   int n;
   const int *rowptr, *col;
-  const i64 *abar;                  /* Abar_0 on the pattern of A       */
+  const i64 *abar;                  /* Abar_0 ... Abar_ns, (ns+1) x nnz  */
   const i64 *fac, *ldiag, *udiag;   /* integer ILU factors (precond=1)  */
+  int ns;                           /* correction terms of eq. (AA)     */
+  const int *alphas;                /* their exponents (alphas[0] = 0)  */
 } or_system;
 
 /* Solves Abar x = bk approximately with m steps of Fig. 2 and adds the
@@ -456,7 +523,7 @@ int or_int_gmres(const or_params *P, const or_system *S, const double *bk,
   double nu;
 
   /* line 1 (FP): r0 = bk - Abar xk; line 1': r0 = Mbar^-1 (bk - Abar xk) */
-  resid_fp_int(n, S->rowptr, S->col, S->abar, xk, bk, r);
+  resid_fp_int(n, S->rowptr, S->col, S->ns, S->abar, S->alphas, xk, bk, r);
   if (P->precond) {
     or_lsolve_fp(n, S->rowptr, S->col, S->fac, S->ldiag, r, t);
     or_usolve_fp(n, S->rowptr, S->col, S->fac, S->udiag, t, r);
@@ -476,7 +543,10 @@ int or_int_gmres(const or_params *P, const or_system *S, const double *bk,
   for (int j = 0; j < m; ++j) {
     i64 *vj = V + (size_t)j * n;
     /* line 5: w = Abar v_j;  line 5': w = Ubar^-1 Lbar^-1 Abar v_j */
-    or_spmv_int(n, S->rowptr, S->col, S->abar, vj, w, &ev[EV_L5]);
+    if (S->ns > 0)
+      or_spmv_int_s(n, S->rowptr, S->col, S->ns, S->abar, S->alphas, vj, w, &ev[EV_L5]);
+    else
+      or_spmv_int(n, S->rowptr, S->col, S->abar, vj, w, &ev[EV_L5]);
     if (P->precond) {
       or_lsolve_int(n, S->rowptr, S->col, S->fac, S->ldiag, w, yv, &ev[EV_L5P]);
       or_usolve_int(n, S->rowptr, S->col, S->fac, S->udiag, yv, w, &ev[EV_L5P]);
@@ -714,7 +784,10 @@ int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
   double *a = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
   double *b = (double *)malloc(sizeof(double) * (size_t)n);
   double *d = (double *)malloc(sizeof(double) * (size_t)n);
-  i64 *abar = (i64 *)malloc(sizeof(i64) * (size_t)(nnz ? nnz : 1));
+  const int S_req = P->s < 0 ? 0 : (P->s > OR_MAX_S ? OR_MAX_S : P->s);
+  i64 *abar = (i64 *)malloc(sizeof(i64) * (size_t)(nnz ? nnz : 1) * (size_t)(S_req + 1));
+  int alphas[OR_MAX_S + 1] = {0};
+  int ns = 0;
   double *f = NULL;
   int *diagpos = NULL;
   i64 *fac = NULL, *ldg = NULL, *udg = NULL;
@@ -726,6 +799,7 @@ int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
   if (st) goto out;
   st = or_cast(nnz, a, abar);
   if (st) goto out;
+  if (S_req > 0) ns = or_multiterm(nnz, a, P->alpha_a, S_req, abar, alphas);
   if (P->precond) {
     f = (double *)malloc(sizeof(double) * (size_t)nnz);
     diagpos = (int *)malloc(sizeof(int) * (size_t)n);
@@ -738,7 +812,7 @@ int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
     if (st) goto out;
   }
   {
-    or_system S = {n, rowptr, col, abar, fac, ldg, udg};
+    or_system S = {n, rowptr, col, abar, fac, ldg, udg, ns, alphas};
     double nb = or_norm2(n, b);
     st = OR_ENOCONV;
     for (int k = 0;; ++k) {
@@ -789,7 +863,18 @@ int or_int_gmres_flat(const or_params *P, int n, const int *rowptr, const int *c
                       const i64 *udiag, const double *bk, double *xk, i64 *V,
                       i64 *H, i64 *Hraw, i64 *cs, i64 *sn, i64 *g, int *jeff,
                       double *nu, i64 *ev) {
-  or_system S = {n, rowptr, col, abar, fac, ldiag, udiag};
+  static const int a0[1] = {0};
+  or_system S = {n, rowptr, col, abar, fac, ldiag, udiag, 0, a0};
+  return or_int_gmres(P, &S, bk, xk, V, H, Hraw, cs, sn, g, jeff, nu, ev);
+}
+
+/* the same with ns correction terms: terms (ns+1) x nnz, alphas ns+1 */
+int or_int_gmres_flat_s(const or_params *P, int n, const int *rowptr, const int *col,
+                        int ns, const i64 *terms, const int *alphas, const i64 *fac,
+                        const i64 *ldiag, const i64 *udiag, const double *bk, double *xk,
+                        i64 *V, i64 *H, i64 *Hraw, i64 *cs, i64 *sn, i64 *g, int *jeff,
+                        double *nu, i64 *ev) {
+  or_system S = {n, rowptr, col, terms, fac, ldiag, udiag, ns, alphas};
   return or_int_gmres(P, &S, bk, xk, V, H, Hraw, cs, sn, g, jeff, nu, ev);
 }
 

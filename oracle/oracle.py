@@ -49,7 +49,7 @@ class _Params(C.Structure):
                 ("beta7", C.c_int), ("beta8", C.c_int), ("beta10", C.c_int),
                 ("beta11a", C.c_int), ("beta11b", C.c_int), ("beta13", C.c_int),
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
-                ("tol", C.c_double), ("max_refine", C.c_int)]
+                ("tol", C.c_double), ("max_refine", C.c_int), ("s", C.c_int)]
 
 
 class _Report(C.Structure):
@@ -90,6 +90,7 @@ class Params:
     beta16b: int = 14
     tol: float = 1e-10
     max_refine: int = 60
+    s: int = 0               # correction terms of eq. (AA), s(k) = s
 
     @staticmethod
     def table4(m: int = 30, **kw) -> "Params":
@@ -109,7 +110,7 @@ class Params:
         return _Params(self.df, self.alpha_a, self.m, self.precond, self.beta7,
                        self.beta8, self.beta10, self.beta11a, self.beta11b,
                        self.beta13, self.beta15, self.beta16a, self.beta16b,
-                       float(self.tol), self.max_refine)
+                       float(self.tol), self.max_refine, self.s)
 
 
 @dataclass
@@ -269,6 +270,36 @@ def spmv_int(rowptr, col, abar, v):
     return w, int(ev.value)
 
 
+def multiterm(a, alpha_a: int, S: int):
+    """Eq. (alpha1), (A): Abar_0 ... Abar_s (s <= S, fewer when a remainder
+    is zero) and their exponents.  Returns (terms (s+1) x nnz, alphas)."""
+    a = _f64(a)
+    nnz = len(a)
+    terms = np.zeros((S + 1, max(nnz, 1)), dtype=np.int64)
+    alphas = np.zeros(S + 1, dtype=np.int32)
+    f = _sig("or_multiterm", _I32, [_I32, C.POINTER(_F64), _I32, _I32, C.POINTER(_I64),
+                                    C.POINTER(_I32)])
+    ns = f(nnz, _p(a, _F64), alpha_a, S, _p(terms, _I64), _p(alphas, _I32))
+    return terms[: ns + 1, :nnz].copy(), alphas[: ns + 1].copy()
+
+
+def spmv_int_s(rowptr, col, terms, alphas, v):
+    """Line 5 with eq. (matvec): w = sum_l (Abar_l v) / 2^alpha_l.
+    Returns (w, events)."""
+    rowptr, col, v = _i32(rowptr), _i32(col), _i64(v)
+    terms = np.ascontiguousarray(terms, dtype=np.int64)
+    alphas = _i32(alphas)
+    n = len(rowptr) - 1
+    w = np.empty(n, dtype=np.int64)
+    ev = _I64(0)
+    f = _sig("or_spmv_int_s", None, [_I32, C.POINTER(_I32), C.POINTER(_I32), _I32,
+                                     C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64),
+                                     C.POINTER(_I64), C.POINTER(_I64)])
+    f(n, _p(rowptr, _I32), _p(col, _I32), len(alphas) - 1, _p(terms, _I64), _p(alphas, _I32),
+      _p(v, _I64), _p(w, _I64), C.byref(ev))
+    return w, int(ev.value)
+
+
 def _solve_int(name, rowptr, col, fac, diag, z):
     rowptr, col, fac, diag, z = _i32(rowptr), _i32(col), _i64(fac), _i64(diag), _i64(z)
     n = len(rowptr) - 1
@@ -331,6 +362,9 @@ def setup(rowptr, col, ahat, bhat, params: Params):
     Returns a dict with the scaled system and its integer data."""
     a, b, d = scale(rowptr, col, ahat, bhat, params.alpha_a)
     out = dict(rowptr=_i32(rowptr), col=_i32(col), a=a, b=b, d=d, abar=cast(a))
+    if params.s > 0:
+        terms, alphas = multiterm(a, params.alpha_a, params.s)
+        out.update(terms=terms, alphas=alphas)
     n = len(rowptr) - 1
     if params.precond:
         fv, dp = ilu0(rowptr, col, a)
@@ -362,15 +396,25 @@ def int_gmres(params: Params, sysd: dict, bk, xk=None):
     pc = params._c()
     abar, fac = _i64(sysd["abar"]), _i64(sysd["fac"])
     ld, ud = _i64(sysd["ldiag"]), _i64(sysd["udiag"])
-    f = _sig("or_int_gmres_flat", _I32,
-             [C.POINTER(_Params), _I32, C.POINTER(_I32), C.POINTER(_I32)]
-             + [C.POINTER(_I64)] * 4 + [C.POINTER(_F64)] * 2
-             + [C.POINTER(_I64)] * 6 + [C.POINTER(_I32), C.POINTER(_F64),
-                                         C.POINTER(_I64)])
-    early = f(C.byref(pc), n, _p(rowptr, _I32), _p(col, _I32), _p(abar, _I64),
-              _p(fac, _I64), _p(ld, _I64), _p(ud, _I64), _p(bk, _F64), _p(x, _F64),
-              _p(V, _I64), _p(H, _I64), _p(Hraw, _I64), _p(cs, _I64), _p(sn, _I64),
-              _p(g, _I64), C.byref(jeff), C.byref(nu), _p(ev, _I64))
+    tail = [C.POINTER(_I64)] * 3 + [C.POINTER(_F64)] * 2 + [C.POINTER(_I64)] * 6 \
+        + [C.POINTER(_I32), C.POINTER(_F64), C.POINTER(_I64)]
+    outs = (_p(bk, _F64), _p(x, _F64), _p(V, _I64), _p(H, _I64), _p(Hraw, _I64),
+            _p(cs, _I64), _p(sn, _I64), _p(g, _I64), C.byref(jeff), C.byref(nu), _p(ev, _I64))
+    if "terms" in sysd and len(sysd["alphas"]) > 1:
+        terms = np.ascontiguousarray(sysd["terms"], dtype=np.int64)
+        alphas = _i32(sysd["alphas"])
+        f = _sig("or_int_gmres_flat_s", _I32,
+                 [C.POINTER(_Params), _I32, C.POINTER(_I32), C.POINTER(_I32), _I32,
+                  C.POINTER(_I64), C.POINTER(_I32)] + tail)
+        early = f(C.byref(pc), n, _p(rowptr, _I32), _p(col, _I32), len(alphas) - 1,
+                  _p(terms, _I64), _p(alphas, _I32), _p(fac, _I64), _p(ld, _I64),
+                  _p(ud, _I64), *outs)
+    else:
+        f = _sig("or_int_gmres_flat", _I32,
+                 [C.POINTER(_Params), _I32, C.POINTER(_I32), C.POINTER(_I32),
+                  C.POINTER(_I64)] + tail)
+        early = f(C.byref(pc), n, _p(rowptr, _I32), _p(col, _I32), _p(abar, _I64),
+                  _p(fac, _I64), _p(ld, _I64), _p(ud, _I64), *outs)
     return dict(x=x, V=V, H=H.T.copy(), Hraw=Hraw.T.copy(), cs=cs, sn=sn, g=g,
                 jeff=int(jeff.value), nu=float(nu.value), ev=ev, early=bool(early))
 
@@ -417,5 +461,6 @@ def fp_gmres(sysd: dict, params: Params, bk, xk=None):
 
 __all__ = ["build", "Params", "Report", "EV_NAMES", "shr", "isqrt", "fx_mul",
            "fx_div", "fx_sqrt", "norm2", "scale", "cast", "ilu0", "ilu_int",
-           "spmv_int", "lsolve_int", "usolve_int", "lsolve_fp", "usolve_fp",
+           "spmv_int", "multiterm", "spmv_int_s", "lsolve_int", "usolve_int",
+           "lsolve_fp", "usolve_fp",
            "resid_fp", "setup", "int_gmres", "ir_solve", "fp_gmres"]
