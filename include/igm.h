@@ -87,10 +87,15 @@ typedef struct {
   int trsv_cluster;/* chunks per thread-block cluster of the substitutions:
                     0 automatic, 1 none, 2, 4 or 8 (results do not depend
                     on it)                                               */
-  int reserved[4];
+  int s;         /* correction terms of Sec. IV-C, eq. (AA), used in every
+                    refinement (s(k) = s, 0 ... IGM_MAX_S): the matrix is
+                    Abar_0 + sum_l Abar_l / 2^alpha_l and line 5 adds each
+                    term's product shifted right by alpha_l (eq. matvec)  */
+  int reserved[3];
 } igm_params;
 
 #define IGM_MAX_M 128
+#define IGM_MAX_S 4
 
 /* Per-solve report.  Histories are indexed by refinement k (Fig. 1). */
 typedef struct {

@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("beta11a", C.c_int), ("beta11b", C.c_int), ("beta13", C.c_int),
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
-                ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("reserved", C.c_int * 4)]
+                ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("s", C.c_int),
+                ("reserved", C.c_int * 3)]
 
     def replace(self, **kw) -> "Params":
         p = Params()

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -155,6 +156,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.trsv_maxw = maxw;
   B.trsv_maxk = maxk;
   B.trsv_cluster = hs[0]->prm.trsv_cluster;
+  B.max_ns = 0;
+  for (auto hh : hs) B.max_ns = std::max(B.max_ns, hh->hs.ns);
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;
@@ -283,6 +286,7 @@ igm_status check_params(const igm_params *p) {
   if (!(p->tol >= 0.0)) return fail(IGM_EINVAL, "tol must be >= 0");
   if (p->inner != 0 && p->inner != 1) return fail(IGM_EINVAL, "inner must be 0 or 1");
   if (p->trsv_chunk < 0) return fail(IGM_EINVAL, "trsv_chunk must be >= 0");
+  if (p->s < 0 || p->s > IGM_MAX_S) return fail(IGM_EINVAL, "s must be 0 ... %d", IGM_MAX_S);
   if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
         p->trsv_cluster == 4 || p->trsv_cluster == 8))
     return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
@@ -395,20 +399,27 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     hsp[sl + 1] = hsp[sl] + 32ll * len;
   }
   const size_t nzs = hsp[nsl] > 0 ? (size_t)hsp[nsl] : 1;
+  const int S = params->s;  // correction terms requested (eq. AA)
   long long *sptr;
   i64 *sval;
   int *scol;
+  double *mtR = nullptr;
+  unsigned long long *mtmax = nullptr;
   Arena &A = h->arena;
   A.want(&sptr, nsl + 1);
-  A.want(&sval, nzs);
+  A.want(&sval, nzs * (S + 1));
   A.want(&scol, nzs);
+  if (S > 0) {
+    A.want(&mtR, nz);
+    A.want(&mtmax, 1);
+  }
   A.want(&rp, n + 1);
   A.want(&cl, nz);
   A.want(&dp, n);
   A.want(&ahat, nz);
   A.want(&a, nz);
   A.want(&dd, n);
-  A.want(&abar, nz);
+  A.want(&abar, nz * (S + 1));
   if (ilu) {
     A.want(&f, nz);
     A.want(&fac, nz);
@@ -477,8 +488,28 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   }
   launch_scale(n, rp, ahat, params->alpha_a, a, dd, err, s);
   launch_cast(nnz, a, abar, err, s);
+  // eq. (alpha1), (A): the correction terms, each from the exact FP64
+  // remainder of the previous ones; fewer than S when a remainder is zero
+  int ns = 0, alphas[IGM_MAX_S + 1] = {0};
+  if (S > 0 && nnz > 0) {
+    launch_mt_init(nnz, a, abar, mtR, s);
+    for (int l = 1; l <= S; ++l) {
+      unsigned long long hmx = 0;
+      CKH(cudaMemsetAsync(mtmax, 0, sizeof(unsigned long long), s));
+      launch_mt_max(nnz, mtR, mtmax, s);
+      CKH(cudaMemcpyAsync(&hmx, mtmax, sizeof(hmx), cudaMemcpyDeviceToHost, s));
+      CKH(cudaStreamSynchronize(s));
+      double mx;
+      std::memcpy(&mx, &hmx, sizeof(mx));
+      if (mx == 0.0) break;
+      alphas[l] = params->alpha_a - std::ilogb(mx);
+      launch_mt_term(nnz, mtR, alphas[l], abar + (size_t)l * nnz, s);
+      ns = l;
+    }
+  }
   CKH(cudaMemcpyAsync(sptr, hsp.data(), sizeof(long long) * (nsl + 1), cudaMemcpyHostToDevice, s));
-  launch_sell_fill(n, nsl, rp, cl, abar, sptr, sval, scol, s);
+  for (int l = 0; l <= ns; ++l)
+    launch_sell_fill(n, nsl, rp, cl, abar + (size_t)l * nnz, sptr, sval + (size_t)l * nzs, scol, s);
   CKH(cudaGetLastError());
   CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKH(cudaStreamSynchronize(s));
@@ -620,6 +651,9 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.sptr = sptr;
   d.sval = sval;
   d.scol = scol;
+  d.nnz_sell = (long long)nzs;
+  d.ns = ns;
+  for (int l = 0; l <= IGM_MAX_S; ++l) d.alphas[l] = alphas[l];
   d.f = f;
   d.fac = fac;
   d.ldiag = ld;
@@ -722,6 +756,7 @@ long long handle_bytes_estimate(int n, int nnz, const igm_params *p) {
   r += 4 * (N + 1) + 4 * Z + 4 * N;                 // rowptr, col, diagpos
   r += 8 * Z * 3 + 8 * N;                           // ahat, a, abar, d
   r += 12 * Z + 12 * N + N / 4 + 8;                 // SELL-32 copy of abar (estimate)
+  r += (long long)p->s * (16 * Z + 8 * N) + (p->s > 0 ? 8 * Z : 0);  // correction terms
   if (p->precond) r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
   r += 8 * N * 8 + 8 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
   return r + 64 * 256 + (long long)sizeof(SysScal) + sizeof(SysDev);

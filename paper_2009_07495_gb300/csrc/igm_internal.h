@@ -91,8 +91,13 @@ struct SysDev {
   // stored column-major: entry k of row 32 s + l at sptr[s] + 32 k + l;
   // padding has value 0) for the line-5 SpMV
   const long long *sptr;
-  const i64 *sval;
+  const i64 *sval;               // (ns + 1) terms, each nnz_sell values
   const int *scol;
+  long long nnz_sell;            // slots per term of the SELL-32 copy
+  // correction terms of eq. (AA): abar and sval hold ns + 1 terms (term l at
+  // l * nnz, resp. l * nnz_sell); alphas[0] = 0
+  int ns;
+  int alphas[IGM_MAX_S + 1];
   const double *f;                       // FP64 ILU(0) factors
   const i64 *fac, *ldiag, *udiag;        // integer factors
   // substitution schedules of the two factors, tri[0] = L, tri[1] = U
@@ -146,6 +151,7 @@ struct BatchDev {
   int trsv_maxw;           // most rows of one level group
   int trsv_maxk;           // most strict entries of one factor row
   int trsv_cluster;        // CTAs per cluster of the substitutions (0 automatic)
+  int max_ns;              // most correction terms of eq. (AA) of a system
 };
 
 // vector selectors for the generic max / norm kernels

@@ -34,6 +34,10 @@ void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, i
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
                     cudaStream_t st);
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st);
+void launch_mt_init(long long nnz, const double *a, const i64 *abar, double *R,
+                    cudaStream_t st);
+void launch_mt_max(long long nnz, const double *R, unsigned long long *mx, cudaStream_t st);
+void launch_mt_term(long long nnz, double *R, int al, i64 *T, cudaStream_t st);
 void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
                       const long long *sptr, i64 *sval, int *scol, cudaStream_t st);
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,

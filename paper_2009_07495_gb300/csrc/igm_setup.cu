@@ -85,6 +85,34 @@ __global__ void s_cast(long long nnz, const double *a, i64 *abar, unsigned *err)
   }
 }
 
+// eq. (A): remainder of term 0, R = A - Abar_0 (exact)
+__global__ void s_mt_init(long long nnz, const double *a, const i64 *abar, double *R) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x)
+    R[k] = __dsub_rn(a[k], (double)abar[k]);
+}
+
+// max |R| as the bit pattern of a non-negative double (ordered like the value)
+__global__ void s_mt_max(long long nnz, const double *R, unsigned long long *mx) {
+  unsigned long long m = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(fabs(R[k])));
+  atomicMax(mx, m);
+}
+
+// eq. (alpha1): Abar_l = trunc(R 2^alpha_l), then R = (R 2^alpha_l - Abar_l)
+// 2^-alpha_l (both exact)
+__global__ void s_mt_term(long long nnz, double *R, int al, i64 *T) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double t = scalbn(R[k], al);
+    const i64 q = __double2ll_rz(t);
+    T[k] = q;
+    R[k] = scalbn(__dsub_rn(t, (double)q), -al);
+  }
+}
+
 // Ā in SELL-32 (see SysDev): one thread per slot row (padding rows of the
 // last slice included)
 __global__ void s_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
@@ -251,6 +279,16 @@ void launch_level_order(int n, int lower, int R, int L, const int *level, const 
   s_scan<<<1, 1024, 0, st>>>(L, cnt, lptr);
   cudaMemcpyAsync(cnt, lptr, sizeof(int) * L, cudaMemcpyDeviceToDevice, st);
   s_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, lower, R, level, levb, cnt, order);
+}
+void launch_mt_init(long long nnz, const double *a, const i64 *abar, double *R,
+                    cudaStream_t st) {
+  s_mt_init<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, a, abar, R);
+}
+void launch_mt_max(long long nnz, const double *R, unsigned long long *mx, cudaStream_t st) {
+  s_mt_max<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, R, mx);
+}
+void launch_mt_term(long long nnz, double *R, int al, i64 *T, cudaStream_t st) {
+  s_mt_term<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, R, al, T);
 }
 void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
                       const long long *sptr, i64 *sval, int *scol, cudaStream_t st) {

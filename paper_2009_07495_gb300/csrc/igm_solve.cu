@@ -196,10 +196,17 @@ __global__ void k_resid_int(BatchDev B) {
   Tile tl = B.tiles[blockIdx.x];
   const SysDev *s = B.sys[tl.sys];
   if (!g_cyc(s->sc)) return;
+  const int ns = s->ns;
+  const long long nnz = s->nnz;
   TILE_LOOP(i) {
     double acc = 0.0;
-    for (int k = s->rowptr[i]; k < s->rowptr[i + 1]; ++k)
-      acc = __dadd_rn(acc, __dmul_rn((double)s->abar[k], s->xk[s->col[k]]));
+    for (int k = s->rowptr[i]; k < s->rowptr[i + 1]; ++k) {
+      // the FP64 value of the matrix of eq. (AA) (exact: a truncation of A)
+      double av = (double)s->abar[k];
+      for (int l = 1; l <= ns; ++l)
+        av = __dadd_rn(av, scalbn((double)s->abar[l * nnz + k], -s->alphas[l]));
+      acc = __dadd_rn(acc, __dmul_rn(av, s->xk[s->col[k]]));
+    }
     s->r[i] = __dsub_rn(s->t[i], acc);
   }
 }
@@ -262,6 +269,7 @@ __global__ void k_cast_v1(BatchDev B) {
 // per row (consecutive threads read consecutive rows' entries, which share
 // cache lines)
 // ---------------------------------------------------------------------------
+template <bool MT>
 __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     B.ticket[2] = 0;
@@ -280,32 +288,41 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   // SELL-32: the 32 rows of a slice are one warp's lanes, so every load of
   // values and columns is one coalesced 256 / 128-byte access; padding
   // entries have value 0 (no product, no event)
+  const int ns = MT ? s->ns : 0;
   TILE_LOOP(i) {
     const int sl = i >> 5;
     const long long base = sptr[sl] + (i & 31);
     const int len = (int)((sptr[sl + 1] - sptr[sl]) >> 5);
-    i128 acc = 0;
-    const i64 *pv = sval + base;
     const int *pc = scol + base;
-    // eight entries at a time: all value and column loads, then all
-    // gathers, then the products (memory-level parallelism per thread)
-    for (int k0 = 0; k0 < len; k0 += 8) {
-      i64 a[8];
-      int c[8];
+    // eq. (matvec): one integer product per term; term l > 0 is divided by
+    // 2^alpha_l (a right shift of its stored word) and the words are added
+    // exactly (s = 0: the plain product)
+    i128 tot = 0;
+    for (int l = 0; l <= ns; ++l) {
+      const i64 *pv = sval + l * s->nnz_sell + base;
+      i128 acc = 0;
+      // eight entries at a time: all value and column loads, then all
+      // gathers, then the products (memory-level parallelism per thread)
+      for (int k0 = 0; k0 < len; k0 += 8) {
+        i64 a[8];
+        int c[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const bool ok = k0 + u < len;
-        a[u] = ok ? __ldcs(pv + 32 * (k0 + u)) : 0;
-        c[u] = ok ? __ldcs(pc + 32 * (k0 + u)) : i;
+        for (int u = 0; u < 8; ++u) {
+          const bool ok = k0 + u < len;
+          a[u] = ok ? __ldcs(pv + 32 * (k0 + u)) : 0;
+          c[u] = ok ? __ldcs(pc + 32 * (k0 + u)) : i;
+        }
+        i64 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
       }
-      i64 x[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
+      ev += out64(acc);
+      tot += (i128)(l == 0 ? wrap(acc) : shr(wrap(acc), s->alphas[l]));
     }
-    ev += out64(acc);
-    s->w[i] = wrap(acc);
+    ev += out64(tot);
+    s->w[i] = wrap(tot);
   }
   flush_ev(ev, &sc->ev[IGM_EV_L5]);
 }
@@ -451,7 +468,8 @@ void launch_cast_v1(const BatchDev &B, cudaStream_t st) {
   k_cast_v1<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);
 }
 void launch_spmv(const BatchDev &B, int j, cudaStream_t st) {
-  k_spmv<<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
+  if (B.max_ns > 0) k_spmv<true><<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
+  else k_spmv<false><<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
 }
 void launch_backsub(const BatchDev &B, cudaStream_t st) {
   k_backsub<<<nb_sys(B), 128, 0, st>>>(B);

@@ -27,7 +27,7 @@ def _oparams(orc, P):
     return orc.Params(df=P.df, alpha_a=P.alpha_a, m=P.m, precond=P.precond, beta7=P.beta7,
                       beta8=P.beta8, beta10=P.beta10, beta11a=P.beta11a, beta11b=P.beta11b,
                       beta13=P.beta13, beta15=P.beta15, beta16a=P.beta16a, beta16b=P.beta16b,
-                      tol=P.tol, max_refine=P.max_refine)
+                      tol=P.tol, max_refine=P.max_refine, s=P.s)
 
 
 def _dev(a):
@@ -111,6 +111,61 @@ def test_ir_solve_bit_exact(L, orc, name, sf, prec, m):
     assert rep["relres_unscaled"] == ro.relres_unscaled
     np.testing.assert_array_equal(xg, xo)
     solver.close()
+
+
+MT_CASES = [
+    ("cd2d_20_s1", lambda: W.small_cd2d(20, seed=48), 0, 20, 1),
+    ("cd2d_20_s3", lambda: W.small_cd2d(20, seed=48), 0, 20, 3),
+    ("cd3d_10_ilu_s2", lambda: W.small_cd3d(10, seed=49), 1, 15, 2),
+]
+
+
+@pytest.mark.parametrize("name,sf,prec,m,S", MT_CASES, ids=[c[0] for c in MT_CASES])
+def test_multiterm_bit_exact(L, orc, name, sf, prec, m, S):
+    """Sec. IV-C with s correction terms (eq. AA, matvec): one inner solve
+    from a non-zero guess (line 1 with the multi-term matrix) and the whole
+    refinement loop equal the oracle's bit for bit."""
+    s = sf()
+    P = L.params_default(prec, m)
+    P.s = S
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    assert 2 <= len(d["alphas"]) <= S + 1     # fewer when A is exact sooner
+    bk = d["b"] / np.abs(d["b"]).max()
+    x0 = np.random.default_rng(6).standard_normal(s.n) * 1e-3
+    o = orc.int_gmres(_oparams(orc, P), d, bk, x0)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    _compare_inner(solver.state(), o, s.n, m)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert rep["status"] == "ok" and rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    solver.close()
+
+
+def test_multiterm_coarse_word_fewer_refinements(L, orc):
+    """A coarse word (alpha_a = 6): s = 0 needs many refinements, s = 2
+    far fewer, on the GPU exactly as in the oracle."""
+    s = W.small_cd2d(16, seed=4)
+    counts = []
+    for S in (0, 2):
+        P = L.params_default(0, 30)
+        P.alpha_a, P.s = 6, S
+        P.beta7 = P.beta8 = P.beta10 = P.beta11a = P.beta13 = P.beta15 = P.beta16a = 6
+        P.beta11b = P.beta16b = 4
+        xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+        solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+        x, rep = solver.ir_solve(_dev(s.b))
+        assert rep["status"] == "ok" and rep["refinements"] == ro.refinements
+        np.testing.assert_array_equal(x.cpu().numpy(), xo)
+        counts.append(rep["refinements"])
+        solver.close()
+    assert counts[1] < counts[0], counts
 
 
 def test_one_by_one(L):
