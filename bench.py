@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="cfg2: systems in the batch")
     ap.add_argument("--requests", type=int, default=400, help="cfg3: requests served")
+    ap.add_argument("--terms", type=int, default=0,
+                    help="correction terms of the multi-term matrix (Sec. IV-C, s)")
     return ap.parse_args()
 
 
@@ -282,6 +284,7 @@ def run_ours(args, wl):
     sysw = wl["gen"]()
     n, nnz = sysw.n, sysw.nnz
     P = L.params_default(wl["precond"], wl["m"])
+    P.s = args.terms
     rp = torch.from_numpy(sysw.rowptr).to(dev)
     cl = torch.from_numpy(sysw.col).to(dev)
     vl = torch.from_numpy(sysw.val).to(dev)
@@ -406,7 +409,7 @@ def run_ours(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "m": wl["m"],
-                       "refinements": refinements, "relres": rep["relres"],
+                       "refinements": refinements, "relres": rep["relres"], "terms_s": args.terms,
                        "inner_steps": rep["inner_steps"],
                        "l2": "working set (~2 GB) > L2, no flush",
                        "parallelism": f"replicas x{world}"},
