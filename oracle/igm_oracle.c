@@ -70,7 +70,8 @@ typedef struct {
   int df;        /* fractional bits d_f of the Q(d_m).(d_f) word        */
   int alpha_a;   /* exponent of the initial scaling, eq. (3)            */
   int m;         /* Arnoldi steps per inner solve                       */
-  int precond;   /* 0: none, 1: integer ILU(0) (Sec. VI)                */
+  int precond;   /* 0: none, 1: integer ILU(0) (Sec. VI), 2: integer
+                    Gauss-Seidel (Sec. VII-D) in the same factor form   */
   int beta7, beta8, beta10, beta11a, beta11b, beta13, beta15, beta16a, beta16b;
   double tol;    /* epsilon of Fig. 1                                   */
   int max_refine;
@@ -325,6 +326,25 @@ int or_ilu0(int n, const int *rowptr, const int *col, const double *a, double *f
     }
     if (f[diagpos[i]] == 0.0) return OR_EZERO_PIVOT;
   }
+  return OR_OK;
+}
+
+/* The Gauss-Seidel preconditioner M = D + L_A (Sec. VII-D mentions it; the
+ * reading here): written as M = (I + L_A D^-1) D it has the form of the
+ * ILU factors, with unit lower factor entries a_ij / a_jj (j < i, correctly
+ * rounded), pivots a_ii and no strict upper part.  f receives that factor
+ * storage, so eq. (dldr)-(ilu2) and the substitutions apply unchanged. */
+int or_gs_factors(int n, const int *rowptr, const int *col, const double *a, double *f,
+                  int *diagpos) {
+  int st = find_diag(n, rowptr, col, diagpos);
+  if (st) return st;
+  for (int i = 0; i < n; ++i)
+    if (a[diagpos[i]] == 0.0) return OR_EZERO_PIVOT;
+  for (int i = 0; i < n; ++i)
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int j = col[k];
+      f[k] = j < i ? a[k] / a[diagpos[j]] : (j == i ? a[k] : 0.0);
+    }
   return OR_OK;
 }
 
@@ -806,7 +826,8 @@ int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
     fac = (i64 *)malloc(sizeof(i64) * (size_t)nnz);
     ldg = (i64 *)malloc(sizeof(i64) * (size_t)n);
     udg = (i64 *)malloc(sizeof(i64) * (size_t)n);
-    st = or_ilu0(n, rowptr, col, a, f, diagpos);
+    st = P->precond == 2 ? or_gs_factors(n, rowptr, col, a, f, diagpos)
+                         : or_ilu0(n, rowptr, col, a, f, diagpos);
     if (st) goto out;
     st = or_ilu_int(n, rowptr, col, f, diagpos, fac, ldg, udg);
     if (st) goto out;

@@ -239,6 +239,22 @@ def ilu0(rowptr, col, a):
     return fv, dp
 
 
+def gs_factors(rowptr, col, a):
+    """The Gauss-Seidel preconditioner D + L_A in the ILU factor form
+    (unit lower a_ij / a_jj, pivots a_ii, no upper part).  Returns
+    (f, diagpos)."""
+    rowptr, col, a = _i32(rowptr), _i32(col), _f64(a)
+    n = len(rowptr) - 1
+    f = np.empty_like(a)
+    dp = np.empty(n, dtype=np.int32)
+    fn = _sig("or_gs_factors", _I32, [_I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F64),
+                                      C.POINTER(_F64), C.POINTER(_I32)])
+    st = fn(n, _p(rowptr, _I32), _p(col, _I32), _p(a, _F64), _p(f, _F64), _p(dp, _I32))
+    if st:
+        raise ValueError(f"gs_factors: status {st}")
+    return f, dp
+
+
 def ilu_int(rowptr, col, fv, diagpos):
     """eq. (dldr)-(ilu2): integer factors.  Returns (fac, ldiag, udiag)."""
     rowptr, col, fv, diagpos = _i32(rowptr), _i32(col), _f64(fv), _i32(diagpos)
@@ -367,7 +383,7 @@ def setup(rowptr, col, ahat, bhat, params: Params):
         out.update(terms=terms, alphas=alphas)
     n = len(rowptr) - 1
     if params.precond:
-        fv, dp = ilu0(rowptr, col, a)
+        fv, dp = gs_factors(rowptr, col, a) if params.precond == 2 else ilu0(rowptr, col, a)
         fac, ld, ud = ilu_int(rowptr, col, fv, dp)
         out.update(f=fv, diagpos=dp, fac=fac, ldiag=ld, udiag=ud)
     else:
@@ -461,6 +477,6 @@ def fp_gmres(sysd: dict, params: Params, bk, xk=None):
 
 __all__ = ["build", "Params", "Report", "EV_NAMES", "shr", "isqrt", "fx_mul",
            "fx_div", "fx_sqrt", "norm2", "scale", "cast", "ilu0", "ilu_int",
-           "spmv_int", "multiterm", "spmv_int_s", "lsolve_int", "usolve_int",
+           "spmv_int", "multiterm", "spmv_int_s", "gs_factors", "lsolve_int", "usolve_int",
            "lsolve_fp", "usolve_fp",
            "resid_fp", "setup", "int_gmres", "ir_solve", "fp_gmres"]
