@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="cfg2: systems in the batch")
     ap.add_argument("--requests", type=int, default=400, help="cfg3: requests served")
+    ap.add_argument("--precond", type=int, default=None,
+                    help="override the workload's preconditioner: 0 none, 1 ILU(0), "
+                         "2 Gauss-Seidel")
     ap.add_argument("--terms", type=int, default=0,
                     help="correction terms of the multi-term matrix (Sec. IV-C, s)")
     return ap.parse_args()
@@ -155,14 +158,15 @@ def job_throughput(local_ms: float, steps: int, dist=None, device="cpu") -> tupl
 
 
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
-                      m: int) -> float:
+                      m: int, terms: int = 0) -> float:
     """Bytes the method must move per launch (the per-unit figures of the
-    design notes): SpMV nnz (b_val + 4) + 4(n+1) + 16n (v_j in, w out); Arnoldi step j = m-1:
+    design notes): SpMV nnz ((s+1) b_val + 4) + 4(n+1) + 16n (s correction
+    terms, v_j in, w out); Arnoldi step j = m-1:
     each of the m basis vectors once (8n each), w in and v_m out (8n each);
     one triangular solve (nnz_tri + n) 12 + 16 n; FP64 residual
     nnz 12 + 4(n+1) + 24 n."""
     if kind == "spmv":
-        return nnz * (val_bytes + 4) + 4 * (n + 1) + 16 * n
+        return nnz * ((terms + 1) * val_bytes + 4) + 4 * (n + 1) + 16 * n
     if kind == "arnoldi":
         return 8.0 * n * (m + 2)
     if kind in ("trsv_l", "trsv_u"):
@@ -283,7 +287,8 @@ def run_ours(args, wl):
 
     sysw = wl["gen"]()
     n, nnz = sysw.n, sysw.nnz
-    P = L.params_default(wl["precond"], wl["m"])
+    precond = wl["precond"] if args.precond is None else args.precond
+    P = L.params_default(precond, wl["m"])
     P.s = args.terms
     rp = torch.from_numpy(sysw.rowptr).to(dev)
     cl = torch.from_numpy(sysw.col).to(dev)
@@ -339,7 +344,7 @@ def run_ours(args, wl):
         per_cycle = launches_per_cycle(name, wl["m"])
         kern[name] = dict(ms=kms[k], launches_per_solve=per_cycle * refinements,
                           ms_per_solve=kms[k] * per_cycle * refinements,
-                          gbs=algorithmic_bytes(name, n, nnz, nnz_l, val_bytes, wl["m"])
+                          gbs=algorithmic_bytes(name, n, nnz, nnz_l, val_bytes, wl["m"], args.terms)
                           / (kms[k] * 1e6))
     tot_k = sum(v["ms_per_solve"] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
@@ -410,6 +415,7 @@ def run_ours(args, wl):
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "m": wl["m"],
                        "refinements": refinements, "relres": rep["relres"], "terms_s": args.terms,
+                       "precond": ["none", "ILU(0)", "Gauss-Seidel"][precond],
                        "inner_steps": rep["inner_steps"],
                        "l2": "working set (~2 GB) > L2, no flush",
                        "parallelism": f"replicas x{world}"},

@@ -72,7 +72,9 @@ typedef struct {
   int df;        /* fractional bits d_f of the Q(d_m).(d_f) int64 word (30)  */
   int alpha_a;   /* initial scaling exponent of eq. (3): 16 none, 32 ILU     */
   int m;         /* Arnoldi steps per inner solve, 1..IGM_MAX_M              */
-  int precond;   /* 0: none; 1: integer ILU(0) (Sec. VI-A, lines 1', 5')     */
+  int precond;   /* 0: none; 1: integer ILU(0) (Sec. VI-A, lines 1', 5');   
+                    2: integer Gauss-Seidel (Sec. VII-D), D + L_A in the
+                    factor form of Sec. VI-A (Table 5 shifts by default) */
   int beta7;     /* line 7: shift of w (beta1; beta2 = 0)                    */
   int beta8;     /* line 8: shift of h (beta1)                               */
   int beta10;    /* line 10: beta1 = beta2                                   */

@@ -277,7 +277,8 @@ igm_status check_params(const igm_params *p) {
   if (p->df < 1 || p->df > 62) return fail(IGM_EINVAL, "df out of range");
   if (p->alpha_a < 0 || p->alpha_a > 62) return fail(IGM_EINVAL, "alpha_a out of range");
   if (p->m < 1 || p->m > IGM_MAX_M) return fail(IGM_EINVAL, "m out of range");
-  if (p->precond != 0 && p->precond != 1) return fail(IGM_EINVAL, "precond must be 0 or 1");
+  if (p->precond < 0 || p->precond > 2)
+    return fail(IGM_EINVAL, "precond must be 0 (none), 1 (ILU(0)) or 2 (Gauss-Seidel)");
   const int b[] = {p->beta7, p->beta8, p->beta10, p->beta11a, p->beta11b, p->beta13,
                    p->beta15, p->beta16a, p->beta16b};
   for (int v : b)
@@ -617,10 +618,15 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       T.maxlev = 1 + *std::max_element(hmax.begin(), hmax.end());
       T.maxw = hmaxw;
     }
-    // eq. (ilu) on the L schedule (epoch 2), then the integer factors
-    CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
-    CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
-    launch_ilu0_lv(n, rp, cl, dp, d.tri[0], R, single, f, tick, 2, err, s);
+    // eq. (ilu) on the L schedule (epoch 2), or the Gauss-Seidel factor
+    // form; then the integer factors
+    if (params->precond == 2) {
+      launch_gs_factors(n, rp, cl, dp, a, f, err, s);
+    } else {
+      CKH(cudaMemcpyAsync(f, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+      CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
+      launch_ilu0_lv(n, rp, cl, dp, d.tri[0], R, single, f, tick, 2, err, s);
+    }
     launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
     for (int tr = 0; tr < 2; ++tr)
       launch_pack(n, rp, cl, dp, tr == 0, d.tri[tr].K, ord[tr], fac, ld, ud, f, pcol[tr], pfac[tr],

@@ -40,6 +40,8 @@ void launch_mt_max(long long nnz, const double *R, unsigned long long *mx, cudaS
 void launch_mt_term(long long nnz, double *R, int al, i64 *T, cudaStream_t st);
 void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i64 *abar,
                       const long long *sptr, i64 *sval, int *scol, cudaStream_t st);
+void launch_gs_factors(int n, const int *rowptr, const int *col, const int *diagpos,
+                       const double *a, double *f, unsigned *err, cudaStream_t st);
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,
                     cudaStream_t st);

@@ -214,6 +214,19 @@ __global__ void s_maxw(int L, const int *lptr, int *out) {
   atomicMax(out, w);
 }
 
+// The Gauss-Seidel preconditioner D + L_A in the ILU factor form: unit lower
+// entries a_ij / a_jj, pivots a_ii, no strict upper part (precond = 2)
+__global__ void s_gs_factors(int n, const int *rowptr, const int *col, const int *diagpos,
+                             const double *a, double *f, unsigned *err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (a[diagpos[i]] == 0.0) atomicOr(err, ERR_ZERO_PIVOT);
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int j = col[k];
+      f[k] = j < i ? __ddiv_rn(a[k], a[diagpos[j]]) : (j == i ? a[k] : 0.0);
+    }
+  }
+}
+
 // eq. (dl), (dl2), (l1), (u1), (ilu2): D_l = |d|^1/2, D_u = sgn(d)|d|^1/2,
 // Lbar = trunc(L D_l), Ubar = trunc(D_u U') with U' = D^-1 U
 __global__ void s_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
@@ -297,6 +310,10 @@ void launch_sell_fill(int n, int nsl, const int *rowptr, const int *col, const i
 }
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st) {
   s_maxw<<<grid_for(L, 256), 256, 0, st>>>(L, lptr, out);
+}
+void launch_gs_factors(int n, const int *rowptr, const int *col, const int *diagpos,
+                       const double *a, double *f, unsigned *err, cudaStream_t st) {
+  s_gs_factors<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, diagpos, a, f, err);
 }
 void launch_ilu_int(int n, const int *rowptr, const int *col, const int *diagpos,
                     const double *f, i64 *fac, i64 *ldiag, i64 *udiag, unsigned *err,

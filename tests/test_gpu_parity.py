@@ -168,6 +168,31 @@ def test_multiterm_coarse_word_fewer_refinements(L, orc):
     assert counts[1] < counts[0], counts
 
 
+GS_CASES = [
+    ("cfg0_gs", lambda: W.config0(), 30),
+    ("cd3d_12_gs", lambda: W.small_cd3d(12, seed=50), 20),
+    ("cd3d_10_27pt_gs", lambda: W.small_cd3d(10, seed=51, points=27), 20),
+]
+
+
+@pytest.mark.parametrize("name,sf,m", GS_CASES, ids=[c[0] for c in GS_CASES])
+def test_gauss_seidel_bit_exact(L, orc, name, sf, m):
+    """The integer Gauss-Seidel preconditioner (precond = 2): the refinement
+    loop equals the oracle's bit for bit and has no overflow event."""
+    s = sf()
+    P = L.params_default(2, m)
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert ro.status == "ok" and rep["status"] == "ok"
+    assert rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    assert int(np.abs(np.asarray(rep["ev"])).sum()) == 0
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    solver.close()
+
+
 def test_one_by_one(L):
     """n = 1: Ahat = [2], bhat = [4] gives x = 2 exactly in one refinement."""
     P = L.params_default(0, 5)
