@@ -77,6 +77,9 @@ typedef struct {
   int max_refine;
   int s;         /* correction terms of eq. (AA) used in every refinement,
                     s(k) = s (0 ... OR_MAX_S)                          */
+  int order;     /* 0: natural row order (the paper's); 1: multicolour
+                    order (or_mc_order), the whole method run on the
+                    permuted system P A P^T (P x) = P b                */
 } or_params;
 
 typedef struct {
@@ -293,6 +296,91 @@ static int find_diag(int n, const int *rowptr, const int *col, int *diagpos) {
     if (diagpos[i] < 0) return OR_EZERO_PIVOT;
   }
   return OR_OK;
+}
+
+/* Multicolour ordering, a GPU-motivated reordering of the preconditioned
+ * solver (the paper runs ILU(0) and Gauss-Seidel in the natural order):
+ * greedy distance-1 colouring of the symmetrised pattern of A (i ~ j when
+ * a_ij or a_ji is stored, i != j), rows visited in natural order, each
+ * taking the smallest colour that none of its already coloured neighbours
+ * has.  The new order lists the rows colour by colour, ascending original
+ * index within a colour: perm[new] = old, cptr[c] = first new index of
+ * colour c (cptr has n + 1 entries).  Returns the number of colours. */
+int or_mc_order(int n, const int *rowptr, const int *col, int *perm, int *cptr) {
+  const int nnz = rowptr[n];
+  /* symmetrised adjacency: every stored off-diagonal entry in both rows */
+  int *deg = (int *)calloc((size_t)n + 1, sizeof(int));
+  for (int i = 0; i < n; ++i)
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] != i) {
+        deg[i]++;
+        deg[col[k]]++;
+      }
+  int *aptr = (int *)malloc(sizeof(int) * ((size_t)n + 1));
+  aptr[0] = 0;
+  for (int i = 0; i < n; ++i) aptr[i + 1] = aptr[i] + deg[i];
+  int *adj = (int *)malloc(sizeof(int) * (size_t)(aptr[n] ? aptr[n] : 1));
+  int *fill = (int *)calloc((size_t)n, sizeof(int));
+  for (int i = 0; i < n; ++i)
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] != i) {
+        int j = col[k];
+        adj[aptr[i] + fill[i]++] = j;
+        adj[aptr[j] + fill[j]++] = i;
+      }
+  (void)nnz;
+  /* greedy colouring */
+  int *color = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  int *mark = (int *)malloc(sizeof(int) * ((size_t)n + 1));
+  for (int c = 0; c <= n; ++c) mark[c] = -1;
+  int ncol = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int k = aptr[i]; k < aptr[i + 1]; ++k) {
+      int j = adj[k];
+      if (j < i) mark[color[j]] = i;
+    }
+    int c = 0;
+    while (mark[c] == i) ++c;
+    color[i] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  /* rows by colour, stable */
+  for (int c = 0; c <= ncol; ++c) cptr[c] = 0;
+  for (int i = 0; i < n; ++i) cptr[color[i] + 1]++;
+  for (int c = 0; c < ncol; ++c) cptr[c + 1] += cptr[c];
+  for (int c = ncol + 1; c <= n; ++c) cptr[c] = n;
+  int *pos = (int *)malloc(sizeof(int) * ((size_t)ncol + 1));
+  for (int c = 0; c < ncol; ++c) pos[c] = cptr[c];
+  for (int i = 0; i < n; ++i) perm[pos[color[i]]++] = i;
+  free(deg); free(aptr); free(adj); free(fill); free(color); free(mark); free(pos);
+  return ncol;
+}
+
+/* the permuted system P A P^T: row r of the result is row perm[r] of A with
+ * columns renumbered by the inverse permutation and sorted ascending */
+void or_permute_csr(int n, const int *rowptr, const int *col, const double *val,
+                    const int *perm, int *rowptr2, int *col2, double *val2) {
+  int *inv = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  for (int r = 0; r < n; ++r) inv[perm[r]] = r;
+  rowptr2[0] = 0;
+  for (int r = 0; r < n; ++r) {
+    int o = perm[r], k2 = rowptr2[r];
+    for (int k = rowptr[o]; k < rowptr[o + 1]; ++k) {
+      /* insertion by new column index */
+      int c = inv[col[k]], q = k2;
+      double v = val[k];
+      while (q > rowptr2[r] && col2[q - 1] > c) {
+        col2[q] = col2[q - 1];
+        val2[q] = val2[q - 1];
+        --q;
+      }
+      col2[q] = c;
+      val2[q] = v;
+      ++k2;
+    }
+    rowptr2[r + 1] = k2;
+  }
+  free(inv);
 }
 
 /* eq. (ilu): A ~ L D U by ILU(0), the IKJ row variant restricted to the
@@ -796,9 +884,35 @@ out:
  * xhat (n) receives the solution.  Stops when the scaled relative residual
  * of Fig. 1 is below tol (status OR_OK) or after max_refine inner solves
  * (OR_ENOCONV). */
+static int ir_solve_natural(const or_params *P, int inner, int n, const int *rowptr,
+                            const int *col, const double *ahat, const double *bhat,
+                            double *xhat, or_report *rep);
+
 int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
                 const int *col, const double *ahat, const double *bhat,
                 double *xhat, or_report *rep) {
+  if (P->order != 1) return ir_solve_natural(P, inner, n, rowptr, col, ahat, bhat, xhat, rep);
+  /* multicolour order: the method on P A P^T (P x) = P b */
+  const int nnz = rowptr[n];
+  int *perm = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
+  int *cptr = (int *)malloc(sizeof(int) * ((size_t)n + 1));
+  int *rp2 = (int *)malloc(sizeof(int) * ((size_t)n + 1));
+  int *cl2 = (int *)malloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+  double *av2 = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+  double *b2 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double *x2 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  or_mc_order(n, rowptr, col, perm, cptr);
+  or_permute_csr(n, rowptr, col, ahat, perm, rp2, cl2, av2);
+  for (int r = 0; r < n; ++r) b2[r] = bhat[perm[r]];
+  int st = ir_solve_natural(P, inner, n, rp2, cl2, av2, b2, x2, rep);
+  for (int r = 0; r < n; ++r) xhat[perm[r]] = x2[r];
+  free(perm); free(cptr); free(rp2); free(cl2); free(av2); free(b2); free(x2);
+  return st;
+}
+
+static int ir_solve_natural(const or_params *P, int inner, int n, const int *rowptr,
+                            const int *col, const double *ahat, const double *bhat,
+                            double *xhat, or_report *rep) {
   int nnz = rowptr[n], st;
   memset(rep, 0, sizeof(*rep));
   double *a = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));

@@ -49,7 +49,8 @@ class _Params(C.Structure):
                 ("beta7", C.c_int), ("beta8", C.c_int), ("beta10", C.c_int),
                 ("beta11a", C.c_int), ("beta11b", C.c_int), ("beta13", C.c_int),
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
-                ("tol", C.c_double), ("max_refine", C.c_int), ("s", C.c_int)]
+                ("tol", C.c_double), ("max_refine", C.c_int), ("s", C.c_int),
+                ("order", C.c_int)]
 
 
 class _Report(C.Structure):
@@ -91,6 +92,7 @@ class Params:
     tol: float = 1e-10
     max_refine: int = 60
     s: int = 0               # correction terms of eq. (AA), s(k) = s
+    order: int = 0           # 0 natural, 1 multicolour (mc_order)
 
     @staticmethod
     def table4(m: int = 30, **kw) -> "Params":
@@ -110,7 +112,7 @@ class Params:
         return _Params(self.df, self.alpha_a, self.m, self.precond, self.beta7,
                        self.beta8, self.beta10, self.beta11a, self.beta11b,
                        self.beta13, self.beta15, self.beta16a, self.beta16b,
-                       float(self.tol), self.max_refine, self.s)
+                       float(self.tol), self.max_refine, self.s, self.order)
 
 
 @dataclass
@@ -237,6 +239,34 @@ def ilu0(rowptr, col, a):
     if st:
         raise ValueError(STATUS[st])
     return fv, dp
+
+
+def mc_order(rowptr, col):
+    """Greedy multicolour order.  Returns (perm with perm[new] = old,
+    cptr: colour c occupies new indices cptr[c] .. cptr[c+1]-1)."""
+    rowptr, col = _i32(rowptr), _i32(col)
+    n = len(rowptr) - 1
+    perm = np.empty(n, dtype=np.int32)
+    cptr = np.empty(n + 1, dtype=np.int32)
+    f = _sig("or_mc_order", _I32, [_I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                                   C.POINTER(_I32)])
+    nc = f(n, _p(rowptr, _I32), _p(col, _I32), _p(perm, _I32), _p(cptr, _I32))
+    return perm, cptr[: nc + 1].copy()
+
+
+def permute_csr(rowptr, col, val, perm):
+    """P A P^T for perm[new] = old (columns sorted ascending)."""
+    rowptr, col, val, perm = _i32(rowptr), _i32(col), _f64(val), _i32(perm)
+    n = len(rowptr) - 1
+    rp2 = np.empty(n + 1, dtype=np.int32)
+    cl2 = np.empty(max(len(col), 1), dtype=np.int32)
+    av2 = np.empty(max(len(col), 1))
+    f = _sig("or_permute_csr", None, [_I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F64),
+                                      C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                                      C.POINTER(_F64)])
+    f(n, _p(rowptr, _I32), _p(col, _I32), _p(val, _F64), _p(perm, _I32), _p(rp2, _I32),
+      _p(cl2, _I32), _p(av2, _F64))
+    return rp2, cl2[: len(col)].copy(), av2[: len(col)].copy()
 
 
 def gs_factors(rowptr, col, a):
@@ -376,8 +406,13 @@ def resid_fp(rowptr, col, a, x, b):
 def setup(rowptr, col, ahat, bhat, params: Params):
     """Setup of Fig. 1: scaling, cast and (precond=1) integer ILU(0).
     Returns a dict with the scaled system and its integer data."""
+    perm = None
+    if params.order == 1:
+        perm, _ = mc_order(rowptr, col)
+        rowptr, col, ahat = permute_csr(rowptr, col, ahat, perm)
+        bhat = _f64(bhat)[perm]
     a, b, d = scale(rowptr, col, ahat, bhat, params.alpha_a)
-    out = dict(rowptr=_i32(rowptr), col=_i32(col), a=a, b=b, d=d, abar=cast(a))
+    out = dict(rowptr=_i32(rowptr), col=_i32(col), a=a, b=b, d=d, abar=cast(a), perm=perm)
     if params.s > 0:
         terms, alphas = multiterm(a, params.alpha_a, params.s)
         out.update(terms=terms, alphas=alphas)
@@ -477,6 +512,6 @@ def fp_gmres(sysd: dict, params: Params, bk, xk=None):
 
 __all__ = ["build", "Params", "Report", "EV_NAMES", "shr", "isqrt", "fx_mul",
            "fx_div", "fx_sqrt", "norm2", "scale", "cast", "ilu0", "ilu_int",
-           "spmv_int", "multiterm", "spmv_int_s", "gs_factors", "lsolve_int", "usolve_int",
+           "spmv_int", "multiterm", "spmv_int_s", "gs_factors", "mc_order", "permute_csr", "lsolve_int", "usolve_int",
            "lsolve_fp", "usolve_fp",
            "resid_fp", "setup", "int_gmres", "ir_solve", "fp_gmres"]
