@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--precond", type=int, default=None,
                     help="override the workload's preconditioner: 0 none, 1 ILU(0), "
                          "2 Gauss-Seidel")
+    ap.add_argument("--order", type=int, default=0,
+                    help="0 natural row order (the paper's), 1 multicolour order")
     ap.add_argument("--terms", type=int, default=0,
                     help="correction terms of the multi-term matrix (Sec. IV-C, s)")
     return ap.parse_args()
@@ -290,6 +292,7 @@ def run_ours(args, wl):
     precond = wl["precond"] if args.precond is None else args.precond
     P = L.params_default(precond, wl["m"])
     P.s = args.terms
+    P.order = args.order
     rp = torch.from_numpy(sysw.rowptr).to(dev)
     cl = torch.from_numpy(sysw.col).to(dev)
     vl = torch.from_numpy(sysw.val).to(dev)
@@ -416,6 +419,7 @@ def run_ours(args, wl):
             "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "m": wl["m"],
                        "refinements": refinements, "relres": rep["relres"], "terms_s": args.terms,
                        "precond": ["none", "ILU(0)", "Gauss-Seidel"][precond],
+                       "order": ["natural", "multicolour"][args.order],
                        "inner_steps": rep["inner_steps"],
                        "l2": "working set (~2 GB) > L2, no flush",
                        "parallelism": f"replicas x{world}"},

@@ -93,7 +93,13 @@ typedef struct {
                     refinement (s(k) = s, 0 ... IGM_MAX_S): the matrix is
                     Abar_0 + sum_l Abar_l / 2^alpha_l and line 5 adds each
                     term's product shifted right by alpha_l (eq. matvec)  */
-  int reserved[3];
+  int order;     /* 0: natural row order (the paper's); 1: multicolour order
+                    (greedy colouring of the symmetrised pattern, rows by
+                    colour): the method runs on P A P^T (P x) = P b, so the
+                    substitutions have as many levels as colours (a
+                    different preconditioner than the natural order's); b
+                    and x stay in the caller's order                      */
+  int reserved[2];
 } igm_params;
 
 #define IGM_MAX_M 128

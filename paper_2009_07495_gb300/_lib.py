@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
                 ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("s", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("order", C.c_int), ("reserved", C.c_int * 2)]
 
     def replace(self, **kw) -> "Params":
         p = Params()

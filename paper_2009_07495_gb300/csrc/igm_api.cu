@@ -48,7 +48,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   std::vector<SysDev *> sp(ns);
   b->m = hs[0]->prm.m;
   b->inner = hs[0]->prm.inner;
-  int maxlev = 1, maxw = 1, maxk = 0;
+  int maxlev = 1, maxw = 1, maxk = 0, max_colors = 0;
   for (int s = 0; s < ns; ++s) {
     igm_handle h = hs[s];
     if (h->prm.m != b->m || h->prm.inner != b->inner) {
@@ -65,7 +65,9 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
     for (int r0 = 0; r0 < h->n; r0 += IGM_STILE)
       stiles.push_back(Tile{s, r0, std::min(IGM_STILE, h->n - r0), 0});
     int cfirst = (int)ctiles.size();
-    for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
+    if (h->hs.ncolors == 0)  // multicolour systems use the colour-by-colour substitutions
+      for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
+    max_colors = std::max(max_colors, h->hs.ncolors);
     b->max_chunk = std::max(b->max_chunk, h->hs.chunk);
     if (h->prm.precond) {
       for (int tr = 0; tr < 2; ++tr) {
@@ -156,6 +158,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.trsv_maxw = maxw;
   B.trsv_maxk = maxk;
   B.trsv_cluster = hs[0]->prm.trsv_cluster;
+  B.max_colors = max_colors;
   B.max_ns = 0;
   for (auto hh : hs) B.max_ns = std::max(B.max_ns, hh->hs.ns);
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
@@ -219,6 +222,73 @@ igm_status capture_graphs(Batch *b) {
   }
   cudaGraphDestroy(g);
   return IGM_OK;
+}
+
+// Multicolour order on the host: greedy colouring of the symmetrised
+// pattern (i ~ j when a_ij or a_ji is stored, i != j), rows in natural order,
+// each taking the smallest colour none of its coloured neighbours has; the
+// new order lists rows colour by colour, ascending within a colour.
+static void mc_order_host(int n, const int *rp, const int *cl, std::vector<int> &perm,
+                          std::vector<int> &cptr) {
+  std::vector<int> deg(n + 1, 0);
+  for (int i = 0; i < n; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (cl[k] != i) {
+        ++deg[i];
+        ++deg[cl[k]];
+      }
+  std::vector<long long> ap(n + 1, 0);
+  for (int i = 0; i < n; ++i) ap[i + 1] = ap[i] + deg[i];
+  std::vector<int> adj(ap[n] > 0 ? ap[n] : 1), at(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = cl[k];
+      if (j == i) continue;
+      adj[ap[i] + at[i]++] = j;
+      adj[ap[j] + at[j]++] = i;
+    }
+  std::vector<int> color(n), seen(n + 1, -1);
+  int ncol = 0;
+  for (int i = 0; i < n; ++i) {
+    for (long long k = ap[i]; k < ap[i + 1]; ++k)
+      if (adj[k] < i) seen[color[adj[k]]] = i;
+    int c = 0;
+    while (seen[c] == i) ++c;
+    color[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  std::vector<int> start(ncol + 1, 0);
+  for (int i = 0; i < n; ++i) ++start[color[i] + 1];
+  for (int c = 0; c < ncol; ++c) start[c + 1] += start[c];
+  cptr.assign(start.begin(), start.end());
+  perm.assign(n, 0);
+  for (int i = 0; i < n; ++i) perm[start[color[i]]++] = i;
+}
+
+// P A P^T on the host (rows in the new order, columns renumbered, sorted)
+static void permute_host(int n, const int *rp, const int *cl, const double *v,
+                         const std::vector<int> &perm, std::vector<int> &rp2,
+                         std::vector<int> &cl2, std::vector<double> &v2) {
+  std::vector<int> inv(n);
+  for (int r = 0; r < n; ++r) inv[perm[r]] = r;
+  rp2.assign(n + 1, 0);
+  cl2.resize(rp[n]);
+  v2.resize(rp[n]);
+  std::vector<std::pair<int, double>> row;
+  for (int r = 0; r < n; ++r) {
+    const int o = perm[r];
+    row.clear();
+    for (int k = rp[o]; k < rp[o + 1]; ++k) row.emplace_back(inv[cl[k]], v[k]);
+    std::sort(row.begin(), row.end(),
+              [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
+                return x.first < y.first;
+              });
+    rp2[r + 1] = rp2[r] + (int)row.size();
+    for (size_t q = 0; q < row.size(); ++q) {
+      cl2[rp2[r] + q] = row[q].first;
+      v2[rp2[r] + q] = row[q].second;
+    }
+  }
 }
 
 // Rows per substitution chunk.  At least the bandwidth of the triangular
@@ -288,6 +358,7 @@ igm_status check_params(const igm_params *p) {
   if (p->inner != 0 && p->inner != 1) return fail(IGM_EINVAL, "inner must be 0 or 1");
   if (p->trsv_chunk < 0) return fail(IGM_EINVAL, "trsv_chunk must be >= 0");
   if (p->s < 0 || p->s > IGM_MAX_S) return fail(IGM_EINVAL, "s must be 0 ... %d", IGM_MAX_S);
+  if (p->order != 0 && p->order != 1) return fail(IGM_EINVAL, "order must be 0 or 1");
   if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
         p->trsv_cluster == 4 || p->trsv_cluster == 8))
     return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
@@ -318,6 +389,28 @@ void fill_report(const SysScal &sc, igm_report *rep) {
 }
 
 }  // namespace
+
+igm_status load_vec(igm_handle h, double *dst, const double *src, cudaStream_t s) {
+  if (!h->perm) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    return IGM_OK;
+  }
+  CK(cudaMemcpyAsync(h->ptmp, src, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  launch_permute(h->n, h->perm, h->ptmp, dst, 0, s);
+  CKL();
+  return IGM_OK;
+}
+
+igm_status store_vec(igm_handle h, double *dst, const double *src, cudaStream_t s) {
+  if (!h->perm) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    return IGM_OK;
+  }
+  launch_permute(h->n, h->perm, src, h->ptmp, 1, s);
+  CKL();
+  CK(cudaMemcpyAsync(dst, h->ptmp, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  return IGM_OK;
+}
 
 extern "C" {
 
@@ -363,6 +456,32 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   if (n < 1 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
     return fail(IGM_EINVAL, "bad sizes or NULL arrays");
   cudaStream_t s = (cudaStream_t)stream;
+  // multicolour order: the whole set-up works on P A P^T, built on the host
+  std::vector<int> mc_perm, mc_cptr, mc_rp, mc_cl;
+  std::vector<double> mc_v;
+  if (params->order == 1) {
+    std::vector<int> hr(n + 1), hc(nnz > 0 ? nnz : 1);
+    std::vector<double> hv(nnz > 0 ? nnz : 1);
+    if (cudaMemcpy(hr.data(), rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault) != cudaSuccess ||
+        (nnz > 0 && (cudaMemcpy(hc.data(), col, sizeof(int) * nnz, cudaMemcpyDefault) !=
+                         cudaSuccess ||
+                     cudaMemcpy(hv.data(), val, sizeof(double) * nnz, cudaMemcpyDefault) !=
+                         cudaSuccess))) {
+      cudaGetLastError();
+      return fail(IGM_EINVAL, "the CSR arrays are not readable");
+    }
+    if (hr[0] != 0 || hr[n] != nnz) return fail(IGM_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+    for (int i = 0; i < n; ++i) {
+      if (hr[i + 1] < hr[i]) return fail(IGM_EINVAL, "rowptr must be non-decreasing");
+      for (int k = hr[i]; k < hr[i + 1]; ++k)
+        if (hc[k] < 0 || hc[k] >= n) return fail(IGM_EINVAL, "column index out of range");
+    }
+    mc_order_host(n, hr.data(), hc.data(), mc_perm, mc_cptr);
+    permute_host(n, hr.data(), hc.data(), hv.data(), mc_perm, mc_rp, mc_cl, mc_v);
+    rowptr = mc_rp.data();
+    col = mc_cl.data();
+    val = mc_v.data();
+  }
   igm_handle h = new igm_handle_s();
   h->n = n;
   h->nnz = nnz;
@@ -447,6 +566,12 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   A.want(&h->d_sys, 1);
   A.want(&h->d_sc, 1);
   A.want(&h->d_err, 4);
+  int *dcptr = nullptr;
+  if (params->order == 1) {
+    A.want(&h->perm, n);
+    A.want(&h->ptmp, n);
+    A.want(&dcptr, mc_cptr.size());
+  }
   if (A.commit() != cudaSuccess) {
     cudaGetLastError();
     size_t need = A.total();
@@ -463,6 +588,11 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     }                                                                             \
   } while (0)
   CKH(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), s));
+  if (h->perm) {
+    CKH(cudaMemcpyAsync(h->perm, mc_perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CKH(cudaMemcpyAsync(dcptr, mc_cptr.data(), sizeof(int) * mc_cptr.size(),
+                        cudaMemcpyHostToDevice, s));
+  }
   CKH(cudaMemsetAsync(h->d_sc, 0, sizeof(SysScal), s));
   CKH(cudaMemcpyAsync(rp, rowptr, sizeof(int) * (n + 1), cudaMemcpyDefault, s));
   if (nnz > 0) {
@@ -658,6 +788,8 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.sval = sval;
   d.scol = scol;
   d.nnz_sell = (long long)nzs;
+  d.ncolors = (params->order == 1 && ilu) ? (int)mc_cptr.size() - 1 : 0;
+  d.cptr = dcptr;
   d.ns = ns;
   for (int l = 0; l <= IGM_MAX_S; ++l) d.alphas[l] = alphas[l];
   d.f = f;
@@ -817,10 +949,16 @@ igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *
   g_err.clear();
   if (!h || !bhat || !xhat) return fail(IGM_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(h->hs.bh, bhat, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  {
+    igm_status ls = load_vec(h, h->hs.bh, bhat, s);
+    if (ls) return ls;
+  }
   igm_status st = run_ir(h->solo, s);
   if (st) return st;
-  CK(cudaMemcpyAsync(xhat, h->hs.xt, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  {
+    igm_status ss = store_vec(h, xhat, h->hs.xt, s);
+    if (ss) return ss;
+  }
   return collect_host(h, rep, s);
 }
 
@@ -848,11 +986,17 @@ igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat
     g_batches.push_back(b);
   }
   for (int i = 0; i < count; ++i)
-    CK(cudaMemcpyAsync(v[i]->hs.bh, bhat[i], sizeof(double) * v[i]->n, cudaMemcpyDefault, s));
+    {
+      igm_status ls = load_vec(v[i], v[i]->hs.bh, bhat[i], s);
+      if (ls) return ls;
+    }
   igm_status st = run_ir(b, s);
   if (st) return st;
   for (int i = 0; i < count; ++i)
-    CK(cudaMemcpyAsync(xhat[i], v[i]->hs.xt, sizeof(double) * v[i]->n, cudaMemcpyDefault, s));
+    {
+      igm_status ss = store_vec(v[i], xhat[i], v[i]->hs.xt, s);
+      if (ss) return ss;
+    }
   igm_status worst = IGM_OK;
   for (int i = 0; i < count; ++i) {
     igm_status e = collect_host(v[i], reps ? reps + i : nullptr, s);
@@ -868,8 +1012,11 @@ igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_repor
   cudaStream_t s = (cudaStream_t)stream;
   Batch *b = h->solo;
   const BatchDev &B = b->bd;
-  CK(cudaMemcpyAsync(h->hs.t, bk, sizeof(double) * h->n, cudaMemcpyDefault, s));
-  CK(cudaMemcpyAsync(h->hs.xk, xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  {
+    igm_status ls = load_vec(h, h->hs.t, bk, s);
+    if (!ls) ls = load_vec(h, h->hs.xk, xk, s);
+    if (ls) return ls;
+  }
   launch_init_scal(B, 1, s);
   if (b->inner == 1) launch_fp64_resid_guess(B, s);
   else launch_resid_int(B, s);
@@ -877,7 +1024,10 @@ igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_repor
   enqueue_inner(b, s);
   CKL();
   g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) + (long long)b->m * (4 + (b->any_ilu ? 2 : 0));
-  CK(cudaMemcpyAsync(xk, h->hs.xk, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  {
+    igm_status ss = store_vec(h, xk, h->hs.xk, s);
+    if (ss) return ss;
+  }
   igm_status st = collect_host(h, rep, s);
   if (st == IGM_ENOCONV) st = IGM_OK;  // a single inner solve has no test
   if (rep && rep->status == IGM_ENOCONV) rep->status = IGM_OK;

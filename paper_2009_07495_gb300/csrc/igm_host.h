@@ -70,7 +70,13 @@ struct igm_handle_s {
   SysScal *d_sc = nullptr;
   unsigned *d_err = nullptr;
   Batch *solo = nullptr;  // batch of one, with its captured graphs
+  int *perm = nullptr;    // multicolour order: perm[new] = old (device)
+  double *ptmp = nullptr; // staging vector of the permutation (device)
 };
+
+// right-hand sides in, solutions out, in the caller's row order
+igm_status load_vec(igm_handle h, double *dst, const double *src, cudaStream_t s);
+igm_status store_vec(igm_handle h, double *dst, const double *src, cudaStream_t s);
 
 struct Batch {
   std::vector<igm_handle> hs;

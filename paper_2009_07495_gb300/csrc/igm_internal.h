@@ -98,6 +98,10 @@ struct SysDev {
   // l * nnz, resp. l * nnz_sell); alphas[0] = 0
   int ns;
   int alphas[IGM_MAX_S + 1];
+  // multicolour order: rows of colour c are [cptr[c], cptr[c+1]) (device),
+  // ncolors > 0 selects the colour-by-colour substitutions
+  int ncolors;
+  const int *cptr;
   const double *f;                       // FP64 ILU(0) factors
   const i64 *fac, *ldiag, *udiag;        // integer factors
   // substitution schedules of the two factors, tri[0] = L, tri[1] = U
@@ -152,6 +156,7 @@ struct BatchDev {
   int trsv_maxk;           // most strict entries of one factor row
   int trsv_cluster;        // CTAs per cluster of the substitutions (0 automatic)
   int max_ns;              // most correction terms of eq. (AA) of a system
+  int max_colors;          // most colours of a multicolour-ordered system
 };
 
 // vector selectors for the generic max / norm kernels

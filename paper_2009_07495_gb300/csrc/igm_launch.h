@@ -33,7 +33,10 @@ void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, i
 // (line 1'), 2 FP64 factors (comparison solver); which 0 line 1', 1 line 5'
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
                     cudaStream_t st);
+void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaStream_t st);
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st);
+void launch_permute(int n, const int *perm, const double *src, double *dst, int back,
+                    cudaStream_t st);
 void launch_mt_init(long long nnz, const double *a, const i64 *abar, double *R,
                     cudaStream_t st);
 void launch_mt_max(long long nnz, const double *R, unsigned long long *mx, cudaStream_t st);

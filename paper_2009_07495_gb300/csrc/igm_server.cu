@@ -78,8 +78,8 @@ igm_status admit(igm_server_s *S, Request *r) {
                                   &r->prm, S->stream, &r->h);
   if (st) return st;
   r->bytes = int_gmres_device_bytes(r->h);
-  CK(cudaMemcpyAsync(r->h->hs.bh, r->b.data(), sizeof(double) * r->n, cudaMemcpyHostToDevice,
-                     S->stream));
+  st = load_vec(r->h, r->h->hs.bh, r->b.data(), S->stream);
+  if (st) return st;
   st = ir_init_host(r->h->solo, S->stream);
   if (st) return st;
   CK(cudaStreamSynchronize(S->stream));
@@ -144,7 +144,7 @@ igm_status round(igm_server_s *S) {
     igm_status fs = ir_finish_host(r->h->solo, s);
     if (!fs) {
       r->x.resize(r->n);
-      cudaMemcpyAsync(r->x.data(), r->h->hs.xt, sizeof(double) * r->n, cudaMemcpyDeviceToHost, s);
+      store_vec(r->h, r->x.data(), r->h->hs.xt, s);
       fs = collect_host(r->h, &r->rep, s);
     }
     int_gmres_destroy(r->h);

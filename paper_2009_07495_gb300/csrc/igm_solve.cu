@@ -428,6 +428,22 @@ void launch_norm2(const double *x, int n, long long *ws, double *mx, double *out
 }
 
 // per-system {active, status, error bits, refinements} for the host
+// dst[r] = src[perm[r]] (into the multicolour order) or dst[perm[r]] =
+// src[r] (back to the caller's order)
+__global__ void k_permute(int n, const int *perm, const double *src, double *dst, int back) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    if (back) dst[perm[r]] = src[r];
+    else dst[r] = src[perm[r]];
+  }
+}
+
+void launch_permute(int n, const int *perm, const double *src, double *dst, int back,
+                    cudaStream_t st) {
+  int g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_permute<<<g, 256, 0, st>>>(n, perm, src, dst, back);
+}
+
 __global__ void k_gather_state(BatchDev B, int4 *out) {
   int si = blockIdx.x * blockDim.x + threadIdx.x;
   if (si >= B.nsys) return;

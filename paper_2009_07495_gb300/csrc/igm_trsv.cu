@@ -635,6 +635,64 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Substitutions in multicolour order: every strict dependency of a row lies
+// in another colour (earlier for L, later for U), so one launch per colour
+// computes all its rows at once, each row from the CSR of the factors in
+// CSR order (the order of the natural substitution).
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(256) k_trsv_color(BatchDev B, int lower, int which, int c) {
+  typedef typename TrsvT<KIND>::V V;
+  const Tile tl = B.tiles[blockIdx.x];
+  const SysDev *s = B.sys[tl.sys];
+  SysScal *sc = s->sc;
+  if (!(sc->cyc != 0 && sc->early == 0) || !s->p.precond || s->ncolors == 0) return;
+  const int nc = s->ncolors;
+  if (c >= nc) return;
+  const int cc = lower ? c : nc - 1 - c;  // U: colours from the last
+  const int r0 = max(tl.row0, s->cptr[cc]), r1 = min(tl.row0 + tl.nrows, s->cptr[cc + 1]);
+  if (r0 >= r1) return;
+  const V *in;
+  V *out;
+  if (KIND == TK_INT) {
+    in = reinterpret_cast<const V *>(lower ? s->w : s->yv);
+    out = reinterpret_cast<V *>(lower ? s->yv : s->w);
+  } else if (KIND == TK_FPI || which == 0) {
+    in = reinterpret_cast<const V *>(lower ? s->r : s->t);
+    out = reinterpret_cast<V *>(lower ? s->t : s->r);
+  } else {
+    in = reinterpret_cast<const V *>(lower ? reinterpret_cast<const double *>(s->w) : s->t);
+    out = reinterpret_cast<V *>(lower ? s->t : reinterpret_cast<double *>(s->w));
+  }
+  unsigned ev = 0;
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+    const int dp = s->diagpos[i];
+    const int k0 = lower ? s->rowptr[i] : dp + 1, k1 = lower ? dp : s->rowptr[i + 1];
+    typedef typename std::conditional<KIND == TK_INT, i128, double>::type A;
+    A acc = (A)in[i];
+    for (int k = k0; k < k1; ++k) {
+      const V yj = __ldcg(out + s->col[k]);
+      if (KIND == TK_INT) acc -= (A)mulw(s->fac[k], (i64)yj, ev);
+      else if (KIND == TK_FPI) acc = __dsub_rn((double)acc, __dmul_rn((double)s->fac[k], (double)yj));
+      else acc = __dsub_rn((double)acc, __dmul_rn(s->f[k], (double)yj));
+    }
+    V y;
+    if (KIND == TK_INT) {
+      ev += out64((i128)acc);
+      y = (V)divt(wrap((i128)acc), lower ? s->ldiag[i] : s->udiag[i], ev);
+    } else if (KIND == TK_FPI) {
+      y = (V)__ddiv_rn((double)acc, (double)(lower ? s->ldiag[i] : s->udiag[i]));
+    } else if (lower) {
+      y = (V)acc;  // unit lower factor
+    } else {
+      y = (V)__ddiv_rn((double)acc, s->f[dp]);
+    }
+    out[i] = y;
+  }
+  if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
+}
+
+// ---------------------------------------------------------------------------
 // eq. (ilu) on the L schedule: one CTA per chunk, local levels in order;
 // row i runs the IKJ update of Saad's Alg. 10.4 (k ascending over its strict
 // lower part: l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for the j > k of
@@ -794,8 +852,17 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
   cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND, KC>, B, lower, which, rows, lev, rmax, pf, kr, cl);
 }
 
+void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaStream_t st) {
+  for (int c = 0; c < B.max_colors; ++c) {
+    if (kind == TK_INT) k_trsv_color<TK_INT><<<B.ntiles, 256, 0, st>>>(B, lower, which, c);
+    else if (kind == TK_FPI) k_trsv_color<TK_FPI><<<B.ntiles, 256, 0, st>>>(B, lower, which, c);
+    else k_trsv_color<TK_FP><<<B.ntiles, 256, 0, st>>>(B, lower, which, c);
+  }
+}
+
 void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
                     cudaStream_t st) {
+  if (B.max_colors > 0) launch_trsv_color(B, kind, lower, which, st);
   if (B.trsv_maxk <= IGM_TRSV_KC_SMALL) {
     if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
     else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);

@@ -27,7 +27,7 @@ def _oparams(orc, P):
     return orc.Params(df=P.df, alpha_a=P.alpha_a, m=P.m, precond=P.precond, beta7=P.beta7,
                       beta8=P.beta8, beta10=P.beta10, beta11a=P.beta11a, beta11b=P.beta11b,
                       beta13=P.beta13, beta15=P.beta15, beta16a=P.beta16a, beta16b=P.beta16b,
-                      tol=P.tol, max_refine=P.max_refine, s=P.s)
+                      tol=P.tol, max_refine=P.max_refine, s=P.s, order=P.order)
 
 
 def _dev(a):
@@ -189,6 +189,49 @@ def test_gauss_seidel_bit_exact(L, orc, name, sf, m):
     np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
     np.testing.assert_array_equal(rep["ev"], ro.ev)
     assert int(np.abs(np.asarray(rep["ev"])).sum()) == 0
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    solver.close()
+
+
+MC_CASES = [
+    ("cd3d_12_ilu_mc", lambda: W.small_cd3d(12, seed=52), 1),
+    ("cd3d_10_27pt_ilu_mc", lambda: W.small_cd3d(10, seed=53, points=27), 1),
+    ("cd3d_12_gs_mc", lambda: W.small_cd3d(12, seed=54), 2),
+    ("banded_2000_ilu_mc", lambda: W.banded_random(2000, np.random.default_rng(55)), 1),
+]
+
+
+@pytest.mark.parametrize("name,sf,prec", MC_CASES, ids=[c[0] for c in MC_CASES])
+def test_multicolour_order_bit_exact(L, orc, name, sf, prec):
+    """order = 1: the method on P A P^T (P x) = P b with the multicolour
+    permutation; one inner solve (basis and Hessenberg matrix in the new
+    order, b and x in the caller's) and the refinement loop equal the
+    oracle's bit for bit."""
+    s = sf()
+    m = 20
+    P = L.params_default(prec, m)
+    P.order = 1
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    perm = d["perm"]
+    bk_new = d["b"] / np.abs(d["b"]).max()
+    x0 = np.random.default_rng(7).standard_normal(s.n) * 1e-3
+    o = orc.int_gmres(_oparams(orc, P), d, bk_new, x0[perm])
+    bk = np.empty(s.n)
+    bk[perm] = bk_new
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    _compare_inner(solver.state(), o, s.n, m)
+    xo_inner = np.empty(s.n)
+    xo_inner[perm] = o["x"]
+    np.testing.assert_array_equal(xk.cpu().numpy(), xo_inner)
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert ro.status == "ok" and rep["status"] == "ok"
+    assert rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
     np.testing.assert_array_equal(x.cpu().numpy(), xo)
     solver.close()
 
