@@ -164,6 +164,10 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
       const i64 *vi = c.V + (size_t)(i <= j ? i : 0) * c.n + c.row0;
       i64 *wg = c.w, *ws = sw + c.off;
       const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
+      // line 8's coefficient as a 32-bit value when it fits: the product
+      // with a basis entry that fits too is one 32x32 -> 64-bit multiply,
+      // exact and never out of range (same word, no event)
+      const bool hs32 = hs == (i64)(int)hs;
       i128 part = 0;
       unsigned evA = 0, evB = 0;
       for (int q0 = threadIdx.x; q0 < nr; q0 += IGM_RPT * IGM_MGS_BLOCK) {
@@ -182,7 +186,12 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
           const int q = q0 + u * IGM_MGS_BLOCK;
           if (q >= nr) continue;
           i64 wl = wv[u];
-          if (i > 0) wl = subw(wl, mulw(hs, pv[u], evB) >> s8, evB);
+          if (i > 0) {
+            const i64 pr = (hs32 && pv[u] == (i64)(int)pv[u])
+                               ? (i64)(int)hs * (i64)(int)pv[u]
+                               : mulw(hs, pv[u], evB);
+            wl = subw(wl, pr >> s8, evB);
+          }
           if (wsm) ws[q] = wl;
           else if (i > 0) wg[q] = wl;
           if (i <= j) {
