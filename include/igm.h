@@ -148,7 +148,8 @@ igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk,
  * b = D^-1 bh, then repeat { r = b - A x; stop if ||r||/||b|| < tol;
  * gamma = max|r_i|; inner solve of A x^(k) = r/gamma; x += gamma x^(k) },
  * xh = x (eq. 1 leaves x unscaled).  bhat, xhat: n doubles.  rep may be
- * NULL.  Returns IGM_ENOCONV when max_refine is reached first. */
+ * NULL.  Returns IGM_ENOCONV when max_refine is reached first, or when
+ * ||r||/||b|| has not decreased over the last three refinements (a stall). */
 igm_status ir_solve(igm_handle h, const double *bhat, double *xhat,
                     igm_report *rep, void *stream);
 

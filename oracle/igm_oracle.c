@@ -882,7 +882,8 @@ out:
 /* Solves Ahat xhat = bhat.  inner = 0: int-GMRES (Fig. 2); inner = 1: the
  * FP64 GMRES(m) cycle in the same refinement loop ("Double" solver).
  * xhat (n) receives the solution.  Stops when the scaled relative residual
- * of Fig. 1 is below tol (status OR_OK) or after max_refine inner solves
+ * of Fig. 1 is below tol (status OR_OK), or after max_refine inner solves or
+ * when the residual has not decreased over the last three refinements
  * (OR_ENOCONV). */
 static int ir_solve_natural(const or_params *P, int inner, int n, const int *rowptr,
                             const int *col, const double *ahat, const double *bhat,
@@ -950,14 +951,18 @@ static int ir_solve_natural(const or_params *P, int inner, int n, const int *row
     or_system S = {n, rowptr, col, abar, fac, ldg, udg, ns, alphas};
     double nb = or_norm2(n, b);
     st = OR_ENOCONV;
+    double ring[4] = {0.0, 0.0, 0.0, 0.0};   /* the last residuals */
     for (int k = 0;; ++k) {
       /* b' = b - A x (FP) and the test of Fig. 1 */
       or_resid_fp(n, rowptr, col, a, x, b, bp);
       double rho = nb == 0.0 ? 0.0 : or_norm2(n, bp) / nb;
       if (k < 65) rep->relres_hist[k] = rho;
       rep->relres = rho;
+      /* stalled: no decrease over the last three refinements */
+      int stall = k >= 3 && rho >= ring[(k - 3) & 3];
+      ring[k & 3] = rho;
       if (rho < P->tol) { st = OR_OK; break; }
-      if (k >= P->max_refine) { st = OR_ENOCONV; break; }
+      if (k >= P->max_refine || stall) { st = OR_ENOCONV; break; }
       /* eq. (gammak), eq. (scale) */
       double gam = or_maxabs(n, bp);
       if (k < 64) rep->gamma_hist[k] = gam;

@@ -53,6 +53,7 @@ struct SysScal {
   i64 hnext;               // h_{j+1,j} before the rotations (line 11)
   double relres_hist[65];
   double gamma_hist[64];
+  double rho_ring[4];      // the last residuals (stall test of the loop)
 };
 
 // Schedule and level-packed data of one triangular factor.  Positions

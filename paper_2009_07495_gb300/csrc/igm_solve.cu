@@ -121,11 +121,14 @@ __device__ void norm_action(const BatchDev &B, const SysDev *s, SysScal *sc, int
       sc->jeff = 0;
       sc->early = 0;
       sc->normj = -1;
+      // stalled: no decrease over the last three refinements
+      const bool stall = k >= 3 && rho >= sc->rho_ring[(k - 3) & 3];
+      sc->rho_ring[k & 3] = rho;
       if (rho < P.tol) {
         sc->active = 0;
         sc->cyc = 0;
         sc->status = 0;
-      } else if (k >= P.max_refine) {
+      } else if (k >= P.max_refine || stall) {
         sc->active = 0;
         sc->cyc = 0;
         sc->status = 5;

@@ -236,6 +236,23 @@ def test_multicolour_order_bit_exact(L, orc, name, sf, prec):
     solver.close()
 
 
+def test_stall_stops_like_the_oracle(L, orc):
+    """A tolerance below FP64's reach: the loop stops at the first stall
+    (no decrease over three refinements) with ENOCONV, at the same
+    refinement as the oracle, with the same residual history."""
+    s = W.config0()
+    P = L.params_default(0, 30)
+    P.tol, P.max_refine = 1e-18, 40
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert ro.status == "enoconv" and rep["status"] == "enoconv"
+    assert rep["refinements"] == ro.refinements < 40
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    solver.close()
+
+
 def test_one_by_one(L):
     """n = 1: Ahat = [2], bhat = [4] gives x = 2 exactly in one refinement."""
     P = L.params_default(0, 5)

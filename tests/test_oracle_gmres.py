@@ -232,3 +232,19 @@ def test_overflow_is_counted(orc):
     x, rep = orc.ir_solve(s.rowptr, s.col, s.val, s.b, P)
     assert rep.ev[2] > 0 or rep.ev[4] > 0       # lines 7 / 10
     assert rep.status in ("ok", "enoconv")
+
+
+def test_refinement_stops_when_the_residual_stalls(orc):
+    """With a tolerance below what FP64 reaches, the residual of Fig. 1
+    falls to rounding level and then stays there; the loop stops
+    (ENOCONV) the first time it has not decreased over three refinements,
+    instead of running to max_refine."""
+    s = W.config0()
+    P = orc.Params.table4(m=30, tol=1e-18, max_refine=40)
+    x, rep = orc.ir_solve(s.rowptr, s.col, s.val, s.b, P)
+    h = rep.relres_hist
+    k = rep.refinements
+    assert rep.status == "enoconv" and k < 40
+    assert h[k] >= h[k - 3]
+    assert all(h[q] < h[q - 3] for q in range(3, k))
+    assert h[k] < 1e-14
