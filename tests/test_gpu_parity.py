@@ -329,6 +329,62 @@ def test_batched_equals_solo(L, orc):
         sv.close()
 
 
+def _variant(L, prec, m, order=0, terms=0):
+    P = L.params_default(prec, m)
+    P.order, P.s = order, terms
+    return P
+
+
+def test_batched_mixed_variants_equal_solo(L, orc):
+    """One batch mixing natural-order ILU(0), multicolour ILU(0) (colour
+    launches beside chunk launches), Gauss-Seidel, multi-term and plain
+    systems: every result equals its solo solve and the oracle's."""
+    import torch
+    rng = np.random.default_rng(61)
+    systems = [W.small_cd3d(11, seed=62), W.small_cd3d(10, seed=63),
+               W.small_cd3d(9, seed=64, points=27), W.small_cd3d(8, seed=65),
+               W.banded_random(1800, rng), W.small_cd2d(24, seed=66)]
+    params = [_variant(L, 1, 20), _variant(L, 1, 20, order=1), _variant(L, 1, 20, order=1),
+              _variant(L, 2, 20), _variant(L, 0, 20, terms=2), _variant(L, 2, 20, order=1)]
+    svs, solos = [], []
+    for sy, P in zip(systems, params):
+        sv = L.Solver(_dev(sy.rowptr), _dev(sy.col), _dev(sy.val), P)
+        x, rep = sv.ir_solve(_dev(sy.b))
+        solos.append((x.cpu().numpy(), rep))
+        svs.append(sv)
+    out = [torch.empty(sy.n, dtype=torch.float64, device="cuda") for sy in systems]
+    reps = L.ir_solve_batched(svs, [_dev(sy.b) for sy in systems], out)
+    for k, sy in enumerate(systems):
+        xo, ro = orc.ir_solve(sy.rowptr, sy.col, sy.val, sy.b, _oparams(orc, params[k]))
+        assert ro.status == "ok"
+        np.testing.assert_array_equal(out[k].cpu().numpy(), solos[k][0])
+        np.testing.assert_array_equal(out[k].cpu().numpy(), xo)
+        assert reps[k]["refinements"] == solos[k][1]["refinements"] == ro.refinements
+        np.testing.assert_array_equal(reps[k]["ev"], ro.ev)
+    for sv in svs:
+        sv.close()
+
+
+def test_server_mixed_variants_equal_solo(L, orc):
+    """The server with requests of every variant (orders, preconditioners,
+    correction terms) returns each request's oracle result."""
+    systems = [W.small_cd3d(9, seed=67), W.small_cd3d(10, seed=68),
+               W.small_cd3d(8, seed=69, points=27), W.small_cd2d(22, seed=70)]
+    params = [_variant(L, 1, 20, order=1), _variant(L, 2, 20), _variant(L, 1, 20, terms=1),
+              _variant(L, 0, 20, order=1)]
+    srv = L.Server(budget_bytes=1 << 30, m=20)
+    ids = [srv.submit(sy.rowptr, sy.col, sy.val, sy.b, P) for sy, P in zip(systems, params)]
+    outs = [srv.poll(i, wait_ms=60000) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(systems) and st["failed"] == 0
+    for (done, x, rep, lat), sy, P in zip(outs, systems, params):
+        xo, ro = orc.ir_solve(sy.rowptr, sy.col, sy.val, sy.b, _oparams(orc, P))
+        assert done and rep["status"] == ro.status == "ok"
+        assert rep["refinements"] == ro.refinements
+        np.testing.assert_array_equal(x, xo)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_fp64_gmres_comparison_solver(L, orc, prec):
     """The FP64 GMRES(m) comparison solver (params.inner = 1) converges like
