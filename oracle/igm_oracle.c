@@ -80,6 +80,9 @@ typedef struct {
   int order;     /* 0: natural row order (the paper's); 1: multicolour
                     order (or_mc_order), the whole method run on the
                     permuted system P A P^T (P x) = P b                */
+  int shift_tune;/* shift auto-tuning (Sec. VII-D): cycles that may be
+                    discarded and rerun with raised shifts in one solve
+                    (0: the shifts stay as given, as in Tables 4 and 5) */
 } or_params;
 
 typedef struct {
@@ -92,6 +95,9 @@ typedef struct {
   double relres_unscaled;   /* final ||bh - Ah xh|| / ||bh||           */
   double gamma_hist[64];
   double relres_hist[65];
+  int shift_retries;        /* cycles discarded by the shift auto-tuning  */
+  int beta_final[5];        /* beta7, beta8, beta10, beta13, beta15 at the
+                               end of the solve                           */
 } or_report;
 
 /* ------------------------------------------------------------------ */
@@ -911,6 +917,25 @@ int or_ir_solve(const or_params *P, int inner, int n, const int *rowptr,
   return st;
 }
 
+/* Shift auto-tuning (Sec. VII-D names it for the solver without
+ * preconditioning and gives no rule; this is the reading used here).  The
+ * lines whose shift beta divides an operand before a product or a sum of
+ * products are 7, 8, 10, 13 and 15 (Table 3): a larger beta makes their
+ * words smaller.  After a cycle that raised overflow events at any of them,
+ * each such line whose beta is below d_f gets beta + 1; returns 1 if a shift
+ * was raised (the cycle is then discarded and run again), else 0. */
+static int raise_shifts(or_params *Pk, const i64 *evc) {
+  const int line[5] = {EV_L7, EV_L8, EV_L10, EV_L13, EV_L15};
+  int *beta[5] = {&Pk->beta7, &Pk->beta8, &Pk->beta10, &Pk->beta13, &Pk->beta15};
+  int raised = 0;
+  for (int t = 0; t < 5; ++t)
+    if (evc[line[t]] > 0 && *beta[t] < Pk->df) {
+      *beta[t] += 1;
+      raised = 1;
+    }
+  return raised;
+}
+
 static int ir_solve_natural(const or_params *P, int inner, int n, const int *rowptr,
                             const int *col, const double *ahat, const double *bhat,
                             double *xhat, or_report *rep) {
@@ -952,6 +977,7 @@ static int ir_solve_natural(const or_params *P, int inner, int n, const int *row
     double nb = or_norm2(n, b);
     st = OR_ENOCONV;
     double ring[4] = {0.0, 0.0, 0.0, 0.0};   /* the last residuals */
+    or_params Pk = *P;                        /* the shifts in use     */
     for (int k = 0;; ++k) {
       /* b' = b - A x (FP) and the test of Fig. 1 */
       or_resid_fp(n, rowptr, col, a, x, b, bp);
@@ -967,12 +993,27 @@ static int ir_solve_natural(const or_params *P, int inner, int n, const int *row
       double gam = or_maxabs(n, bp);
       if (k < 64) rep->gamma_hist[k] = gam;
       for (int l = 0; l < n; ++l) bp[l] = bp[l] / gam;
-      memset(xk, 0, sizeof(double) * (size_t)n);
       int jeff = 0;
       if (inner == 0) {
-        if (or_int_gmres(P, &S, bp, xk, NULL, NULL, NULL, NULL, NULL, NULL, &jeff, NULL, rep->ev))
-          rep->breakdowns++;
+        /* the cycle with the current shifts; with auto-tuning, a cycle that
+         * overflowed at a shifted line is discarded (x is not updated, the
+         * refinement is not counted) and rerun from the same b^(k) */
+        for (;;) {
+          i64 evc[EV_COUNT] = {0};
+          memset(xk, 0, sizeof(double) * (size_t)n);
+          jeff = 0;
+          int early = or_int_gmres(&Pk, &S, bp, xk, NULL, NULL, NULL, NULL, NULL, NULL,
+                                   &jeff, NULL, evc);
+          for (int e = 0; e < EV_COUNT; ++e) rep->ev[e] += evc[e];
+          if (rep->shift_retries < P->shift_tune && raise_shifts(&Pk, evc)) {
+            rep->shift_retries++;
+            continue;
+          }
+          if (early) rep->breakdowns++;
+          break;
+        }
       } else {
+        memset(xk, 0, sizeof(double) * (size_t)n);
         or_fp_gmres(n, rowptr, col, a, f, diagpos, P->m, P->precond, bp, xk, &jeff);
       }
       rep->refinements++;
@@ -983,6 +1024,11 @@ static int ir_solve_natural(const or_params *P, int inner, int n, const int *row
         x[l] = x[l] + p;
       }
     }
+    rep->beta_final[0] = Pk.beta7;
+    rep->beta_final[1] = Pk.beta8;
+    rep->beta_final[2] = Pk.beta10;
+    rep->beta_final[3] = Pk.beta13;
+    rep->beta_final[4] = Pk.beta15;
     memcpy(xhat, x, sizeof(double) * (size_t)n);
     /* residual of the original system, for reporting */
     or_resid_fp(n, rowptr, col, ahat, x, bhat, bp);

@@ -50,7 +50,7 @@ class _Params(C.Structure):
                 ("beta11a", C.c_int), ("beta11b", C.c_int), ("beta13", C.c_int),
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("s", C.c_int),
-                ("order", C.c_int)]
+                ("order", C.c_int), ("shift_tune", C.c_int)]
 
 
 class _Report(C.Structure):
@@ -58,7 +58,8 @@ class _Report(C.Structure):
                 ("inner_steps", C.c_int), ("breakdowns", C.c_int),
                 ("status", C.c_int), ("relres", C.c_double),
                 ("relres_unscaled", C.c_double),
-                ("gamma_hist", C.c_double * 64), ("relres_hist", C.c_double * 65)]
+                ("gamma_hist", C.c_double * 64), ("relres_hist", C.c_double * 65),
+                ("shift_retries", C.c_int), ("beta_final", C.c_int * 5)]
 
 
 def _load():
@@ -93,6 +94,7 @@ class Params:
     max_refine: int = 60
     s: int = 0               # correction terms of eq. (AA), s(k) = s
     order: int = 0           # 0 natural, 1 multicolour (mc_order)
+    shift_tune: int = 0      # cycles the shift auto-tuning may discard (Sec. VII-D)
 
     @staticmethod
     def table4(m: int = 30, **kw) -> "Params":
@@ -112,7 +114,8 @@ class Params:
         return _Params(self.df, self.alpha_a, self.m, self.precond, self.beta7,
                        self.beta8, self.beta10, self.beta11a, self.beta11b,
                        self.beta13, self.beta15, self.beta16a, self.beta16b,
-                       float(self.tol), self.max_refine, self.s, self.order)
+                       float(self.tol), self.max_refine, self.s, self.order,
+                       self.shift_tune)
 
 
 @dataclass
@@ -126,6 +129,8 @@ class Report:
     ev: np.ndarray = field(repr=False)
     gamma_hist: np.ndarray = field(repr=False)
     relres_hist: np.ndarray = field(repr=False)
+    shift_retries: int = 0
+    beta_final: tuple = ()   # beta7, beta8, beta10, beta13, beta15 at the end
 
 
 def _p(a, ct):
@@ -488,7 +493,8 @@ def ir_solve(rowptr, col, ahat, bhat, params: Params, inner: int = 0):
                relres=rep.relres, relres_unscaled=rep.relres_unscaled,
                ev=np.array(rep.ev[:], dtype=np.int64),
                gamma_hist=np.array(rep.gamma_hist[:rep.refinements]),
-               relres_hist=np.array(rep.relres_hist[:min(rep.refinements + 1, 65)]))
+               relres_hist=np.array(rep.relres_hist[:min(rep.refinements + 1, 65)]),
+               shift_retries=rep.shift_retries, beta_final=tuple(rep.beta_final[:]))
     return x, r
 
 
