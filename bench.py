@@ -82,6 +82,12 @@ def parse():
                     help="0 natural row order (the paper's), 1 multicolour order")
     ap.add_argument("--terms", type=int, default=0,
                     help="correction terms of the multi-term matrix (Sec. IV-C, s)")
+    ap.add_argument("--shift-tune", type=int, default=0,
+                    help="shift auto-tuning budget (Sec. VII-D): inner solves that may "
+                         "be discarded and rerun with raised shifts")
+    ap.add_argument("--shifts", type=int, default=None,
+                    help="start the shifts of lines 7, 8, 10, 13, 15 at this value "
+                         "(default: Table 4 / Table 5)")
     return ap.parse_args()
 
 
@@ -293,6 +299,10 @@ def run_ours(args, wl):
     P = L.params_default(precond, wl["m"])
     P.s = args.terms
     P.order = args.order
+    P.shift_tune = args.shift_tune
+    if args.shifts is not None:
+        for k in ("beta7", "beta8", "beta10", "beta13", "beta15"):
+            setattr(P, k, args.shifts)
     rp = torch.from_numpy(sysw.rowptr).to(dev)
     cl = torch.from_numpy(sysw.col).to(dev)
     vl = torch.from_numpy(sysw.val).to(dev)
@@ -442,6 +452,10 @@ def run_ours(args, wl):
                        "precond": ["none", "ILU(0)", "Gauss-Seidel"][precond],
                        "order": ["natural", "multicolour"][args.order],
                        "inner_steps": rep["inner_steps"],
+                       "shift_tune": args.shift_tune,
+                       "shifts_start": [P.beta7, P.beta8, P.beta10, P.beta13, P.beta15],
+                       "shift_retries": rep["shift_retries"],
+                       "shifts_final": list(rep["beta_final"]),
                        "l2": "working set (~2 GB) > L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(step_ms, 50)),

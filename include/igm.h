@@ -99,7 +99,17 @@ typedef struct {
                     substitutions have as many levels as colours (a
                     different preconditioner than the natural order's); b
                     and x stay in the caller's order                      */
-  int reserved[2];
+  int shift_tune;/* shift auto-tuning (Sec. VII-D), 0 ... 64 (0: off, the
+                    shifts stay as given, as in Tables 4 and 5): in the
+                    refinement loop, an inner solve that raised overflow
+                    events at lines 7, 8, 10, 13 or 15 of Fig. 2 raises the
+                    shift of each such line by one (up to d_f), is
+                    discarded (x is not updated, the refinement is not
+                    counted) and runs again from the same b^(k); at most
+                    shift_tune inner solves are discarded per solve, and
+                    every solve starts from the shifts given here.  Not
+                    used by int_gmres_solve.                              */
+  int reserved[1];
 } igm_params;
 
 #define IGM_MAX_M 128
@@ -116,6 +126,9 @@ typedef struct {
   double relres_unscaled;     /* final ||bh - Ah xh|| / ||bh||              */
   double gamma_hist[64];      /* gamma^(k) of eq. (gammak)                  */
   double relres_hist[65];     /* relative residual before refinement k      */
+  int shift_retries;          /* inner solves discarded by shift_tune       */
+  int beta_final[5];          /* beta7, beta8, beta10, beta13, beta15 at the
+                                 end of the solve                           */
 } igm_report;
 
 /* Fills p with the paper's settings: d_f = 30 (Sec. VII-B); precond = 0:

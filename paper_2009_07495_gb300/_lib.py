@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
                 ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("s", C.c_int),
-                ("order", C.c_int), ("reserved", C.c_int * 2)]
+                ("order", C.c_int), ("shift_tune", C.c_int), ("reserved", C.c_int * 1)]
 
     def replace(self, **kw) -> "Params":
         p = Params()
@@ -54,7 +54,8 @@ class Report(C.Structure):
     _fields_ = [("ev", C.c_longlong * 16), ("refinements", C.c_int),
                 ("inner_steps", C.c_int), ("breakdowns", C.c_int), ("status", C.c_int),
                 ("relres", C.c_double), ("relres_unscaled", C.c_double),
-                ("gamma_hist", C.c_double * 64), ("relres_hist", C.c_double * 65)]
+                ("gamma_hist", C.c_double * 64), ("relres_hist", C.c_double * 65),
+                ("shift_retries", C.c_int), ("beta_final", C.c_int * 5)]
 
     def as_dict(self) -> dict:
         k = self.refinements
@@ -63,7 +64,8 @@ class Report(C.Structure):
                     relres=self.relres, relres_unscaled=self.relres_unscaled,
                     ev=np.array(self.ev[:], dtype=np.int64),
                     gamma_hist=np.array(self.gamma_hist[:min(k, 64)]),
-                    relres_hist=np.array(self.relres_hist[:min(k + 1, 65)]))
+                    relres_hist=np.array(self.relres_hist[:min(k + 1, 65)]),
+                    shift_retries=self.shift_retries, beta_final=tuple(self.beta_final[:]))
 
 
 class ServerConfig(C.Structure):

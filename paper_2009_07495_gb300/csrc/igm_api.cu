@@ -359,6 +359,7 @@ igm_status check_params(const igm_params *p) {
   if (p->trsv_chunk < 0) return fail(IGM_EINVAL, "trsv_chunk must be >= 0");
   if (p->s < 0 || p->s > IGM_MAX_S) return fail(IGM_EINVAL, "s must be 0 ... %d", IGM_MAX_S);
   if (p->order != 0 && p->order != 1) return fail(IGM_EINVAL, "order must be 0 or 1");
+  if (p->shift_tune < 0 || p->shift_tune > 64) return fail(IGM_EINVAL, "shift_tune must be 0 ... 64");
   if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
         p->trsv_cluster == 4 || p->trsv_cluster == 8))
     return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
@@ -386,6 +387,8 @@ void fill_report(const SysScal &sc, igm_report *rep) {
   rep->relres_unscaled = sc.relres_unscaled;
   memcpy(rep->gamma_hist, sc.gamma_hist, sizeof rep->gamma_hist);
   memcpy(rep->relres_hist, sc.relres_hist, sizeof rep->relres_hist);
+  rep->shift_retries = sc.retries;
+  for (int t = 0; t < 5; ++t) rep->beta_final[t] = sc.beta[t];
 }
 
 }  // namespace
@@ -776,7 +779,13 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.p = SysParams{params->df,     params->alpha_a, m,                params->precond,
                   params->beta7,  params->beta8,   params->beta10,   params->beta11a,
                   params->beta11b, params->beta13, params->beta15,   params->beta16a,
-                  params->beta16b, params->inner,  params->max_refine, params->tol};
+                  params->beta16b, params->inner,  params->max_refine, params->tol,
+                  params->shift_tune};
+  {
+    const int b0[5] = {params->beta7, params->beta8, params->beta10, params->beta13,
+                       params->beta15};
+    for (int t = 0; t < 5; ++t) d.beta0[t] = b0[t];
+  }
   d.rowptr = rp;
   d.col = cl;
   d.diagpos = dp;
@@ -910,8 +919,8 @@ igm_status run_ir(Batch *b, cudaStream_t s) {
   if (st) return st;
   st = ir_init_host(b, s);
   if (st) return st;
-  int maxr = 0;
-  for (auto h : b->hs) maxr = std::max(maxr, h->prm.max_refine);
+  int maxr = 0;  // refinements plus the inner solves auto-tuning may discard
+  for (auto h : b->hs) maxr = std::max(maxr, h->prm.max_refine + h->prm.shift_tune);
   for (int k = 0; k <= maxr + 1; ++k) {
     CK(cudaGraphLaunch(b->g_check, s));
     g_launches += b->nodes_check;

@@ -32,6 +32,7 @@ struct SysParams {
   int b7, b8, b10, b11a, b11b, b13, b15, b16a, b16b;
   int inner, max_refine;
   double tol;
+  int tune;               // inner solves the shift auto-tuning may discard
 };
 
 // error bits of SysScal::err
@@ -54,6 +55,11 @@ struct SysScal {
   double relres_hist[65];
   double gamma_hist[64];
   double rho_ring[4];      // the last residuals (stall test of the loop)
+  // shift auto-tuning, per line 7, 8, 10, 13, 15 of Fig. 2 (in this order)
+  u64 ev0[5];              // their event counts when the inner solve began
+  int retries;             // inner solves discarded so far
+  int retry;               // 1: the inner solve that just ran is discarded
+  int beta[5];             // their shifts in use (a copy of SysDev::p)
 };
 
 // Schedule and level-packed data of one triangular factor.  Positions
@@ -84,7 +90,9 @@ struct Tri {
 struct SysDev {
   int n, nnz, ld;          // ld = m + 1
   int pad;
-  SysParams p;
+  SysParams p;             // shifts of lines 7, 8, 10, 13, 15 change while
+                           // a solve auto-tunes them
+  int beta0[5];            // those shifts as set up
   const int *rowptr, *col, *diagpos;
   const double *ahat, *a, *d;
   const i64 *abar;

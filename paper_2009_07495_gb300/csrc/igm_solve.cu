@@ -46,7 +46,17 @@ __device__ __forceinline__ const double *vec_of(const SysDev *s, int which) {
 __global__ void k_init_scal(BatchDev B, int mode) {
   int si = blockIdx.x * blockDim.x + threadIdx.x;
   if (si >= B.nsys) return;
-  SysScal *sc = B.sys[si]->sc;
+  SysDev *s = B.sys[si];
+  SysScal *sc = s->sc;
+  // every solve starts from the shifts as set up
+  int *beta[5] = {&s->p.b7, &s->p.b8, &s->p.b10, &s->p.b13, &s->p.b15};
+  for (int t = 0; t < 5; ++t) {
+    *beta[t] = s->beta0[t];
+    sc->beta[t] = s->beta0[t];
+    sc->ev0[t] = 0;
+  }
+  sc->retries = 0;
+  sc->retry = 0;
   for (int k = 0; k < IGM_NEV; ++k) sc->ev[k] = 0;
   sc->status = 5;  // IGM_ENOCONV until the test of Fig. 1 passes
   sc->active = mode == 0 ? 1 : 0;
@@ -225,7 +235,13 @@ __global__ void k_rhs(BatchDev B) {
   const SysDev *s = B.sys[tl.sys];
   SysScal *sc = s->sc;
   if (!g_cyc(sc)) return;
-  if (blockIdx.x == tl.first && threadIdx.x == 0) sc->seq += 1;
+  if (blockIdx.x == tl.first && threadIdx.x == 0) {
+    sc->seq += 1;
+    // event counts of the tuned lines before this inner solve
+    const int line[5] = {IGM_EV_L7, IGM_EV_L8, IGM_EV_L10, IGM_EV_L13, IGM_EV_L15};
+    for (int t = 0; t < 5; ++t) sc->ev0[t] = sc->ev[line[t]];
+    sc->retry = 0;
+  }
   double gam = sc->gamma;
   TILE_LOOP(i) s->r[i] = __ddiv_rn(s->r[i], gam);
 }
@@ -336,7 +352,7 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
 __global__ void k_backsub(BatchDev B) {
   int si = blockIdx.x * blockDim.x + threadIdx.x;
   if (si >= B.nsys) return;
-  const SysDev *s = B.sys[si];
+  SysDev *s = B.sys[si];
   SysScal *sc = s->sc;
   if (!g_cyc(sc)) return;
   const int jeff = sc->jeff, ld = s->ld, df = s->p.df;
@@ -348,6 +364,26 @@ __global__ void k_backsub(BatchDev B) {
     z[a] = __ddiv_rn(acc, scalbn((double)s->H[a + a * ld], -df));
   }
   for (int a = 0; a < jeff; ++a) z[a] = __dmul_rn(sc->nu, z[a]);
+  // shift auto-tuning (refinement loop only): an inner solve that raised
+  // events at a shifted line raises those lines' shifts by one (up to d_f)
+  // and is discarded; the next test of Fig. 1 sees the same x and repeats
+  // refinement k with the new shifts
+  if (sc->mode == 0 && sc->retries < s->p.tune) {
+    const int line[5] = {IGM_EV_L7, IGM_EV_L8, IGM_EV_L10, IGM_EV_L13, IGM_EV_L15};
+    int *beta[5] = {&s->p.b7, &s->p.b8, &s->p.b10, &s->p.b13, &s->p.b15};
+    bool raised = false;
+    for (int t = 0; t < 5; ++t)
+      if (sc->ev[line[t]] != sc->ev0[t] && *beta[t] < s->p.df) {
+        *beta[t] += 1;
+        sc->beta[t] = *beta[t];
+        raised = true;
+      }
+    if (raised) {
+      sc->retries += 1;
+      sc->retry = 1;
+      return;
+    }
+  }
   sc->refinements += 1;
   sc->inner_steps += jeff;
   if (sc->early == 1) sc->breakdowns += 1;
@@ -359,7 +395,7 @@ __global__ void k_update(BatchDev B) {
   Tile tl = B.tiles[blockIdx.x];
   const SysDev *s = B.sys[tl.sys];
   SysScal *sc = s->sc;
-  if (!g_cyc(sc)) return;
+  if (!g_cyc(sc) || sc->retry) return;
   const int jeff = sc->jeff, n = s->n, df = s->p.df;
   const bool ir = sc->mode == 0;
   double gam = sc->gamma;

@@ -27,7 +27,8 @@ def _oparams(orc, P):
     return orc.Params(df=P.df, alpha_a=P.alpha_a, m=P.m, precond=P.precond, beta7=P.beta7,
                       beta8=P.beta8, beta10=P.beta10, beta11a=P.beta11a, beta11b=P.beta11b,
                       beta13=P.beta13, beta15=P.beta15, beta16a=P.beta16a, beta16b=P.beta16b,
-                      tol=P.tol, max_refine=P.max_refine, s=P.s, order=P.order)
+                      tol=P.tol, max_refine=P.max_refine, s=P.s, order=P.order,
+                      shift_tune=P.shift_tune)
 
 
 def _dev(a):
@@ -383,6 +384,86 @@ def test_server_mixed_variants_equal_solo(L, orc):
         assert done and rep["status"] == ro.status == "ok"
         assert rep["refinements"] == ro.refinements
         np.testing.assert_array_equal(x, xo)
+
+
+def _tuned(L, prec, m, b, tune):
+    """shifts of lines 7, 8, 10, 13, 15 set to b, auto-tuning budget tune"""
+    P = L.params_default(prec, m)
+    for k in ("beta7", "beta8", "beta10", "beta13", "beta15"):
+        setattr(P, k, b)
+    P.shift_tune = tune
+    return P
+
+
+@pytest.mark.parametrize("b", [12, 8, 4])
+def test_shift_tune_bit_exact(L, orc, b):
+    """Shift auto-tuning (Sec. VII-D) from shifts too small for the system
+    (the retries fall in the first and in later refinements): the discarded
+    inner solves, the raised shifts and the whole loop equal the oracle's
+    bit for bit; a second solve on the same handle starts again from the
+    set-up shifts and repeats the first."""
+    s = W.config0()
+    P = _tuned(L, 0, 30, b, 40)
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    assert ro.status == "ok" and ro.shift_retries > 0
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    for _ in range(2):
+        x, rep = solver.ir_solve(_dev(s.b))
+        assert rep["status"] == "ok"
+        assert rep["shift_retries"] == ro.shift_retries
+        assert rep["beta_final"] == ro.beta_final
+        assert (rep["refinements"], rep["inner_steps"], rep["breakdowns"]) == \
+            (ro.refinements, ro.inner_steps, ro.breakdowns)
+        np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+        np.testing.assert_array_equal(rep["gamma_hist"], ro.gamma_hist)
+        np.testing.assert_array_equal(rep["ev"], ro.ev)
+        np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    # the retry budget binds on the device as in the oracle
+    P2 = _tuned(L, 0, 30, b, 2)
+    xo2, ro2 = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P2))
+    solver2 = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P2)
+    x2, rep2 = solver2.ir_solve(_dev(s.b))
+    assert rep2["status"] == ro2.status and rep2["shift_retries"] == ro2.shift_retries == 2
+    assert rep2["beta_final"] == ro2.beta_final
+    np.testing.assert_array_equal(rep2["relres_hist"], ro2.relres_hist)
+    np.testing.assert_array_equal(x2.cpu().numpy(), xo2)
+    solver.close()
+    solver2.close()
+
+
+def test_shift_tune_batched_and_served(L, orc):
+    """Systems that tune their shifts beside systems that do not, in one
+    batch and in the server: each result equals its solo solve and the
+    oracle's (retries, final shifts and solution)."""
+    import torch
+    systems = [W.config0(), W.small_cd2d(40, seed=5), W.small_cd3d(10, seed=71),
+               W.small_cd2d(24, seed=72)]
+    params = [_tuned(L, 0, 30, 8, 40), _tuned(L, 0, 30, 0, 40), _tuned(L, 1, 30, 0, 10),
+              L.params_default(0, 30)]
+    svs, solos = [], []
+    for sy, P in zip(systems, params):
+        sv = L.Solver(_dev(sy.rowptr), _dev(sy.col), _dev(sy.val), P)
+        x, rep = sv.ir_solve(_dev(sy.b))
+        solos.append((x.cpu().numpy(), rep))
+        svs.append(sv)
+    out = [torch.empty(sy.n, dtype=torch.float64, device="cuda") for sy in systems]
+    reps = L.ir_solve_batched(svs, [_dev(sy.b) for sy in systems], out)
+    srv = L.Server(budget_bytes=1 << 30, m=30)
+    ids = [srv.submit(sy.rowptr, sy.col, sy.val, sy.b, P) for sy, P in zip(systems, params)]
+    served = [srv.poll(i, wait_ms=60000) for i in ids]
+    srv.close()
+    for k, sy in enumerate(systems):
+        xo, ro = orc.ir_solve(sy.rowptr, sy.col, sy.val, sy.b, _oparams(orc, params[k]))
+        assert ro.status == "ok"
+        for x, rep in ((out[k].cpu().numpy(), reps[k]), solos[k], served[k][1:3]):
+            np.testing.assert_array_equal(x, xo)
+            assert rep["shift_retries"] == ro.shift_retries
+            assert rep["beta_final"] == ro.beta_final
+            assert rep["refinements"] == ro.refinements
+            np.testing.assert_array_equal(rep["ev"], ro.ev)
+    assert solos[0][1]["shift_retries"] > 0 and solos[3][1]["shift_retries"] == 0
+    for sv in svs:
+        sv.close()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
