@@ -16,6 +16,8 @@ namespace igm {
 
 // one CTA per SM: few grid-barrier arrivals, many rows in flight per CTA
 #define IGM_MGS_BLOCK 1024
+// threads of the one-CTA mode (at most IGM_MGS_BLOCK rows: IGM_RPT per thread)
+#define IGM_MGS_ONE_BLOCK 256
 
 // sense-reversal grid barrier with a bounded wait; false if it expired
 __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *err) {
@@ -49,6 +51,22 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *err) {
   return s_ok != 0;
 }
 
+// asynchronous 8-byte copy global -> shared (the one-CTA mode's basis staging)
+__device__ __forceinline__ void mgs_cp_async8(i64 *dst, const i64 *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+__device__ __forceinline__ void mgs_cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void mgs_cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void acc_add(u64 *a, i128 v) {
   u64 lo = (u64)(u128)v, hi = (u64)((u128)v >> 64);
   u64 old = atomicAdd(a, lo);
@@ -72,6 +90,13 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
 #define IGM_RPT 4           // rows in flight per thread
 #define IGM_MSEG_CACHE 64   // segment descriptors a CTA keeps in shared memory
 #define IGM_MGS_WMAX 20480  // rows of w a CTA may keep in shared memory (160 KB)
+
+// the step kernel's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows
+// in all, each system one segment of it (ns segments), every segment
+// descriptor cached in shared memory
+__host__ __device__ __forceinline__ bool mgs_one_cta(const BatchDev &B, int ns) {
+  return B.mgs_g == 1 && B.mgs_wrows > 0 && B.mgs_wrows <= IGM_MGS_BLOCK && ns <= IGM_MSEG_CACHE;
+}
 
 // a segment as the step kernel sees it: its system's arrays and shifts
 struct MSegC {
@@ -112,8 +137,7 @@ __device__ __forceinline__ void mseg_make(const BatchDev &B, int g, int j, MSegC
 // after the barrier of pass i: the exact total of the pass; h_{i,j} (line 7)
 // or h_{j+1,j} (line 10), recorded once per system with the total's event;
 // returns the coefficient pass i+1 needs (line 8) or h_{j+1,j}
-__device__ __forceinline__ i64 mseg_total(const BatchDev &B, const MSegC &c, int i, int j) {
-  const i128 tot = acc_load(acc_slot(B, i % 3, c.sys));
+__device__ __forceinline__ i64 mseg_coef(const MSegC &c, i128 tot, int i, int j) {
   unsigned e = out64(tot);
   if (i <= j) {
     const i64 h = shr(wrap(tot), c.df - c.b7);
@@ -128,21 +152,66 @@ __device__ __forceinline__ i64 mseg_total(const BatchDev &B, const MSegC &c, int
   return h;
 }
 
+__device__ __forceinline__ i64 mseg_total(const BatchDev &B, const MSegC &c, int i, int j) {
+  return mseg_coef(c, acc_load(acc_slot(B, i % 3, c.sys)), i, j);
+}
+
 // Every CTA owns the same rows in every pass (a balanced partition of all
 // systems' rows, planned on the host); when they fit, its rows of w stay in
 // shared memory from pass 0 to line 11, so a pass reads only the two basis
 // vectors it needs (v_i from HBM, v_{i-1} mostly from L2).
-__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j) {
+template <bool ONE>
+__global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
+    k_mgs_step(BatchDev B, int j) {
+  constexpr int BS = ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK;  // threads
   extern __shared__ i64 sw[];  // this CTA's rows of w (B.mgs_wrows > 0)
   __shared__ MSegC s_seg[IGM_MSEG_CACHE + 1];
   __shared__ i64 s_h[IGM_MSEG_CACHE];
+  __shared__ i128 s_tot[ONE ? IGM_MSEG_CACHE : 1];   // pass totals (one-CTA mode)
+  __shared__ i64 s_v[ONE ? 3 : 1][ONE ? IGM_MGS_BLOCK : 1];  // v_{i-1}, v_i, v_{i+1}
   unsigned *err0 = &B.sys[0]->sc->err;
   const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
   const bool wsm = B.mgs_wrows > 0;
+  // ONE: one CTA of IGM_MGS_ONE_BLOCK threads holds every row of every
+  // system (small systems, mgs_one_cta): each system is one segment of it,
+  // its pass totals stay in shared memory, a block barrier replaces the grid
+  // barrier, the basis vectors are staged in shared memory (v_{i+1} copied
+  // asynchronously during pass i, so no pass waits on a global load), and
+  // lines 10 (store) and 12-19 run at the end of this kernel instead of in
+  // k_givens_step; fewer threads keep the per-pass reductions short
+  constexpr bool one = ONE;
   for (int k = threadIdx.x; k < ns && k < IGM_MSEG_CACHE; k += blockDim.x)
     mseg_make(B, g0 + k, j, s_seg[k]);
   __syncthreads();
+  // one-CTA mode: stage v_i into s_v[i % 3] (i <= j)
+  auto stage = [&](int i) {
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = s_seg[k];
+      if (!c.active) continue;
+      const i64 *src = c.V + (size_t)i * c.n + c.row0;
+      i64 *dst = &s_v[i % 3][c.off];
+      for (int q = threadIdx.x; q < c.nrows; q += blockDim.x) mgs_cp_async8(dst + q, src + q);
+    }
+    mgs_cp_async_commit();
+  };
+  if (one) {
+    stage(0);
+    mgs_cp_async_wait_all();
+    __syncthreads();
+  }
   for (int i = 0; i <= j + 1; ++i) {
+    if (one && i + 1 <= j) stage(i + 1);
+    // grid mode: pull this CTA's rows of v_{i+1} into L2 while pass i runs
+    // and waits at its barrier, so pass i+1 streams them from L2
+    if (!one && i + 1 <= j)
+      for (int k = 0; k < ns && k < IGM_MSEG_CACHE; ++k) {
+        const MSegC &c = s_seg[k];
+        if (!c.active) continue;
+        const char *base = (const char *)(c.V + (size_t)(i + 1) * c.n + c.row0);
+        const size_t bytes = (size_t)c.nrows * sizeof(i64);
+        for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
+      }
     // slot (i+1)%3 was last read right after barrier i-2, before barrier i-1
     if (blockIdx.x == 0)
       for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
@@ -160,8 +229,9 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
       if (!c.active) continue;
       const i64 hs = i == 0 ? 0 : (k < IGM_MSEG_CACHE ? s_h[k] : B.mseg_h[g0 + k]);
       const int nr = c.nrows;
-      const i64 *vp = c.V + (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
-      const i64 *vi = c.V + (size_t)(i <= j ? i : 0) * c.n + c.row0;
+      const i64 *vp = one ? &s_v[(i + 2) % 3][c.off]
+                          : c.V + (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
+      const i64 *vi = one ? &s_v[i % 3][c.off] : c.V + (size_t)(i <= j ? i : 0) * c.n + c.row0;
       i64 *wg = c.w, *ws = sw + c.off;
       const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
       // line 8's coefficient as a 32-bit value when it fits: the product
@@ -170,12 +240,12 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
       const bool hs32 = hs == (i64)(int)hs;
       i128 part = 0;
       unsigned evA = 0, evB = 0;
-      for (int q0 = threadIdx.x; q0 < nr; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+      for (int q0 = threadIdx.x; q0 < nr; q0 += IGM_RPT * BS) {
         // all loads of the thread's rows first (memory-level parallelism)
         i64 wv[IGM_RPT], pv[IGM_RPT], qv[IGM_RPT];
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
-          const int q = q0 + u * IGM_MGS_BLOCK;
+          const int q = q0 + u * BS;
           const bool ok = q < nr;
           wv[u] = ok ? ((wsm && i > 0) ? ws[q] : wg[q]) : 0;
           pv[u] = (ok && i > 0) ? vp[q] : 0;
@@ -183,7 +253,7 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
         }
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
-          const int q = q0 + u * IGM_MGS_BLOCK;
+          const int q = q0 + u * BS;
           if (q >= nr) continue;
           i64 wl = wv[u];
           if (i > 0) {
@@ -205,18 +275,24 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
       flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
       flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
       part = block_sum_i128(part);
-      if (threadIdx.x == 0) acc_add(acc_slot(B, i % 3, c.sys), part);
+      if (threadIdx.x == 0) {
+        if (one) s_tot[k] = part;
+        else acc_add(acc_slot(B, i % 3, c.sys), part);
+      }
     }
-    if (!grid_sync(B.bar, err0)) return;
+    if constexpr (ONE) __syncthreads();
+    else if (!grid_sync(B.bar, err0)) return;
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
       if (k < IGM_MSEG_CACHE) {
-        if (s_seg[k].active) s_h[k] = mseg_total(B, s_seg[k], i, j);
+        if (s_seg[k].active)
+          s_h[k] = one ? mseg_coef(s_seg[k], s_tot[k], i, j) : mseg_total(B, s_seg[k], i, j);
       } else {
         MSegC c;
         mseg_make(B, g0 + k, j, c);
         if (c.active) B.mseg_h[g0 + k] = mseg_total(B, c, i, j);
       }
     }
+    if (one) mgs_cp_async_wait_all();  // v_{i+1} is in place for pass i+1
     __syncthreads();
   }
   // line 11 for every system whose divisor is non-zero
@@ -233,16 +309,16 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
     i64 *vn = c.V + (size_t)(j + 1) * c.n + c.row0;
     const i64 *wg = c.w, *ws = sw + c.off;
     unsigned ev = 0, evr = 0;
-    for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+    for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * BS) {
       i64 wv[IGM_RPT];
 #pragma unroll
       for (int u = 0; u < IGM_RPT; ++u) {
-        const int q = q0 + u * IGM_MGS_BLOCK;
+        const int q = q0 + u * BS;
         wv[u] = q < c.nrows ? (wsm ? ws[q] : wg[q]) : 0;
       }
 #pragma unroll
       for (int u = 0; u < IGM_RPT; ++u) {
-        const int q = q0 + u * IGM_MGS_BLOCK;
+        const int q = q0 + u * BS;
         if (q >= c.nrows) continue;
         const i64 v = fx_div(wv[u], hn, c.b11a, c.b11b, c.df, ev);
         evr += (v < INT32_MIN || v > INT32_MAX);
@@ -251,6 +327,21 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_step(BatchDev B, int j
     }
     flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
     flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
+  }
+  if (one) {
+    // lines 10 (store) and 12-19, one thread per system, after line 11 as
+    // in k_givens_step
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      const MSegC &c = s_seg[k];
+      if (!c.active) continue;
+      const SysDev *s = B.sys[c.sys];
+      const i64 hj1 = s_h[k];
+      s->H[j + 1 + j * c.ld] = hj1;
+      c.sc->hnext = hj1;
+      c.sc->normj = shr(hj1, c.b11b) == 0 ? -1 : j;
+      givens_col(s, c.sc, j, hj1);
+    }
   }
 }
 
@@ -403,7 +494,7 @@ int persistent_grid(int ntiles) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step, IGM_MGS_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step<false>, IGM_MGS_BLOCK, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0);
     g_mgs_blocks_per_sm = a < b ? a : b;
     if (g_mgs_blocks_per_sm < 1) g_mgs_blocks_per_sm = 1;
@@ -450,16 +541,21 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> 
 }
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
+  if (mgs_one_cta(B, B.nsys)) {
+    // one CTA, no grid barrier; it runs lines 12-19 itself
+    k_mgs_step<true><<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
+    return;
+  }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mgs_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mgs_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          IGM_MGS_WMAX * (int)sizeof(i64));
     attr = true;
   }
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};
-  cudaLaunchCooperativeKernel((const void *)k_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args,
+  cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G), dim3(IGM_MGS_BLOCK), args,
                               (size_t)B.mgs_wrows * sizeof(i64), st);
   k_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j);
   k_acc_clear<<<(B.nsys + 255) / 256, 256, 0, st>>>(B);
