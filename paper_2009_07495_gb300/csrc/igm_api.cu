@@ -94,11 +94,13 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   int mgs_g = 1, mgs_wrows = 0;
   std::vector<int> mptr;
   std::vector<Tile> mseg;
-  mgs_plan(sysn, persistent_grid(1 << 30), mgs_g, mptr, mseg, mgs_wrows);
+  std::vector<int> sys_seg;
+  mgs_plan(sysn, persistent_grid(1 << 30), mgs_g, mptr, mseg, mgs_wrows, sys_seg);
   const int MS = (int)mseg.size();
-  int *d_mptr;
+  int *d_mptr, *d_sysseg;
   Tile *d_mseg;
   long long *d_mh;
+  u64 *d_mpart;
   b->arena.want(&d_tiles, T);
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
   b->arena.want(&d_stiles, ST);
@@ -114,6 +116,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   b->arena.want(&d_mptr, mgs_g + 1);
   b->arena.want(&d_mseg, MS > 0 ? MS : 1);
   b->arena.want(&d_mh, MS > 0 ? MS : 1);
+  b->arena.want(&d_mpart, 4 * (size_t)(MS > 0 ? MS : 1));
+  b->arena.want(&d_sysseg, ns + 1);
   if (b->arena.commit() != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -130,6 +134,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   CK(cudaMemset(d_acc, 0, 6 * sizeof(u64) * ns));
   CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (mgs_g + 1), cudaMemcpyHostToDevice));
   if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_sysseg, sys_seg.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
   BatchDev &B = b->bd;
   B = BatchDev{};
   B.nsys = ns;
@@ -153,6 +158,9 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.mseg_ptr = d_mptr;
   B.mseg = d_mseg;
   B.mseg_h = d_mh;
+  B.nseg = MS;
+  B.mpart = d_mpart;
+  B.sys_seg = d_sysseg;
   B.mgs_wrows = mgs_wrows;
   B.trsv_maxlev = maxlev;
   B.trsv_maxw = maxw;

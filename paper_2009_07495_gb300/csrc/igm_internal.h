@@ -149,7 +149,8 @@ struct BatchDev {
   unsigned *ticket;        // 4 dynamic-ticket counters
   int *nact;               // systems still refining
   unsigned *bar;           // grid barrier: [0] arrivals, [1] generation
-  u64 *acc;                // 3 slots x nsys x {lo, hi}: exact int128 sums
+  u64 *acc;                // 3 slots x nsys x {lo, hi}: the line-10 total of
+                           // the integer Arnoldi step (slot (j+1) % 3)
   double *cpart;           // 3 slots x maxG x nsys FP64 per-CTA partials
   int maxg;                // CTAs of the persistent kernels
   // integer Arnoldi step: CTA c sweeps the segments
@@ -159,6 +160,10 @@ struct BatchDev {
   const int *mseg_ptr;
   const Tile *mseg;
   i64 *mseg_h;             // per segment: the coefficient of the next pass
+  int nseg;                // segments in all
+  u64 *mpart;              // 2 slots (pass parity) x nseg {lo, hi}: a pass's
+                           // exact int128 sum over each segment
+  const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
   int mgs_wrows;           // rows of w each CTA keeps in shared memory (0: global)
   int trsv_maxlev;         // most local levels of a substitution chunk
   int trsv_maxw;           // most rows of one level group

@@ -19,32 +19,55 @@ namespace igm {
 // threads of the one-CTA mode (at most IGM_MGS_BLOCK rows: IGM_RPT per thread)
 #define IGM_MGS_ONE_BLOCK 256
 
-// sense-reversal grid barrier with a bounded wait; false if it expired
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid barrier with a bounded wait; false if it expired.  bar[0] counts
+// arrivals, bar[1] is the generation.  Thread 0 arrives with an acq_rel add
+// after the block barrier (so the CTA's writes before the barrier are
+// released with it); the last arrival resets the count and releases the
+// next generation, which the others acquire.
 __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned *err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
+    unsigned *gen = bar + 1;
+    const unsigned g = ld_relaxed_u32(gen);
+    const unsigned arrived = atom_add_acq_rel_u32(bar, 1u);
     int ok = 1;
     if (arrived == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      st_relaxed_u32(bar, 0u);
+      st_release_u32(gen, g + 1u);
     } else {
       int it = 0;
-      while (*gen == g) {
+      while (ld_acquire_u32(gen) == g) {
         if (++it > IGM_SPIN_MAX) {
           atomicOr(err, ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        if (it > 64) __nanosleep(20);
+        if (it > 256) __nanosleep(20);
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -67,16 +90,15 @@ __device__ __forceinline__ void mgs_cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-__device__ __forceinline__ void acc_add(u64 *a, i128 v) {
-  u64 lo = (u64)(u128)v, hi = (u64)((u128)v >> 64);
-  u64 old = atomicAdd(a, lo);
-  u64 carry = (old + lo) < old ? 1ull : 0ull;
-  atomicAdd(a + 1, hi + carry);
+// a pass's int128 sum over one segment: 2 slots (pass parity) x segments
+__device__ __forceinline__ u64 *mpart_at(const BatchDev &B, int i, int g) {
+  return B.mpart + 2 * ((size_t)(i & 1) * B.nseg + g);
 }
 
+// an int128 {lo, hi} pair (16-byte aligned) read from L2
 __device__ __forceinline__ i128 acc_load(const u64 *a) {
-  u64 lo = __ldcg((const unsigned long long *)a), hi = __ldcg((const unsigned long long *)a + 1);
-  return (i128)(((u128)hi << 64) | (u128)lo);
+  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(a));
+  return (i128)(((u128)v.y << 64) | (u128)v.x);
 }
 
 __device__ __forceinline__ u64 *acc_slot(const BatchDev &B, int slot, int sys) {
@@ -152,8 +174,36 @@ __device__ __forceinline__ i64 mseg_coef(const MSegC &c, i128 tot, int i, int j)
   return h;
 }
 
-__device__ __forceinline__ i64 mseg_total(const BatchDev &B, const MSegC &c, int i, int j) {
-  return mseg_coef(c, acc_load(acc_slot(B, i % 3, c.sys)), i, j);
+// mseg_coef in grid mode; after the last pass the segment holding row 0 also
+// hands the line-10 total to k_givens_step
+__device__ __forceinline__ i64 mseg_publish(const BatchDev &B, const MSegC &c, i128 tot, int i,
+                                            int j) {
+  if (i == j + 1 && c.first) {
+    u64 *a = acc_slot(B, (j + 1) % 3, c.sys);
+    a[0] = (u64)(u128)tot;
+    a[1] = (u64)((u128)tot >> 64);
+  }
+  return mseg_coef(c, tot, i, j);
+}
+
+// the exact total of pass i over every segment of c's system, summed by one
+// warp from the segments' sums (valid in lane 0)
+__device__ __forceinline__ i128 mseg_sum(const BatchDev &B, const MSegC &c, int i) {
+  const int lane = threadIdx.x & 31;
+  const int lo = B.sys_seg[c.sys], hi = B.sys_seg[c.sys + 1];
+  i128 t = 0;
+  // up to 256 segments per round, all loads in flight together
+  for (int g0 = lo + lane; g0 < hi; g0 += 32 * 8) {
+    i128 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int g = g0 + 32 * u;
+      v[u] = g < hi ? acc_load(mpart_at(B, i, g)) : (i128)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += v[u];
+  }
+  return warp_sum_i128(t);
 }
 
 // Every CTA owns the same rows in every pass (a balanced partition of all
@@ -212,13 +262,6 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
         for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
       }
-    // slot (i+1)%3 was last read right after barrier i-2, before barrier i-1
-    if (blockIdx.x == 0)
-      for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
-        u64 *a = acc_slot(B, (i + 1) % 3, s);
-        a[0] = 0;
-        a[1] = 0;
-      }
     for (int k = 0; k < ns; ++k) {
       if (k >= IGM_MSEG_CACHE) {  // descriptor beyond the cache: one spare slot
         __syncthreads();
@@ -276,20 +319,36 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
       flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
       part = block_sum_i128(part);
       if (threadIdx.x == 0) {
-        if (one) s_tot[k] = part;
-        else acc_add(acc_slot(B, i % 3, c.sys), part);
+        if (one) {
+          s_tot[k] = part;
+        } else {  // slot i & 1 was last read before barrier i-1
+          u64 *pp = mpart_at(B, i, g0 + k);
+          pp[0] = (u64)(u128)part;
+          pp[1] = (u64)((u128)part >> 64);
+        }
       }
     }
-    if constexpr (ONE) __syncthreads();
-    else if (!grid_sync(B.bar, err0)) return;
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      if (k < IGM_MSEG_CACHE) {
-        if (s_seg[k].active)
-          s_h[k] = one ? mseg_coef(s_seg[k], s_tot[k], i, j) : mseg_total(B, s_seg[k], i, j);
-      } else {
-        MSegC c;
-        mseg_make(B, g0 + k, j, c);
-        if (c.active) B.mseg_h[g0 + k] = mseg_total(B, c, i, j);
+    if constexpr (ONE) {
+      __syncthreads();
+      for (int k = threadIdx.x; k < ns; k += blockDim.x)
+        if (s_seg[k].active) s_h[k] = mseg_coef(s_seg[k], s_tot[k], i, j);
+    } else {
+      if (!grid_sync(B.bar, err0)) return;
+      // one warp per segment: its system's total from all segment sums; the
+      // CTA holding row 0 hands the line-10 total to k_givens_step
+      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int k = wid; k < ns; k += BS / 32) {
+        if (k < IGM_MSEG_CACHE) {
+          if (!s_seg[k].active) continue;
+          const i128 tot = mseg_sum(B, s_seg[k], i);
+          if (lane == 0) s_h[k] = mseg_publish(B, s_seg[k], tot, i, j);
+        } else {
+          MSegC c;
+          mseg_make(B, g0 + k, j, c);
+          if (!c.active) continue;
+          const i128 tot = mseg_sum(B, c, i);
+          if (lane == 0) B.mseg_h[g0 + k] = mseg_publish(B, c, tot, i, j);
+        }
       }
     }
     if (one) mgs_cp_async_wait_all();  // v_{i+1} is in place for pass i+1
@@ -359,16 +418,6 @@ __global__ void k_givens_step(BatchDev B, int j) {
   sc->hnext = hj1;
   sc->normj = shr(hj1, P.b11b) == 0 ? -1 : j;
   givens_col(s, sc, j, hj1);
-}
-
-// keeps accumulator slot 0 zero between steps (pass 0 of the next step sums
-// into it); runs after k_givens_step has read the last slot
-__global__ void k_acc_clear(BatchDev B) {
-  for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < B.nsys; si += gridDim.x * blockDim.x) {
-    u64 *a = acc_slot(B, 0, si);
-    a[0] = 0;
-    a[1] = 0;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -513,7 +562,7 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
 }
 
 void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> &ptr,
-              std::vector<Tile> &seg, int &wrows) {
+              std::vector<Tile> &seg, int &wrows, std::vector<int> &sys_seg) {
   long long N = 0;
   for (int v : n) N += v;
   long long g = (N + IGM_MGS_BLOCK - 1) / IGM_MGS_BLOCK;
@@ -538,6 +587,9 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> 
   }
   ptr[G] = (int)seg.size();
   wrows = maxrows <= IGM_MGS_WMAX ? maxrows : 0;
+  // segments run in system order: system s owns [sys_seg[s], sys_seg[s+1])
+  sys_seg.assign(n.size() + 1, (int)seg.size());
+  for (int g = (int)seg.size() - 1; g >= 0; --g) sys_seg[seg[g].sys] = g;
 }
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
@@ -558,7 +610,6 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G), dim3(IGM_MGS_BLOCK), args,
                               (size_t)B.mgs_wrows * sizeof(i64), st);
   k_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j);
-  k_acc_clear<<<(B.nsys + 255) / 256, 256, 0, st>>>(B);
 }
 
 }  // namespace igm
