@@ -307,11 +307,15 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
           }
           if (wsm) ws[q] = wl;
           else if (i > 0) wg[q] = wl;
+          // lines 7 / 10: a 32x32 -> 64-bit multiply when both factors fit
+          // (exact, never out of range: the same word, no event)
           if (i <= j) {
-            part += (i128)mulw(wl >> s7, qv[u], evA);
+            const i64 a = wl >> s7, b = qv[u];
+            part += (i128)((a == (i64)(int)a && b == (i64)(int)b) ? (i64)(int)a * (i64)(int)b
+                                                                  : mulw(a, b, evA));
           } else {
             const i64 a = wl >> s10;
-            part += (i128)mulw(a, a, evA);
+            part += (i128)(a == (i64)(int)a ? (i64)(int)a * (i64)(int)a : mulw(a, a, evA));
           }
         }
       }
