@@ -356,14 +356,16 @@ __global__ void k_backsub(BatchDev B) {
   SysScal *sc = s->sc;
   if (!g_cyc(sc)) return;
   const int jeff = sc->jeff, ld = s->ld, df = s->p.df;
-  double *z = s->yfp;
+  // y in thread-local memory while it is formed: the loads of H do not
+  // wait for the stores of y
+  double z[IGM_MAX_M];
   for (int a = jeff - 1; a >= 0; --a) {
     double acc = scalbn((double)s->g[a], -df);
     for (int b = a + 1; b < jeff; ++b)
       acc = __dsub_rn(acc, __dmul_rn(scalbn((double)s->H[a + b * ld], -df), z[b]));
     z[a] = __ddiv_rn(acc, scalbn((double)s->H[a + a * ld], -df));
   }
-  for (int a = 0; a < jeff; ++a) z[a] = __dmul_rn(sc->nu, z[a]);
+  for (int a = 0; a < jeff; ++a) s->yfp[a] = __dmul_rn(sc->nu, z[a]);
   // shift auto-tuning (refinement loop only): an inner solve that raised
   // events at a shifted line raises those lines' shifts by one (up to d_f)
   // and is discarded; the next test of Fig. 1 sees the same x and repeats
@@ -399,12 +401,16 @@ __global__ void k_update(BatchDev B) {
   const int jeff = sc->jeff, n = s->n, df = s->p.df;
   const bool ir = sc->mode == 0;
   double gam = sc->gamma;
+  __shared__ double s_y[IGM_MAX_M];
+  for (int i = threadIdx.x; i < jeff; i += blockDim.x) s_y[i] = s->yfp[i];
+  __syncthreads();
   // y_i (v_il 2^-df): the scaled basis entry is exact, built with integer
   // operations (GB300's FP64 rate is low)
   TILE_LOOP(l) {
     double acc = ir ? 0.0 : s->xk[l];
+#pragma unroll 8
     for (int i = 0; i < jeff; ++i)
-      acc = __dadd_rn(acc, __dmul_rn(s->yfp[i], i2d_scaled(s->V[(size_t)i * n + l], df)));
+      acc = __dadd_rn(acc, __dmul_rn(s_y[i], i2d_scaled(s->V[(size_t)i * n + l], df)));
     if (ir) s->xt[l] = __dadd_rn(s->xt[l], __dmul_rn(gam, acc));
     else s->xk[l] = acc;
   }
