@@ -466,6 +466,46 @@ def test_shift_tune_batched_and_served(L, orc):
         sv.close()
 
 
+@pytest.mark.parametrize("count", [64, 80])
+def test_batched_many_tiny_systems(L, orc, count):
+    """Tiny systems (n = 9) batched so that every row fits one CTA: 64
+    systems run the Arnoldi step's one-CTA mode (its segment cache full),
+    80 the cooperative grid mode with one CTA whose segments overflow the
+    cache.  Every result equals the oracle's bit for bit."""
+    import torch
+    systems = [W.small_cd2d(3, seed=200 + k) for k in range(count)]
+    P = L.params_default(0, 10)
+    svs = [L.Solver(_dev(sy.rowptr), _dev(sy.col), _dev(sy.val), P) for sy in systems]
+    out = [torch.empty(sy.n, dtype=torch.float64, device="cuda") for sy in systems]
+    reps = L.ir_solve_batched(svs, [_dev(sy.b) for sy in systems], out)
+    for k, sy in enumerate(systems):
+        xo, ro = orc.ir_solve(sy.rowptr, sy.col, sy.val, sy.b, _oparams(orc, P))
+        assert ro.status == "ok" and reps[k]["status"] == "ok"
+        assert reps[k]["refinements"] == ro.refinements
+        np.testing.assert_array_equal(reps[k]["relres_hist"], ro.relres_hist)
+        np.testing.assert_array_equal(out[k].cpu().numpy(), xo)
+    for sv in svs:
+        sv.close()
+
+
+@pytest.mark.parametrize("n", [1024, 1025])
+def test_arnoldi_mode_boundary(L, orc, n):
+    """n = 1024 is the largest system of the one-CTA Arnoldi mode, 1025 the
+    smallest of the grid mode (two CTAs): both equal the oracle bit for
+    bit, including the basis and Hessenberg state of the last inner solve."""
+    s = W.config0() if n == 1024 else W.banded_random(1025, np.random.default_rng(7))
+    P = L.params_default(0, 30)
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert ro.status == "ok" and rep["status"] == "ok"
+    assert rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["relres_hist"], ro.relres_hist)
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    solver.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_fp64_gmres_comparison_solver(L, orc, prec):
     """The FP64 GMRES(m) comparison solver (params.inner = 1) converges like
