@@ -1,12 +1,14 @@
 // igm_mgs.cu -- lines 6-11 of Fig. 2 (modified Gram-Schmidt, norm, division)
 // for one Arnoldi step j as ONE persistent kernel: all CTAs are co-resident
 // (cooperative launch) and sweep the rows of every system once per pass;
-// between passes the exact int128 sum of the pass is formed by two-word
-// atomics (low word with carry into the high word) and published by a
-// bounded grid barrier.  Pass i <= j fuses the line-8 update with h_{i-1,j}
-// and the line-7 inner product with v_i; pass j+1 fuses the last update with
-// the line-10 norm; then line 11 and (one thread per system) lines 12-19.
-// The basis streams from HBM once per pass; w stays in L2.
+// each CTA stores its exact int128 sum of the pass per segment, a bounded
+// grid barrier publishes them, and every CTA adds up the sums of its
+// systems.  Pass i <= j fuses the line-8 update with h_{i-1,j} and the
+// line-7 inner product with v_i; pass j+1 fuses the last update with the
+// line-10 norm; then line 11 and (one thread per system) lines 12-19.  The
+// basis streams from HBM once per pass; w stays in shared memory.  Small
+// batches (every row in one CTA) run a one-CTA variant without the grid
+// barrier that also does lines 12-19 itself.
 #include <algorithm>
 
 #include "igm_dev.cuh"
