@@ -86,7 +86,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   long long *d_part;
   double *d_partd;
   unsigned *d_ticket, *d_bar;
-  u64 *d_acc;
   double *d_cpart;
   int maxg = persistent_grid(ST);
   std::vector<int> sysn(ns);
@@ -105,7 +104,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
   b->arena.want(&d_stiles, ST);
   b->arena.want(&d_bar, 2);
-  b->arena.want(&d_acc, 6 * (size_t)ns);
   b->arena.want(&d_cpart, 3 * (size_t)maxg * ns);
   b->arena.want(&d_snt, ns);
   b->arena.want(&d_sp, ns);
@@ -131,7 +129,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
   CK(cudaMemset(d_nact, 0, sizeof(int)));
   CK(cudaMemset(d_bar, 0, 2 * sizeof(unsigned)));
-  CK(cudaMemset(d_acc, 0, 6 * sizeof(u64) * ns));
   CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (mgs_g + 1), cudaMemcpyHostToDevice));
   if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sysseg, sys_seg.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
@@ -151,7 +148,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.ticket = d_ticket;
   B.nact = d_nact;
   B.bar = d_bar;
-  B.acc = d_acc;
   B.cpart = d_cpart;
   B.maxg = maxg;
   B.mgs_g = mgs_g;

@@ -149,8 +149,6 @@ struct BatchDev {
   unsigned *ticket;        // 4 dynamic-ticket counters
   int *nact;               // systems still refining
   unsigned *bar;           // grid barrier: [0] arrivals, [1] generation
-  u64 *acc;                // 3 slots x nsys x {lo, hi}: the line-10 total of
-                           // the integer Arnoldi step (slot (j+1) % 3)
   double *cpart;           // 3 slots x maxG x nsys FP64 per-CTA partials
   int maxg;                // CTAs of the persistent kernels
   // integer Arnoldi step: CTA c sweeps the segments

@@ -5,10 +5,10 @@
 // grid barrier publishes them, and every CTA adds up the sums of its
 // systems.  Pass i <= j fuses the line-8 update with h_{i-1,j} and the
 // line-7 inner product with v_i; pass j+1 fuses the last update with the
-// line-10 norm; then line 11 and (one thread per system) lines 12-19.  The
-// basis streams from HBM once per pass; w stays in shared memory.  Small
-// batches (every row in one CTA) run a one-CTA variant without the grid
-// barrier that also does lines 12-19 itself.
+// line-10 norm; then line 11 and, by the CTA holding each system's row 0,
+// lines 12-19.  The basis streams from HBM once per pass; w stays in shared
+// memory.  Small batches (every row in one CTA) run a one-CTA variant
+// without the grid barrier.
 #include <algorithm>
 
 #include "igm_dev.cuh"
@@ -103,10 +103,6 @@ __device__ __forceinline__ i128 acc_load(const u64 *a) {
   return (i128)(((u128)v.y << 64) | (u128)v.x);
 }
 
-__device__ __forceinline__ u64 *acc_slot(const BatchDev &B, int slot, int sys) {
-  return B.acc + 2 * ((size_t)slot * B.nsys + sys);
-}
-
 __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
   return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
 }
@@ -176,16 +172,13 @@ __device__ __forceinline__ i64 mseg_coef(const MSegC &c, i128 tot, int i, int j)
   return h;
 }
 
-// mseg_coef in grid mode; after the last pass the segment holding row 0 also
-// hands the line-10 total to k_givens_step
-__device__ __forceinline__ i64 mseg_publish(const BatchDev &B, const MSegC &c, i128 tot, int i,
-                                            int j) {
-  if (i == j + 1 && c.first) {
-    u64 *a = acc_slot(B, (j + 1) % 3, c.sys);
-    a[0] = (u64)(u128)tot;
-    a[1] = (u64)((u128)tot >> 64);
-  }
-  return mseg_coef(c, tot, i, j);
+// lines 10 (store of h_{j+1,j}) and 12-19 of c's system (one thread)
+__device__ __forceinline__ void givens_tail(const BatchDev &B, const MSegC &c, int j, i64 hj1) {
+  const SysDev *s = B.sys[c.sys];
+  s->H[j + 1 + j * c.ld] = hj1;
+  c.sc->hnext = hj1;
+  c.sc->normj = shr(hj1, c.b11b) == 0 ? -1 : j;
+  givens_col(s, c.sc, j, hj1);
 }
 
 // the exact total of pass i over every segment of c's system, summed by one
@@ -228,9 +221,8 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
   // system (small systems, mgs_one_cta): each system is one segment of it,
   // its pass totals stay in shared memory, a block barrier replaces the grid
   // barrier, the basis vectors are staged in shared memory (v_{i+1} copied
-  // asynchronously during pass i, so no pass waits on a global load), and
-  // lines 10 (store) and 12-19 run at the end of this kernel instead of in
-  // k_givens_step; fewer threads keep the per-pass reductions short
+  // asynchronously during pass i, so no pass waits on a global load); fewer
+  // threads keep the per-pass reductions short
   constexpr bool one = ONE;
   for (int k = threadIdx.x; k < ns && k < IGM_MSEG_CACHE; k += blockDim.x)
     mseg_make(B, g0 + k, j, s_seg[k]);
@@ -340,20 +332,19 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
         if (s_seg[k].active) s_h[k] = mseg_coef(s_seg[k], s_tot[k], i, j);
     } else {
       if (!grid_sync(B.bar, err0)) return;
-      // one warp per segment: its system's total from all segment sums; the
-      // CTA holding row 0 hands the line-10 total to k_givens_step
+      // one warp per segment: its system's total from all segment sums
       const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
       for (int k = wid; k < ns; k += BS / 32) {
         if (k < IGM_MSEG_CACHE) {
           if (!s_seg[k].active) continue;
           const i128 tot = mseg_sum(B, s_seg[k], i);
-          if (lane == 0) s_h[k] = mseg_publish(B, s_seg[k], tot, i, j);
+          if (lane == 0) s_h[k] = mseg_coef(s_seg[k], tot, i, j);
         } else {
           MSegC c;
           mseg_make(B, g0 + k, j, c);
           if (!c.active) continue;
           const i128 tot = mseg_sum(B, c, i);
-          if (lane == 0) B.mseg_h[g0 + k] = mseg_publish(B, c, tot, i, j);
+          if (lane == 0) B.mseg_h[g0 + k] = mseg_coef(c, tot, i, j);
         }
       }
     }
@@ -393,38 +384,20 @@ __global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
     flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
     flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
   }
-  if (one) {
-    // lines 10 (store) and 12-19, one thread per system, after line 11 as
-    // in k_givens_step
-    __syncthreads();
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      const MSegC &c = s_seg[k];
-      if (!c.active) continue;
-      const SysDev *s = B.sys[c.sys];
-      const i64 hj1 = s_h[k];
-      s->H[j + 1 + j * c.ld] = hj1;
-      c.sc->hnext = hj1;
-      c.sc->normj = shr(hj1, c.b11b) == 0 ? -1 : j;
-      givens_col(s, c.sc, j, hj1);
+  // lines 10 (store) and 12-19, one thread per system, after line 11: the
+  // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
+  __syncthreads();
+  for (int k = threadIdx.x; k < ns; k += BS) {
+    if (k < IGM_MSEG_CACHE) {
+      if (s_seg[k].active && s_seg[k].first) givens_tail(B, s_seg[k], j, s_h[k]);
+    } else {
+      MSegC c;
+      mseg_make(B, g0 + k, j, c);
+      if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
     }
   }
 }
 
-// lines 10 (store) and 12-19 after k_mgs_step, one thread per system
-__global__ void k_givens_step(BatchDev B, int j) {
-  int si = blockIdx.x * blockDim.x + threadIdx.x;
-  if (si >= B.nsys) return;
-  const SysDev *s = B.sys[si];
-  SysScal *sc = s->sc;
-  if (!m_step(s, j)) return;
-  const SysParams &P = s->p;
-  unsigned e = 0;
-  i64 hj1 = fx_sqrt(wrap(acc_load(acc_slot(B, (j + 1) % 3, si))), 2 * P.df - 2 * P.b10, P.df, e);
-  s->H[j + 1 + j * s->ld] = hj1;
-  sc->hnext = hj1;
-  sc->normj = shr(hj1, P.b11b) == 0 ? -1 : j;
-  givens_col(s, sc, j, hj1);
-}
 
 // ---------------------------------------------------------------------------
 // The same step for the FP64 comparison solver: per-CTA partial sums per
@@ -600,7 +573,7 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> 
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   if (mgs_one_cta(B, B.nsys)) {
-    // one CTA, no grid barrier; it runs lines 12-19 itself
+    // one CTA, no grid barrier
     k_mgs_step<true><<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
     return;
   }
@@ -615,7 +588,6 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   void *args[] = {&b, &j};
   cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G), dim3(IGM_MGS_BLOCK), args,
                               (size_t)B.mgs_wrows * sizeof(i64), st);
-  k_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j);
 }
 
 }  // namespace igm
