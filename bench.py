@@ -167,8 +167,7 @@ def job_throughput(local_ms: float, steps: int, dist=None, device="cpu") -> tupl
 
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
                       m: int, terms: int = 0) -> float:
-    """Bytes the method must move per launch (the per-unit figures of the
-    design notes): SpMV nnz ((s+1) b_val + 4) + 4(n+1) + 16n (s correction
+    """Bytes the method must move per launch: SpMV nnz ((s+1) b_val + 4) + 4(n+1) + 16n (s correction
     terms, v_j in, w out); Arnoldi step j = m-1:
     each of the m basis vectors once (8n each), w in and v_m out (8n each);
     one triangular solve (nnz_tri + n) 12 + 16 n; FP64 residual

@@ -18,7 +18,7 @@
  * A sum counts once if its exact total (of the int64 summands) is out of
  * range, and each product counts once if its exact value is.
  *
- * Readings of the paper that this file fixes (all listed in the design notes):
+ * Readings of the paper that this file fixes:
  *  - "right shift by beta" is floor division by 2^beta (arithmetic shift),
  *    Sec. V-A;
  *  - "cast" from FP to integer truncates toward zero (Sec. IV-B, V-D, VI-A);
