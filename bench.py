@@ -167,11 +167,11 @@ def job_throughput(local_ms: float, steps: int, dist=None, device="cpu") -> tupl
 
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
                       m: int, terms: int = 0) -> float:
-    """Bytes the method must move per launch: SpMV nnz ((s+1) b_val + 4) + 4(n+1) + 16n (s correction
-    terms, v_j in, w out); Arnoldi step j = m-1:
-    each of the m basis vectors once (8n each), w in and v_m out (8n each);
-    one triangular solve (nnz_tri + n) 12 + 16 n; FP64 residual
-    nnz 12 + 4(n+1) + 24 n."""
+    """Bytes the method must move per launch.  SpMV: nnz ((s+1) b_val + 4)
+    + 4(n+1) + 16n (s correction terms, v_j in, w out).  Arnoldi step
+    j = m-1: each of the m basis vectors once (8n each), w in and v_m out
+    (8n each).  One triangular solve: (nnz_tri + n) 12 + 16n.  FP64
+    residual: nnz 12 + 4(n+1) + 24n."""
     if kind == "spmv":
         return nnz * ((terms + 1) * val_bytes + 4) + 4 * (n + 1) + 16 * n
     if kind == "arnoldi":
