@@ -39,6 +39,10 @@ def test_default_params_are_the_papers(lib):
     assert (p.beta11a, p.beta11b, p.beta13, p.beta15, p.beta16a, p.beta16b) == (16, 14, 16, 16, 16, 14)
     q = L.params_default(1, 50)
     assert (q.alpha_a, q.beta7, q.beta11a, q.beta11b, q.beta16a, q.m) == (32, 0, 30, 0, 30, 50)
+    # the paper's method by default: natural order, s = 0, fixed shifts,
+    # integer inner solver, tol 1e-10
+    for r in (p, q):
+        assert (r.order, r.s, r.shift_tune, r.inner, r.tol) == (0, 0, 0, 0, 1e-10)
 
 
 def test_struct_layouts(tmp_path):
