@@ -109,7 +109,20 @@ typedef struct {
                     shift_tune inner solves are discarded per solve, and
                     every solve starts from the shifts given here.  Not
                     used by int_gmres_solve.                              */
-  int reserved[1];
+  /* Launch-configuration knobs (the results do not depend on them; tests use
+     them to reach every code path on small systems). */
+  int mgs_wmax;  /* rows of w one CTA of the Arnoldi step (lines 6-11) may
+                    keep in shared memory: 0 automatic (20,480), -1 none (w
+                    stays in global memory), k > 0 at most k rows.  In a
+                    batch the first system's value applies.               */
+  int wait_us;   /* bound of each device wait of the line-1'/5' substitutions
+                    in microseconds (0: 1 s); an expired wait ends the call
+                    with IGM_ETIMEOUT                                      */
+  int test_stall;/* tests of the bounded waits only: 1 = the first chunk of
+                    every substitution never signals its progress, so the
+                    next chunk's wait expires and the call returns
+                    IGM_ETIMEOUT (0 in normal use)                         */
+  int reserved[4];
 } igm_params;
 
 #define IGM_MAX_M 128
@@ -202,8 +215,9 @@ igm_status igm_norm2(const double *x, int n, double *out, void *stream);
  * Scratch (per-CTA partial sums and counters, 32 KB) lives in a static
  * device array held by every GPU that loads the library until the process
  * exits; the call allocates nothing.  x: n doubles and out: one double,
- * both already in device (or managed) memory; 0 <= n <= 8,388,608, larger n
- * is rejected with IGM_EINVAL.  The first call on each device resolves the
+ * both already in device (or managed) memory of the current device (memory
+ * of another device is refused with IGM_EINVAL); 0 <= n <= 8,388,608,
+ * larger n is rejected with IGM_EINVAL.  The first call on each device resolves the
  * array's device address; make that first call before any stream capture.
  * All calls share the array: calls whose GPU work overlaps (other streams
  * or threads on the same device) race; calls on one stream are ordered.

@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("beta15", C.c_int), ("beta16a", C.c_int), ("beta16b", C.c_int),
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
                 ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("s", C.c_int),
-                ("order", C.c_int), ("shift_tune", C.c_int), ("reserved", C.c_int * 1)]
+                ("order", C.c_int), ("shift_tune", C.c_int), ("mgs_wmax", C.c_int),
+                ("wait_us", C.c_int), ("test_stall", C.c_int), ("reserved", C.c_int * 4)]
 
     def replace(self, **kw) -> "Params":
         p = Params()

@@ -32,6 +32,20 @@ igm_status fail(igm_status st, const char *fmt, ...) {
 
 std::atomic<long long> g_launches{0};
 
+namespace igm {
+namespace {
+thread_local cudaError_t t_launch_err = cudaSuccess;
+}
+void note_launch(cudaError_t e) {
+  if (e != cudaSuccess && t_launch_err == cudaSuccess) t_launch_err = e;
+}
+cudaError_t take_launch_error() {
+  const cudaError_t e = t_launch_err;
+  t_launch_err = cudaSuccess;
+  return e;
+}
+}  // namespace igm
+
 namespace {
 
 std::mutex g_batches_mu;
@@ -94,7 +108,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   std::vector<int> mptr;
   std::vector<Tile> mseg;
   std::vector<int> sys_seg;
-  mgs_plan(sysn, persistent_grid(1 << 30), mgs_g, mptr, mseg, mgs_wrows, sys_seg);
+  mgs_plan(sysn, persistent_grid(1 << 30), hs[0]->prm.mgs_wmax, mgs_g, mptr, mseg, mgs_wrows,
+           sys_seg);
   const int MS = (int)mseg.size();
   int *d_mptr, *d_sysseg;
   Tile *d_mseg;
@@ -364,6 +379,9 @@ igm_status check_params(const igm_params *p) {
   if (p->s < 0 || p->s > IGM_MAX_S) return fail(IGM_EINVAL, "s must be 0 ... %d", IGM_MAX_S);
   if (p->order != 0 && p->order != 1) return fail(IGM_EINVAL, "order must be 0 or 1");
   if (p->shift_tune < 0 || p->shift_tune > 64) return fail(IGM_EINVAL, "shift_tune must be 0 ... 64");
+  if (p->mgs_wmax < -1) return fail(IGM_EINVAL, "mgs_wmax must be -1, 0 or positive");
+  if (p->wait_us < 0) return fail(IGM_EINVAL, "wait_us must be >= 0");
+  if (p->test_stall != 0 && p->test_stall != 1) return fail(IGM_EINVAL, "test_stall must be 0 or 1");
   if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
         p->trsv_cluster == 4 || p->trsv_cluster == 8))
     return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
@@ -784,7 +802,8 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
                   params->beta7,  params->beta8,   params->beta10,   params->beta11a,
                   params->beta11b, params->beta13, params->beta15,   params->beta16a,
                   params->beta16b, params->inner,  params->max_refine, params->tol,
-                  params->shift_tune};
+                  params->shift_tune, params->test_stall,
+                  params->wait_us > 0 ? 1000ull * (u64)params->wait_us : 1000000000ull};
   {
     const int b0[5] = {params->beta7, params->beta8, params->beta10, params->beta13,
                        params->beta15};

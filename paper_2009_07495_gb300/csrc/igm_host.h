@@ -21,7 +21,9 @@
 
 #define CKL()                                                                     \
   do {                                                                            \
-    cudaError_t e_ = cudaGetLastError();                                          \
+    cudaError_t e_ = igm::take_launch_error();                                    \
+    cudaError_t l_ = cudaGetLastError();                                          \
+    if (e_ == cudaSuccess) e_ = l_;                                               \
     if (e_ != cudaSuccess) return fail(IGM_ECUDA, "launch: %s", cudaGetErrorString(e_)); \
   } while (0)
 

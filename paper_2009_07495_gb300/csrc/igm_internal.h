@@ -33,6 +33,8 @@ struct SysParams {
   int inner, max_refine;
   double tol;
   int tune;               // inner solves the shift auto-tuning may discard
+  int stall;              // tests: the first substitution chunk never signals
+  u64 wait_ns;            // bound of each substitution wait (ns)
 };
 
 // error bits of SysScal::err

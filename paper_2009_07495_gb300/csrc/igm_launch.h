@@ -8,6 +8,13 @@
 
 namespace igm {
 
+// a launch whose own return value reports an error (cooperative or extended
+// launches) records it here; the host driver checks it with the launch error
+void note_launch(cudaError_t e);
+// the first recorded launch error of this thread since the last call (and
+// clears it), else cudaSuccess
+cudaError_t take_launch_error();
+
 // set-up (one system)
 void launch_validate(int n, int nnz, const int *rowptr, const int *col, int *diagpos,
                      unsigned *err, cudaStream_t st);
@@ -65,7 +72,7 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 int persistent_grid(int ntiles);  // CTAs of the persistent kernels
 // the row partition of the integer Arnoldi step over systems of sizes n
-void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> &ptr,
+void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::vector<int> &ptr,
               std::vector<Tile> &seg, int &wrows, std::vector<int> &sys_seg);
 void launch_backsub(const BatchDev &B, cudaStream_t st);
 void launch_update(const BatchDev &B, cudaStream_t st);

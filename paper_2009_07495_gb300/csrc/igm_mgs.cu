@@ -521,9 +521,18 @@ int persistent_grid(int ntiles) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    // co-resident CTAs with the most dynamic shared memory a plan may give
+    // the integer step (every row of w in shared memory)
+    cudaFuncSetAttribute(k_mgs_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IGM_MGS_WMAX * (int)sizeof(i64));
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step<false>, IGM_MGS_BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step<false>, IGM_MGS_BLOCK,
+                                                      IGM_MGS_WMAX * sizeof(i64)) != cudaSuccess)
+      a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0) !=
+        cudaSuccess)
+      b = 1;
+    cudaGetLastError();
     g_mgs_blocks_per_sm = a < b ? a : b;
     if (g_mgs_blocks_per_sm < 1) g_mgs_blocks_per_sm = 1;
   }
@@ -536,12 +545,16 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   int G = persistent_grid(B.nstiles);
   BatchDev b = B;
   void *args[] = {&b, &j};
-  cudaLaunchCooperativeKernel((const void *)f_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK), args, 0, st);
+  note_launch(cudaLaunchCooperativeKernel((const void *)f_mgs_step, dim3(G), dim3(IGM_MGS_BLOCK),
+                                          args, 0, st));
   f_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j, G);
 }
 
-void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> &ptr,
+void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::vector<int> &ptr,
               std::vector<Tile> &seg, int &wrows, std::vector<int> &sys_seg) {
+  // rows of w a CTA may keep in shared memory: 0 automatic, -1 none, k > 0
+  // at most k (never above what the kernel reserves)
+  const int cap = wmax == 0 ? IGM_MGS_WMAX : wmax < 0 ? 0 : std::min(wmax, IGM_MGS_WMAX);
   long long N = 0;
   for (int v : n) N += v;
   long long g = (N + IGM_MGS_BLOCK - 1) / IGM_MGS_BLOCK;
@@ -565,7 +578,7 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int &G, std::vector<int> 
     maxrows = std::max(maxrows, off);
   }
   ptr[G] = (int)seg.size();
-  wrows = maxrows <= IGM_MGS_WMAX ? maxrows : 0;
+  wrows = maxrows <= cap ? maxrows : 0;
   // segments run in system order: system s owns [sys_seg[s], sys_seg[s+1])
   sys_seg.assign(n.size() + 1, (int)seg.size());
   for (int g = (int)seg.size() - 1; g >= 0; --g) sys_seg[seg[g].sys] = g;
@@ -586,8 +599,9 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};
-  cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G), dim3(IGM_MGS_BLOCK), args,
-                              (size_t)B.mgs_wrows * sizeof(i64), st);
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G),
+                                          dim3(IGM_MGS_BLOCK), args,
+                                          (size_t)B.mgs_wrows * sizeof(i64), st));
 }
 
 }  // namespace igm

@@ -59,6 +59,10 @@ extern "C" igm_status igm_norm2_noalloc(const double *x, int n, double *out, voi
     }
     if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
       return fail(IGM_EINVAL, "x and out must be device (or managed) memory");
+    // memory of another GPU would be dereferenced from this one: refused
+    if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+      return fail(IGM_EINVAL, "x and out must be on the current device (%d), not device %d",
+                  dev, pa.device);
   }
   // once per device, with that device current: the array's device address
   // (in host code the symbol is only a host-side stand-in)

@@ -134,7 +134,12 @@ __device__ void norm_action(const BatchDev &B, const SysDev *s, SysScal *sc, int
       // stalled: no decrease over the last three refinements
       const bool stall = k >= 3 && rho >= sc->rho_ring[(k - 3) & 3];
       sc->rho_ring[k & 3] = rho;
-      if (rho < P.tol) {
+      if (*(volatile unsigned *)&sc->err) {
+        // a device error (an expired wait) ends this system's loop; the host
+        // reports the error bits
+        sc->active = 0;
+        sc->cyc = 0;
+      } else if (rho < P.tol) {
         sc->active = 0;
         sc->cyc = 0;
         sc->status = 0;

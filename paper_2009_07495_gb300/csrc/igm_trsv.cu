@@ -299,12 +299,11 @@ __device__ __forceinline__ u64 gtimer() {
   return t;
 }
 
-// The three waits of a substitution CTA are bounded in time, nested so that
-// a wait never expires while the wait it depends on can still succeed: the
-// waiter gives up after IGM_WAIT_NS, the compute warps (who wait on the
-// waiter) after twice that, the publisher (who waits on them) after four
-// times.  An iteration cap backs up each bound.
-#define IGM_WAIT_NS 1000000000ull
+// The waits of a substitution CTA are bounded in time (the system's
+// p.wait_ns, 1 s unless set), nested so that a wait never expires while the
+// wait it depends on can still succeed: the waiter gives up after the bound,
+// the publisher (who waits on the compute warps, who wait on the waiter)
+// after four times.  An iteration cap backs up each bound.
 #define IGM_WAIT_ITERS (1 << 28)
 
 // spin until the shared counter *p reaches at least v; false if the bound
@@ -395,6 +394,9 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
     out = reinterpret_cast<V *>(lower ? s->t : reinterpret_cast<double *>(s->w));
   }
   const u64 ep = (u64)(unsigned)sc->seq << 32;
+  const u64 wns = s->p.wait_ns;
+  // tests of the bounded waits: the system's first chunk never signals
+  const bool mute = s->p.stall != 0 && c == 0;
   const int g0 = T.levb[c], nlev = T.levb[c + 1] - g0;
   const bool single = s->single_pred != 0;
   const bool lev_smem = nlev <= smem_lev;
@@ -438,7 +440,7 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
             v = ld_acquire_cluster_local(s_pred_p);
             if (v >= (unsigned)nd) break;
             if ((it & 255) == 255 &&
-                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > IGM_WAIT_NS))
+                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > wns))
               break;
           }
         }
@@ -458,7 +460,7 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
             v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
             if (v >= want) break;
             if ((it & 255) == 255 &&
-                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > IGM_WAIT_NS))
+                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > wns))
               break;
           }
         }
@@ -478,8 +480,9 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
     if (lane == 0) {
       for (unsigned pub = 0; pub < (unsigned)nlev;) {
         // levels every compute warp has finished
-        if (!wait_cta(&s_done, (pub + 1) * IGM_TRSV_CW, err, 4 * IGM_WAIT_NS)) break;
+        if (!wait_cta(&s_done, (pub + 1) * IGM_TRSV_CW, err, 4 * wns)) break;
         pub = ld_acquire_cta(&s_done) / IGM_TRSV_CW;
+        if (mute) continue;
         if (succ_cl) st_release_cluster_remote(s_pred_p, rank + 1, pub);
         else st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
       }
@@ -849,7 +852,8 @@ static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cu
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = cl > 1 ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND, KC>, B, lower, which, rows, lev, rmax, pf, kr, cl);
+  note_launch(cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND, KC>, B, lower, which, rows, lev, rmax, pf,
+                                 kr, cl));
 }
 
 void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaStream_t st) {

@@ -29,7 +29,7 @@ def _noalloc(L, x_dev, out_dev, n=None):
     return st
 
 
-@pytest.mark.parametrize("n", [0, 1, 4096, 4097, 1_000_003])
+@pytest.mark.parametrize("n", [0, 1, 4096, 4097, 1_000_003, 8_388_608])
 def test_noalloc_matches_allocating_entry_point(lib, n):
     """Two calls in a row equal igm_norm2 bit for bit (the tolerance of the
     norm's tests: it is an exact, order-independent definition)."""
@@ -56,3 +56,20 @@ def test_noalloc_rejects_too_large_n(lib):
     xh = np.zeros(4)
     st = L.load().igm_norm2_noalloc(xh.ctypes.data, 4, out.data_ptr(), 0)
     assert st == 1
+
+
+def test_noalloc_grid_sizes_in_sequence(lib):
+    """Calls on one stream whose grids shrink and grow (n = 1,000,003, 4097,
+    8,388,608 -- every partial-sum slot -- then 1): each call clears its own
+    counters, so partial sums an earlier, larger call left behind never
+    reach a later result; each equals igm_norm2 bit for bit."""
+    import torch
+    L = lib
+    rng = np.random.default_rng(11)
+    for n in (1_000_003, 4097, 8_388_608, 1):
+        x = rng.standard_normal(n) * (10.0 ** rng.integers(-3, 3))
+        xd = torch.from_numpy(x).cuda()
+        out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        assert _noalloc(L, xd, out) == 0, L.load().igm_last_error()
+        torch.cuda.synchronize()
+        assert out.item() == L.norm2(xd), (n, out.item())
