@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--shift-tune", type=int, default=0,
                     help="shift auto-tuning budget (Sec. VII-D): inner solves that may "
                          "be discarded and rerun with raised shifts")
+    ap.add_argument("--trsv-chunk", type=int, default=0,
+                    help="rows per chunk of the substitutions (0: automatic)")
     ap.add_argument("--shifts", type=int, default=None,
                     help="start the shifts of lines 7, 8, 10, 13, 15 at this value "
                          "(default: Table 4 / Table 5)")
@@ -299,6 +301,7 @@ def run_ours(args, wl):
     P.s = args.terms
     P.order = args.order
     P.shift_tune = args.shift_tune
+    P.trsv_chunk = args.trsv_chunk
     if args.shifts is not None:
         for k in ("beta7", "beta8", "beta10", "beta13", "beta15"):
             setattr(P, k, args.shifts)

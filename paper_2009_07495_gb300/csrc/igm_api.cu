@@ -62,7 +62,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   std::vector<SysDev *> sp(ns);
   b->m = hs[0]->prm.m;
   b->inner = hs[0]->prm.inner;
-  int maxlev = 1, maxw = 1, maxk = 0, max_colors = 0;
+  int maxk = 0, max_colors = 0;
   for (int s = 0; s < ns; ++s) {
     igm_handle h = hs[s];
     if (h->prm.m != b->m || h->prm.inner != b->inner) {
@@ -83,13 +83,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
       for (int c = 0; c < h->hs.tri[0].nchunk; ++c) ctiles.push_back(Tile{s, c, 0, cfirst});
     max_colors = std::max(max_colors, h->hs.ncolors);
     b->max_chunk = std::max(b->max_chunk, h->hs.chunk);
-    if (h->prm.precond) {
-      for (int tr = 0; tr < 2; ++tr) {
-        maxlev = std::max(maxlev, h->hs.tri[tr].maxlev);
-        maxw = std::max(maxw, h->hs.tri[tr].maxw);
-        maxk = std::max(maxk, h->hs.tri[tr].K);
-      }
-    }
+    if (h->prm.precond && h->hs.ncolors == 0)
+      for (int tr = 0; tr < 2; ++tr) maxk = std::max(maxk, h->hs.tri[tr].K);
   }
   int CT = (int)ctiles.size(), ST = (int)stiles.size();
   Tile *d_ctiles = nullptr, *d_stiles = nullptr;
@@ -173,10 +168,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.mpart = d_mpart;
   B.sys_seg = d_sysseg;
   B.mgs_wrows = mgs_wrows;
-  B.trsv_maxlev = maxlev;
-  B.trsv_maxw = maxw;
   B.trsv_maxk = maxk;
-  B.trsv_cluster = hs[0]->prm.trsv_cluster;
   B.max_colors = max_colors;
   B.max_ns = 0;
   for (auto hh : hs) B.max_ns = std::max(B.max_ns, hh->hs.ns);
@@ -193,12 +185,12 @@ namespace {
 void enqueue_inner(Batch *b, cudaStream_t st) {
   const BatchDev &B = b->bd;
   if (b->inner == 1) {
-    launch_fp64_inner(B, b->m, b->any_ilu, b->max_chunk, st);
+    launch_fp64_inner(B, b->m, b->any_ilu, st);
     return;
   }
   if (b->any_ilu) {  // line 1'
-    launch_trsv_lv(B, 1, 1, 0, b->max_chunk, st);
-    launch_trsv_lv(B, 1, 0, 0, b->max_chunk, st);
+    launch_trsv_lv(B, 1, 1, 0, st);
+    launch_trsv_lv(B, 1, 0, 0, st);
   }
   launch_max(B, VEC_R, 2, st);
   launch_norm(B, VEC_R, ACT_NU, 2, st);
@@ -206,8 +198,8 @@ void enqueue_inner(Batch *b, cudaStream_t st) {
   for (int j = 0; j < b->m; ++j) {
     launch_spmv(B, j, st);
     if (b->any_ilu) {  // line 5'
-      launch_trsv_lv(B, 0, 1, 1, b->max_chunk, st);
-      launch_trsv_lv(B, 0, 0, 1, b->max_chunk, st);
+      launch_trsv_lv(B, 0, 1, 1, st);
+      launch_trsv_lv(B, 0, 0, 1, st);
     }
     launch_mgs_step(B, j, st);
   }
@@ -312,11 +304,11 @@ static void permute_host(int n, const int *rp, const int *cl, const double *v,
 
 // Rows per substitution chunk.  At least the bandwidth of the triangular
 // factors, so that every chunk depends on its predecessor only, and a
-// multiple of the matrix's row period P (for a natural-order stencil the grid
-// plane, N^2 in 3D), so that chunks start on plane boundaries: then a chunk's
-// first rows need only early levels of the previous chunk and consecutive
-// chunks pipeline; at least 1024 rows; with a bandwidth too large for that
-// (fewer than 8 chunks), about one chunk per SM.
+// multiple (two or more) of the matrix's row period P (for a natural-order
+// stencil the grid plane, N^2 in 3D), so that chunks start on plane
+// boundaries: then a chunk's first rows need only early levels of the
+// previous chunk and consecutive chunks pipeline; at least 1024 rows; with a
+// bandwidth too large for that (fewer than 8 chunks), about one chunk per SM.
 // The row period of a banded matrix: among 64 rows spread over the middle
 // half, the one with the most dependencies farther than half the lower
 // bandwidth gives the median of those far offsets (N^2 for 7- and 27-point 3D
@@ -350,7 +342,10 @@ int auto_chunk(int n, int bw, int P) {
   long long r;
   if (P < 1 || P > bw) P = bw;
   if (bw >= 1 && (long long)bw * 8 <= n) {
-    r = P;
+    // two periods (planes) per chunk at least: fewer chunk hand-offs on the
+    // critical path, groups still narrow (measured best on 7- and 27-point
+    // grids of 128^3 and 200^3)
+    r = 2 * P;
     while (r < bw || r < 1024) r += P;
   } else {
     r = ((long long)n + sms - 1) / sms;
@@ -675,6 +670,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     return e;
   }
   int R = 0, nch = 0, single = 0;
+  i64 *xbuf = nullptr;
   if (ilu) {
     // a stored diagonal is required by ILU(0)
     std::vector<int> hdp(n);
@@ -693,46 +689,53 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     const int bw = std::max(hbw[0], hbw[1]);
     R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n, bw, row_period(n, rp, cl, hbw[0]));
     nch = (n + R - 1) / R;
-    single = R >= bw ? 1 : 0;
-    // the schedules and level-packed rows of L (t = 0) and U (t = 1)
+    // single: every chunk of both factors reads only itself and its
+    // predecessor (exact check over all dependencies)
+    {
+      int hcd[2] = {0, 0};
+      CKH(cudaMemsetAsync(bwd, 0, 2 * sizeof(int), s));
+      launch_chunkdist(n, rp, cl, dp, 1, R, bwd, s);
+      launch_chunkdist(n, rp, cl, dp, 0, R, bwd + 1, s);
+      CKH(cudaMemcpyAsync(hcd, bwd, sizeof(hcd), cudaMemcpyDeviceToHost, s));
+      CKH(cudaStreamSynchronize(s));
+      single = std::max(hcd[0], hcd[1]) <= 1 ? 1 : 0;
+    }
+    // the predecessor copies read up to one position past the last (their
+    // 16-byte rounding)
+    const int npad = (n + 4 + 3) & ~3;
+    // the schedules of L (t = 0) and U (t = 1)
     const int fp = params->inner == 1;
     Arena &A2 = h->arena2;
-    int *ord[2], *lptr[2], *levb[2], *lev[2], *need[2], *pcol[2], *chmax, *cnt;
-    i64 *pfac[2], *pdiag[2];
-    u64 *pdm[2];
-    double *pfacd[2] = {nullptr, nullptr}, *pdiagd[2] = {nullptr, nullptr};
+    int *ord[2], *lptr[2], *levb[2], *lev[2], *need[2], *posof[2], *chmax, *cnt;
     u64 *prog[2];
     for (int tr = 0; tr < 2; ++tr) {
-      const size_t K = std::max(1, hbw[2 + tr]);
       A2.want(&ord[tr], n);
       A2.want(&lptr[tr], n + 1);
       A2.want(&levb[tr], nch + 1);
       A2.want(&lev[tr], n);
       A2.want(&need[tr], n + 1);
-      A2.want(&pcol[tr], K * n);
-      A2.want(&pfac[tr], K * n);
-      A2.want(&pdiag[tr], n);
-      A2.want(&pdm[tr], n);
+      A2.want(&posof[tr], n);
       A2.want(&prog[tr], (size_t)nch * IGM_PROG_STRIDE);
-      if (fp) {
-        A2.want(&pfacd[tr], K * n);
-        A2.want(&pdiagd[tr], n);
-      }
     }
-    A2.want(&chmax, nch);
+    A2.want(&chmax, std::max(nch, 4));  // also two 64-bit maxima
     A2.want(&cnt, n + 1);
+    A2.want(&xbuf, npad);
     if (A2.commit() != cudaSuccess) {
       cudaGetLastError();
       size_t need2 = A2.total();
       int_gmres_destroy(h);
       return fail(IGM_EOOM, "device allocation of %zu bytes failed", need2);
     }
-    // chunk-local levels and (chunk, level) orders of the two factors
+    // chunk-local levels and (chunk, level) orders of the two factors, with
+    // levels wider than the kernel's slots split into several groups
     unsigned *tick = (unsigned *)(h->d_err + 1);
     int *flg[2] = {lfl, ufl};
-    std::vector<int> hmax(nch), hlevb(nch + 1);
+    std::vector<int> hmax(nch), hlevb(nch + 1), hlevb2(nch + 1), hl, nl, nb;
+    std::vector<int> gw[2];  // the width of every group of each factor
+    int pring_ok[2] = {1, 1};
     for (int tr = 0; tr < 2; ++tr) {
       const int lower = tr == 0;
+      const int K = hbw[2 + tr];
       CKH(cudaMemsetAsync(flg[tr], 0, sizeof(int) * n, s));
       CKH(cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
       CKH(cudaMemsetAsync(chmax, 0, sizeof(int) * nch, s));
@@ -746,32 +749,103 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
                           cudaMemcpyHostToDevice, s));
       CKH(cudaMemsetAsync(cnt, 0, sizeof(int) * (L + 1), s));
       launch_level_order(n, lower, R, L, lev[tr], levb[tr], cnt, lptr[tr], ord[tr], s);
-      int hmaxw = 0;
-      CKH(cudaMemsetAsync(chmax, 0, sizeof(int), s));
-      launch_maxw(L, lptr[tr], chmax, s);
-      CKH(cudaMemcpyAsync(&hmaxw, chmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+      // split the levels wider than the cap into consecutive groups
+      hl.resize(L + 1);
+      CKH(cudaMemcpyAsync(hl.data(), lptr[tr], sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, s));
       CKH(cudaStreamSynchronize(s));
-      CKH(cudaMemsetAsync(need[tr], 0, sizeof(int) * (L + 1), s));
+      const int cap = trsv_group_cap(K);
+      nb.assign(L, 0);
+      nl.clear();
+      int maxw = 1, maxlev = 1;
+      for (int c = 0; c < nch; ++c) {
+        hlevb2[c] = (int)nl.size();
+        for (int g = hlevb[c]; g < hlevb[c + 1]; ++g) {
+          nb[g] = (int)nl.size();
+          const int w = hl[g + 1] - hl[g];
+          for (int t0 = 0; t0 < w; t0 += cap) {
+            nl.push_back(hl[g] + t0);
+            maxw = std::max(maxw, std::min(cap, w - t0));
+          }
+        }
+        maxlev = std::max(maxlev, (int)nl.size() - hlevb2[c]);
+      }
+      hlevb2[nch] = (int)nl.size();
+      nl.push_back(n);
+      const int L2 = hlevb2[nch];
+      gw[tr].resize(L2);
+      for (int g = 0; g < L2; ++g) gw[tr][g] = nl[g + 1] - nl[g];
+      CKH(cudaMemcpyAsync(cnt, nb.data(), sizeof(int) * L, cudaMemcpyHostToDevice, s));
+      CKH(cudaMemcpyAsync(need[tr], hlevb2.data(), sizeof(int) * (nch + 1), cudaMemcpyHostToDevice,
+                          s));
+      launch_regroup(n, R, ord[tr], lev[tr], levb[tr], lptr[tr], cnt, need[tr], cap, posof[tr], s);
+      CKH(cudaMemcpyAsync(lptr[tr], nl.data(), sizeof(int) * (L2 + 1), cudaMemcpyHostToDevice, s));
+      CKH(cudaMemcpyAsync(levb[tr], hlevb2.data(), sizeof(int) * (nch + 1), cudaMemcpyHostToDevice,
+                          s));
+      CKH(cudaMemsetAsync(need[tr], 0, sizeof(int) * (L2 + 1), s));
       launch_need(n, rp, cl, dp, lower, R, ord[tr], levb[tr], lev[tr], need[tr], s);
+      // the value ring: the farthest same-chunk dependency; the predecessor
+      // ring: the span between the copies' front and the oldest value read
+      int hd[2] = {0, 0};
+      CKH(cudaMemsetAsync(bwd + 2, 0, 2 * sizeof(int), s));
+      launch_ringdist(n, rp, cl, dp, lower, R, ord[tr], posof[tr], lev[tr], levb[tr], lptr[tr],
+                      bwd + 2, s);
+      std::vector<int> hneed(L2 + 1);
+      CKH(cudaMemcpyAsync(hneed.data(), need[tr], sizeof(int) * (L2 + 1), cudaMemcpyDeviceToHost,
+                          s));
+      CKH(cudaStreamSynchronize(s));
+      for (int c = 0; c < nch; ++c)
+        for (int g = hlevb2[c] + 1; g < hlevb2[c + 1]; ++g) hneed[g] = std::max(hneed[g], hneed[g - 1]);
+      CKH(cudaMemcpyAsync(cnt, hneed.data(), sizeof(int) * L2, cudaMemcpyHostToDevice, s));
+      if (single)
+        launch_pringdist(n, rp, cl, dp, lower, R, ord[tr], posof[tr], lev[tr], levb[tr], lptr[tr],
+                         cnt, bwd + 3, s);
+      CKH(cudaMemcpyAsync(hd, bwd + 2, sizeof(hd), cudaMemcpyDeviceToHost, s));
       CKH(cudaMemsetAsync(prog[tr], 0, sizeof(u64) * nch * IGM_PROG_STRIDE, s));
       CKH(cudaStreamSynchronize(s));
+      auto pow2 = [](int v) {
+        int r = 2;
+        while (r < v && r < IGM_TRSV_RING_MAX) r <<= 1;
+        return r;
+      };
+      // farther dependencies are read late (same chunk) or late after the
+      // waiter's wait (previous chunk, when its ring would be too large)
+      pring_ok[tr] = hd[1] <= IGM_TRSV_RING_MAX;
       Tri &T = d.tri[tr];
       T.ord = ord[tr];
       T.lptr = lptr[tr];
       T.levb = levb[tr];
       T.lev = lev[tr];
       T.need = need[tr];
-      T.pcol = pcol[tr];
-      T.pfac = pfac[tr];
-      T.pdiag = pdiag[tr];
-      T.pdm = pdm[tr];
-      T.pfacd = pfacd[tr];
-      T.pdiagd = tr == 1 ? pdiagd[tr] : nullptr;
       T.prog = prog[tr];
       T.nchunk = nch;
-      T.K = hbw[2 + tr];
-      T.maxlev = 1 + *std::max_element(hmax.begin(), hmax.end());
-      T.maxw = hmaxw;
+      T.K = K;
+      T.maxlev = maxlev;
+      T.maxw = maxw;
+      T.ring = pow2(hd[0]);
+      T.pring = pow2(hd[1]);
+    }
+    // the groups' packed blocks, sized for 8-byte factors (int32 factors,
+    // decided after the factorisation, use less), and their offsets
+    unsigned char *blob[2], *blobd[2] = {nullptr, nullptr};
+    long long *boff[2], *boffd[2] = {nullptr, nullptr};
+    {
+      Arena &A3 = h->arena3;
+      for (int tr = 0; tr < 2; ++tr) {
+        size_t tot = 0;
+        for (int w : gw[tr]) tot += trsv_blk_bytes(trsv_wp(w), d.tri[tr].K, 8);
+        A3.want(&blob[tr], tot + 16);
+        A3.want(&boff[tr], gw[tr].size() + 1);
+        if (fp) {
+          A3.want(&blobd[tr], tot + 16);
+          A3.want(&boffd[tr], gw[tr].size() + 1);
+        }
+      }
+      if (A3.commit() != cudaSuccess) {
+        cudaGetLastError();
+        size_t need3 = A3.total();
+        int_gmres_destroy(h);
+        return fail(IGM_EOOM, "device allocation of %zu bytes failed", need3);
+      }
     }
     // eq. (ilu) on the L schedule (epoch 2), or the Gauss-Seidel factor
     // form; then the integer factors
@@ -783,9 +857,43 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
       launch_ilu0_lv(n, rp, cl, dp, d.tri[0], R, single, f, tick, 2, err, s);
     }
     launch_ilu_int(n, rp, cl, dp, f, fac, ld, ud, err, s);
-    for (int tr = 0; tr < 2; ++tr)
-      launch_pack(n, rp, cl, dp, tr == 0, d.tri[tr].K, ord[tr], fac, ld, ud, f, pcol[tr], pfac[tr],
-                  pdiag[tr], pdm[tr], pfacd[tr], tr == 1 ? pdiagd[tr] : nullptr, s);
+    // factors that fit pack as int32 (half the bytes, cheaper products)
+    {
+      unsigned long long *fmx = reinterpret_cast<unsigned long long *>(chmax);
+      unsigned long long hfm[2] = {0, 0};
+      CKH(cudaMemsetAsync(fmx, 0, 2 * sizeof(unsigned long long), s));
+      launch_facmax(n, rp, dp, 1, fac, fmx, s);
+      launch_facmax(n, rp, dp, 0, fac, fmx + 1, s);
+      CKH(cudaMemcpyAsync(hfm, fmx, sizeof(hfm), cudaMemcpyDeviceToHost, s));
+      CKH(cudaStreamSynchronize(s));
+      for (int tr = 0; tr < 2; ++tr) d.tri[tr].fac32 = hfm[tr] < (1ull << 31) ? 1 : 0;
+    }
+    std::vector<long long> hoff[2];
+    for (int tr = 0; tr < 2; ++tr) {
+      Tri &T = d.tri[tr];
+      const int ng = (int)gw[tr].size();
+      hoff[tr].assign(ng + 1, 0);
+      for (int g = 0; g < ng; ++g)
+        hoff[tr][g + 1] = hoff[tr][g] + trsv_blk_bytes(trsv_wp(gw[tr][g]), T.K, T.fac32 ? 4 : 8);
+      CKH(cudaMemcpyAsync(boff[tr], hoff[tr].data(), sizeof(long long) * (ng + 1),
+                          cudaMemcpyHostToDevice, s));
+      CKH(cudaMemsetAsync(blob[tr], 0, hoff[tr][ng] + 16, s));
+      if (fp) {
+        std::vector<long long> hd8(ng + 1, 0);
+        for (int g = 0; g < ng; ++g) hd8[g + 1] = hd8[g] + trsv_blk_bytes(trsv_wp(gw[tr][g]), T.K, 8);
+        CKH(cudaMemcpyAsync(boffd[tr], hd8.data(), sizeof(long long) * (ng + 1),
+                            cudaMemcpyHostToDevice, s));
+        CKH(cudaMemsetAsync(blobd[tr], 0, hd8[ng] + 16, s));
+        CKH(cudaStreamSynchronize(s));  // hd8 leaves scope
+      }
+      launch_pack(n, rp, cl, dp, tr == 0, T.K, R, single && pring_ok[tr], T.ring, T.pring,
+                  T.fac32, ord[tr], posof[tr], lev[tr], levb[tr], lptr[tr], boff[tr], boffd[tr],
+                  fac, ld, ud, f, blob[tr], blobd[tr], s);
+      T.blob = blob[tr];
+      T.blobd = blobd[tr];
+      T.boff = boff[tr];
+      T.boffd = boffd[tr];
+    }
     CKH(cudaGetLastError());
     CKH(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));
@@ -829,6 +937,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.ldiag = ld;
   d.udiag = ud;
   d.chunk = R;
+  d.xbuf = xbuf;
   d.single_pred = single;
   d.lflag = lfl;
   d.uflag = ufl;
@@ -882,11 +991,12 @@ void int_gmres_destroy(igm_handle h) {
   delete h->solo;
   h->arena.release();
   h->arena2.release();
+  h->arena3.release();
   delete h;
 }
 
 long long int_gmres_device_bytes(igm_handle h) {
-  return h ? (long long)(h->arena.size + h->arena2.size) : 0;
+  return h ? (long long)(h->arena.size + h->arena2.size + h->arena3.size) : 0;
 }
 
 }  // extern "C"
@@ -1168,12 +1278,12 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream) {
     float tot = 0.f;
     for (int r = 0; r < reps; ++r) {
       if (k == IGM_K_TRSV_L || k == IGM_K_TRSV_U) launch_spmv(B, m / 2, s);  // arms flags
-      if (k == IGM_K_TRSV_U) launch_trsv_lv(B, 0, 1, 1, b->max_chunk, s);
+      if (k == IGM_K_TRSV_U) launch_trsv_lv(B, 0, 1, 1, s);
       CK(cudaEventRecord(e0, s));
       switch (k) {
         case IGM_K_SPMV: launch_spmv(B, m / 2, s); break;
-        case IGM_K_TRSV_L: launch_trsv_lv(B, 0, 1, 1, b->max_chunk, s); break;
-        case IGM_K_TRSV_U: launch_trsv_lv(B, 0, 0, 1, b->max_chunk, s); break;
+        case IGM_K_TRSV_L: launch_trsv_lv(B, 0, 1, 1, s); break;
+        case IGM_K_TRSV_U: launch_trsv_lv(B, 0, 0, 1, s); break;
         case IGM_K_ARNOLDI: launch_mgs_step(B, m - 1, s); break;
         case IGM_K_RESID: launch_resid(B, 0, s); break;
       }

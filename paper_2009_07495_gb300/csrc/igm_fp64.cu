@@ -108,11 +108,11 @@ __global__ void f_resid_guess(BatchDev B) {
   }
 }
 
-void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, int max_chunk, cudaStream_t st) {
+void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, cudaStream_t st) {
   const int T = B.ntiles;
   if (any_ilu) {  // line 1' with the FP64 factors
-    launch_trsv_lv(B, 2, 1, 0, max_chunk, st);
-    launch_trsv_lv(B, 2, 0, 0, max_chunk, st);
+    launch_trsv_lv(B, 2, 1, 0, st);
+    launch_trsv_lv(B, 2, 0, 0, st);
   }
   launch_max(B, VEC_R, 2, st);
   launch_norm(B, VEC_R, ACT_NU, 2, st);
@@ -120,8 +120,8 @@ void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, int max_chunk, cud
   for (int j = 0; j < m; ++j) {
     f_spmv<<<T, IGM_BLOCK, 0, st>>>(B, j);
     if (any_ilu) {  // line 5' with the FP64 factors
-      launch_trsv_lv(B, 2, 1, 1, max_chunk, st);
-      launch_trsv_lv(B, 2, 0, 1, max_chunk, st);
+      launch_trsv_lv(B, 2, 1, 1, st);
+      launch_trsv_lv(B, 2, 0, 1, st);
     }
     launch_fp64_mgs_step(B, j, st);
   }

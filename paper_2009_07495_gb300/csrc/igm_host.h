@@ -67,6 +67,7 @@ struct igm_handle_s {
   int n = 0, nnz = 0;
   igm_params prm{};
   Arena arena, arena2;   // system data; substitution schedules
+  Arena arena3;          // the substitutions' packed group blocks
   SysDev hs{};           // host copy of the descriptor (device pointers)
   SysDev *d_sys = nullptr;
   SysScal *d_sc = nullptr;

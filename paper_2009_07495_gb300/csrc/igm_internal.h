@@ -64,30 +64,96 @@ struct SysScal {
   int beta[5];             // their shifts in use (a copy of SysDev::p)
 };
 
-// Schedule and level-packed data of one triangular factor.  Positions
-// p = 0..n-1 run in dependency order (L: row p, U: row n-1-p), are cut into
-// chunks of `chunk` positions, and inside each chunk grouped by local level
-// (dependency depth counted inside the chunk).  ord[p] is the row at
-// position p; group g = (chunk, level) covers positions lptr[g]..lptr[g+1];
-// levb[c] is the first group of chunk c.  The strict part of the row at
-// position p is packed dependency-major: pcol[q*n + p], pfac[q*n + p]
-// (q < K, col -1 past the row's end), with its diagonal pdiag[p]; pfacd,
-// pdiagd: the same from the FP64 factors (FP64 comparison solver only).
-// need[g]: progress the previous chunk must reach before group g runs.
-// progress words one 128-byte line apart (pollers of different chunks do not
-// share a line)
+// Schedule and packed data of one triangular factor.  Positions p = 0..n-1
+// run in dependency order (L: row p, U: row n-1-p), are cut into chunks of
+// `chunk` positions, and inside each chunk grouped by local level
+// (dependency depth counted inside the chunk), a level wider than the
+// factor's group cap being split into several consecutive groups.  ord[p]
+// is the row at position p; group g = (chunk, local group index) covers
+// positions lptr[g]..lptr[g+1]; levb[c] is the first group of chunk c and
+// lev[i] the local group index of row i.  Each group's rows are packed into
+// one block (layout below): the strict part of every row farthest
+// dependency first (L: columns ascending, U: columns descending), each
+// dependency as a factor entry and a source code.  need[g]: progress the
+// previous chunk must reach before group g runs.  Progress words one
+// 128-byte line apart (pollers of different chunks do not share a line).
 #define IGM_PROG_STRIDE 16
 
+// Source code of a dependency: the values a chunk reads sit in one
+// shared-memory array, [the chunk's own ring of `ring` values | the
+// predecessor ring of `pring` values | one zero], so a code >= 0 is the
+// value's index there (own values at their chunk-local position mod ring,
+// the previous chunk's at their position mod pring, padding at the zero); a
+// code -1 - p reads the value at position p from the position-ordered copy
+// of the results when the row is computed (after waiting for p's chunk when
+// chunks may depend on chunks before their predecessor).
+// slots of the substitution kernel: each holds one group's packed block
+// (bulk-copied) and its right-hand sides (gathered); as many as fit, up to
+// IGM_TRSV_NA_MAX and at least IGM_TRSV_NA_MIN
+#define IGM_TRSV_NA_MAX 8
+#define IGM_TRSV_NA_MIN 4
+#define IGM_TRSV_NB 3              // predecessor-copy barriers (one per group, round robin)
+#define IGM_TRSV_PFB 2             // groups ahead of a group the predecessor copy is issued
+#define IGM_TRSV_RING_MAX 4096
+// dynamic shared memory the substitution kernel uses per CTA
+#define IGM_TRSV_SMEM (224 * 1024)
+
+// Packed block of one group of w rows (wp = w rounded up to a multiple of
+// 4), everything a row needs but its right-hand side and dependency values,
+// each array 16-byte aligned: codes [K][wp] int32, orders [wp] int32, bounds
+// [wp] int32, factors [K][wp] (fb bytes), diagonals [wp] (8 bytes),
+// division multipliers [wp] u64.
+__host__ __device__ inline unsigned trsv_wp(int w) { return ((unsigned)(w < 1 ? 1 : w) + 3u) & ~3u; }
+__host__ __device__ inline unsigned trsv_blk_bytes(unsigned wp, int K, int fb) {
+  const unsigned k = (unsigned)(K < 0 ? 0 : K);
+  return wp * (4u * k + 8u + (unsigned)fb * k + 16u);
+}
+
 struct Tri {
-  const int *ord, *lptr, *levb, *lev, *need, *pcol;
-  const i64 *pfac, *pdiag;
-  const u64 *pdm;               // magic multipliers of |pdiag| (exact divisions)
-  const double *pfacd, *pdiagd;
-  u64 *prog;                    // per chunk (IGM_PROG_STRIDE apart): (epoch << 32) | levels done
+  const int *ord, *lptr, *levb, *lev, *need;
+  // the groups' packed blocks (integer factors, int32 when fac32; FP64
+  // factors for the comparison solver in blobd) and each group's byte offset
+  const unsigned char *blob, *blobd;
+  const long long *boff, *boffd;
+  u64 *prog;                    // per chunk (IGM_PROG_STRIDE apart): (epoch << 32) | groups done
   int nchunk, K;
-  int maxlev;                   // most local levels of one chunk
-  int maxw;                     // most rows of one level group
+  int maxlev;                   // most groups of one chunk
+  int maxw;                     // most rows of one group
+  int ring;                     // slots of the chunk's value ring (power of two)
+  int pring;                    // slots of the predecessor ring (power of two)
+  int fac32;                    // every strict factor entry fits in int32
 };
+
+// Shared-memory carve-up of one substitution CTA for a factor with groups of
+// at most W rows, K dependencies per row, rings of `ring` and `pring` values,
+// `nlev` staged groups and factor entries of fb bytes (byte offsets; the same
+// on the host and in the kernel): [values: own ring | predecessor ring |
+// zero] [na slots: block | right-hand sides] [group pointers].
+struct TrsvLayout {
+  unsigned szBlk;               // bytes of the largest block
+  unsigned szSlot;              // bytes of a slot (block + W right-hand sides)
+  unsigned oSlots, na, oLev, lev, total;
+};
+
+__host__ __device__ inline unsigned trsv_r128(unsigned b) { return (b + 127u) & ~127u; }
+
+// na: slots to use (0: as many as fit in IGM_TRSV_SMEM, at least IGM_TRSV_NA_MIN)
+__host__ __device__ inline TrsvLayout trsv_layout(int W, int K, int ring, int pring, int nlev,
+                                                  int fb, int na = 0) {
+  TrsvLayout t;
+  t.szBlk = trsv_blk_bytes(trsv_wp(W), K, fb);
+  t.szSlot = trsv_r128(t.szBlk + (unsigned)(W < 1 ? 1 : W) * 8u);
+  t.oSlots = trsv_r128(((unsigned)ring + (unsigned)pring + 2u) * 8u);
+  t.na = na > 0 ? (unsigned)na : IGM_TRSV_NA_MAX;
+  while (na <= 0 && t.na > IGM_TRSV_NA_MIN && t.oSlots + t.na * t.szSlot > IGM_TRSV_SMEM) --t.na;
+  t.oLev = t.oSlots + t.na * t.szSlot;
+  // the chunk's group pointers and requirements, and the previous chunk's
+  // group pointers, if they fit
+  const unsigned lb = (3u * (unsigned)nlev + 3u) * 4u;
+  t.lev = (t.oLev + lb <= IGM_TRSV_SMEM) ? (unsigned)nlev : 0u;
+  t.total = t.oLev + (t.lev ? trsv_r128(lb) : 0u);
+  return t;
+}
 
 struct SysDev {
   int n, nnz, ld;          // ld = m + 1
@@ -123,6 +189,7 @@ struct SysDev {
   int *lflag, *uflag;           // per-row ready flags (set-up, line 1' none)
   double *b, *bh, *xt, *r, *t, *xk;
   i64 *w, *yv, *V;
+  i64 *xbuf;                    // substitution results in position order
   i64 *H, *cs, *sn, *g;
   double *yfp;
   SysScal *sc;
@@ -165,10 +232,7 @@ struct BatchDev {
                            // exact int128 sum over each segment
   const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
   int mgs_wrows;           // rows of w each CTA keeps in shared memory (0: global)
-  int trsv_maxlev;         // most local levels of a substitution chunk
-  int trsv_maxw;           // most rows of one level group
   int trsv_maxk;           // most strict entries of one factor row
-  int trsv_cluster;        // CTAs per cluster of the substitutions (0 automatic)
   int max_ns;              // most correction terms of eq. (AA) of a system
   int max_colors;          // most colours of a multicolour-ordered system
 };

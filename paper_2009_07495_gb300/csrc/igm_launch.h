@@ -30,16 +30,32 @@ void launch_level_order(int n, int lower, int R, int L, const int *level, const 
 void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos, const Tri &T,
                     int R, int single, double *f, unsigned *ticket, int epoch, unsigned *err,
                     cudaStream_t st);
+void launch_chunkdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                      int R, int *dmax, cudaStream_t st);
+void launch_regroup(int n, int R, const int *ord, int *lev, const int *levb_old,
+                    const int *lptr_old, const int *newbase, const int *levb_new, int cap,
+                    int *posof, cudaStream_t st);
+void launch_ringdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                     int R, const int *ord, const int *posof, const int *lev, const int *levb,
+                     const int *lptr, int *dmax, cudaStream_t st);
+void launch_pringdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                      int R, const int *ord, const int *posof, const int *lev, const int *levb,
+                      const int *lptr, const int *needpm, int *dmax, cudaStream_t st);
+void launch_facmax(int n, const int *rowptr, const int *diagpos, int lower, const i64 *fac,
+                   unsigned long long *mx, cudaStream_t st);
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
-                 const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
-                 double *pfacd, double *pdiagd, cudaStream_t st);
+                 int R, int single, int ring, int pring, int fac32, const int *ord,
+                 const int *posof, const int *lev, const int *levb, const int *lptr,
+                 const long long *boff, const long long *boffd, const i64 *fac, const i64 *ldiag,
+                 const i64 *udiag, const double *f, unsigned char *blob, unsigned char *blobd,
+                 cudaStream_t st);
+// the widest group a factor with K dependencies per row may have
+int trsv_group_cap(int K);
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
                  const int *ord, const int *levb, const int *lev, int *need, cudaStream_t st);
 // substitutions: kind 0 integer (line 5'), 1 FP64 on the integer factors
 // (line 1'), 2 FP64 factors (comparison solver); which 0 line 1', 1 line 5'
-void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
-                    cudaStream_t st);
+void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, cudaStream_t st);
 void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaStream_t st);
 void launch_maxw(int L, const int *lptr, int *out, cudaStream_t st);
 void launch_permute(int n, const int *perm, const double *src, double *dst, int back,
@@ -85,7 +101,7 @@ void launch_norm2_grid(const double *x, int n, int g, long long *ws, double *mx,
 void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st);
 
 // FP64 GMRES(m) comparison solver (lines 1-23 after line 1's residual)
-void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, int max_chunk, cudaStream_t st);
+void launch_fp64_inner(const BatchDev &B, int m, int any_ilu, cudaStream_t st);
 void launch_fp64_resid_guess(const BatchDev &B, cudaStream_t st);
 
 }  // namespace igm

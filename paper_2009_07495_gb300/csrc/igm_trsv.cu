@@ -1,4 +1,4 @@
-// igm_trsv.cu -- sparse triangular substitutions on chunked level schedules:
+// igm_trsv.cu -- sparse triangular substitutions on chunked group schedules:
 // line 5' of Sec. VI (integer Lbar, Ubar: y_i = (z_i - sum Lbar_ij y_j) /
 // Lbar_ii with an exact int128 numerator and truncating division), line 1'
 // (the same in FP64 on the integer factors) and the FP64 comparison solver's
@@ -6,15 +6,16 @@
 // and the FP64 ILU(0) factorisation (eq. ilu) on the same schedule.
 //
 // A CTA takes one chunk of consecutive positions (by ticket, in dependency
-// order) and walks its local levels separated by CTA barriers.  Dependencies
-// inside the chunk were computed at an earlier level by the same CTA (kept in
-// shared memory); when the chunk size is at least the factor's bandwidth,
-// every other dependency lies in the previous chunk and one thread waits,
-// once per level, for that chunk's progress word to reach the level the
-// group needs (precomputed); otherwise each row waits for its own
-// dependencies.  A chunk publishes its progress after every level.  Each
-// thread prefetches its row of the next level while computing the current.
-#include <cooperative_groups.h>
+// order) and walks its groups (local levels, split to a width cap) in order,
+// one named barrier per group.  Values of the chunk's recent groups stay in a
+// ring in shared memory; everything else a row reads (its packed factors,
+// diagonal, right-hand side, and the values of earlier chunks or of older
+// groups) is brought into shared memory ahead of time: a producer warp
+// bulk-copies each group's packed data (cp.async.bulk with mbarrier
+// completion) several groups ahead, and the compute threads gather the
+// right-hand sides and far values with cp.async two groups ahead, once a
+// waiter warp has seen the previous chunk reach the groups they need.  A
+// publisher warp releases the chunk's progress after each group.
 #include <type_traits>
 
 #include "igm_dev.cuh"
@@ -22,17 +23,14 @@
 
 namespace igm {
 
-namespace cg = cooperative_groups;
-
 #define IGM_TRSV_BLOCK 256
-// dependencies of a row held in registers (and in the prefetch ring): 4 for
-// 5/7-point stencils, 16 for up to 27-point ones; longer rows read the rest
-// from the packed arrays
+// dependencies of a row held in registers: 4 for 5/7-point stencils, 16 for
+// up to 27-point ones; longer rows read the rest from shared memory
 #define IGM_TRSV_KC_SMALL 4
 #define IGM_TRSV_KC_LARGE 16
 
 // ---------------------------------------------------------------------------
-// set-up: packed rows, predecessor requirements
+// set-up: schedules and packed rows
 // ---------------------------------------------------------------------------
 
 // max strict-part entries per row of L (lower) or U
@@ -43,26 +41,185 @@ __global__ void s_maxdeps(int n, const int *rowptr, const int *diagpos, int lowe
   atomicMax(kmax, k);
 }
 
-// packs the strict part of the row at each position, dependency-major
-__global__ void s_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
-                       int K, const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                       const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
-                       double *pfacd, double *pdiagd) {
+// the chunk of a row: chunks cut the dependency order (L: i, U: n-1-i)
+__device__ __forceinline__ int chunk_of(int i, int n, int lower, int R) {
+  return (lower ? i : n - 1 - i) / R;
+}
+
+// the largest distance, in chunks, from a row to one of its dependencies:
+// at most 1 means every chunk reads only itself and its predecessor
+__global__ void s_chunkdist(int n, const int *rowptr, const int *col, const int *diagpos,
+                            int lower, int R, int *dmax) {
+  int d = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+    const int k1 = lower ? diagpos[i] : rowptr[i + 1];
+    const int ci = chunk_of(i, n, lower, R);
+    for (int k = k0; k < k1; ++k) d = max(d, ci - chunk_of(col[k], n, lower, R));
+  }
+  atomicMax(dmax, d);
+}
+
+// Splits every level group wider than `cap` rows into consecutive groups of
+// at most cap rows (rows of one level are independent, so any split keeps
+// the dependencies); records each row's new group index local to its chunk
+// and its position.  ord is the order of the level groups (positions kept);
+// lptr_old/levb_old their bounds, newbase[g] the first new group of old
+// group g, levb_new the first new group of each chunk.
+__global__ void s_regroup(int n, int R, const int *ord, int *lev, const int *levb_old,
+                          const int *lptr_old, const int *newbase, const int *levb_new, int cap,
+                          int *posof) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    int i = ord[p];
-    int k0 = lower ? rowptr[i] : diagpos[i] + 1;
-    int k1 = lower ? diagpos[i] : rowptr[i + 1];
-    for (int q = 0; q < K; ++q) {
-      int k = k0 + q;
-      bool in = k < k1;
-      pcol[(size_t)q * n + p] = in ? col[k] : -1;
-      pfac[(size_t)q * n + p] = in ? fac[k] : 0;
-      if (pfacd) pfacd[(size_t)q * n + p] = in ? f[k] : 0.0;
+    const int i = ord[p];
+    const int c = p / R;
+    const int g = levb_old[c] + lev[i];
+    const int gn = newbase[g] + (p - lptr_old[g]) / cap;
+    lev[i] = gn - levb_new[c];
+    posof[i] = p;
+  }
+}
+
+// the largest (end of a row's group) - (position of a same-chunk dependency):
+// a ring of at least this many values holds every same-chunk dependency
+// until it is read
+__global__ void s_ringdist(int n, const int *rowptr, const int *col, const int *diagpos,
+                           int lower, int R, const int *ord, const int *posof, const int *lev,
+                           const int *levb, const int *lptr, int *dmax) {
+  int d = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = ord[p];
+    const int c = p / R, first = c * R;
+    const int b = lptr[levb[c] + lev[i] + 1];
+    const int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+    const int k1 = lower ? diagpos[i] : rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int pj = posof[col[k]];
+      if (pj >= first) d = max(d, b - pj);
     }
-    pdiag[p] = lower ? ldiag[i] : udiag[i];
-    const i64 dg = pdiag[p];
-    pdm[p] = dg == 0 ? 0 : magic_u64(dg < 0 ? 0ull - (u64)dg : (u64)dg);
-    if (pdiagd) pdiagd[p] = f[diagpos[i]];
+  }
+  atomicMax(dmax, d);
+}
+
+// The predecessor ring: after iteration l of chunk c (the copy that serves
+// group l + IGM_TRSV_PFB) the previous chunk's values up to position
+// front[c][l] (+1 for the even rounding of the copies) are in the ring,
+// front = lptr of the previous chunk at the largest need of groups
+// 0 .. l + PFB (needpm: that prefix maximum per group).  Copies of iteration
+// l must not overwrite values that groups l and later still read, so the
+// ring needs front + 2 - (each such value's position) slots.
+__global__ void s_pringdist(int n, const int *rowptr, const int *col, const int *diagpos,
+                            int lower, int R, const int *ord, const int *posof, const int *lev,
+                            const int *levb, const int *lptr, const int *needpm, int *dmax) {
+  int d = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = ord[p];
+    const int c = p / R, first = c * R;
+    if (c == 0) continue;
+    const int l = lev[i], nl = levb[c + 1] - levb[c];
+    const int g = min(l + IGM_TRSV_PFB, nl - 1);
+    const int front = lptr[levb[c - 1] + needpm[levb[c] + g]];
+    const int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+    const int k1 = lower ? diagpos[i] : rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int pj = posof[col[k]];
+      if (pj < first) d = max(d, front + 2 - pj);
+    }
+  }
+  atomicMax(dmax, d);
+}
+
+// the largest |entry| of the strict part of L (lower) or U: whether the
+// factor packs as int32
+__global__ void s_facmax(int n, const int *rowptr, const int *diagpos, int lower, const i64 *fac,
+                         unsigned long long *mx) {
+  u64 m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+    const int k1 = lower ? diagpos[i] : rowptr[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const i64 v = fac[k];
+      const u64 a = v < 0 ? 0ull - (u64)v : (u64)v;
+      m = a > m ? a : m;
+    }
+  }
+  atomicMax(mx, m);
+}
+
+// Packs the rows of every group into the group's block (the layout of
+// trsv_blk_bytes): each row's strict part farthest dependency first (L:
+// columns ascending, U: descending) with each dependency's code
+// (IGM_DEP_*): same-chunk values recent enough for the own ring at their
+// chunk-local position mod ring; values of the previous chunk (single = 1,
+// every dependency in this chunk or the previous one) at ring + their
+// position mod pring; padding at the zero (ring + pring); the rest as late
+// reads.  Factors as int32 when fac32.  Bound: with S = sum_q |fac_q| of the
+// row, every |y_q| <= 2^bound keeps each product and the sum below 2^62 in
+// magnitude (62 - bit length of S; -1 when no such bound exists).  blobd
+// (FP64 comparison solver, may be NULL): the same rows with FP64 factors
+// and diagonals (1 for the unit lower factor), offsets boffd.
+__global__ void s_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                       int K, int R, int single, int ring, int pring, int fac32, const int *ord,
+                       const int *posof, const int *lev, const int *levb, const int *lptr,
+                       const long long *boff, const long long *boffd, const i64 *fac,
+                       const i64 *ldiag, const i64 *udiag, const double *f, unsigned char *blob,
+                       unsigned char *blobd) {
+  const int zero = ring + pring;
+  const int fb = fac32 ? 4 : 8;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = ord[p];
+    const int c = p / R, first = c * R;
+    const int g = levb[c] + lev[i];
+    const int r = p - lptr[g], wp = (int)trsv_wp(lptr[g + 1] - lptr[g]);
+    const int b = lptr[g + 1];
+    unsigned char *base = blob + boff[g];
+    int *bcode = reinterpret_cast<int *>(base);
+    int *bord = bcode + (size_t)K * wp;
+    int *byb = bord + wp;
+    unsigned char *bfac = reinterpret_cast<unsigned char *>(byb + wp);
+    i64 *bdiag = reinterpret_cast<i64 *>(bfac + (size_t)fb * K * wp);
+    u64 *bdm = reinterpret_cast<u64 *>(bdiag + wp);
+    unsigned char *based = blobd ? blobd + boffd[g] : nullptr;
+    const int k0 = lower ? rowptr[i] : diagpos[i] + 1;
+    const int k1 = lower ? diagpos[i] : rowptr[i + 1];
+    const int cnt = k1 - k0;
+    u128 sabs = 0;
+    for (int q = 0; q < K; ++q) {
+      int code = zero;
+      i64 fv = 0;
+      double fd = 0.0;
+      if (q < cnt) {
+        const int k = lower ? k0 + q : k1 - 1 - q;
+        const int pj = posof[col[k]];
+        if (pj >= first) code = (b - pj <= ring) ? ((pj - first) & (ring - 1)) : -1 - pj;
+        else if (single) code = ring + (pj & (pring - 1));
+        else code = -1 - pj;
+        fv = fac[k];
+        if (f) fd = f[k];
+        sabs += (u128)(fv < 0 ? 0ull - (u64)fv : (u64)fv);
+      }
+      bcode[(size_t)q * wp + r] = code;
+      if (fac32) reinterpret_cast<int *>(bfac)[(size_t)q * wp + r] = (int)fv;
+      else reinterpret_cast<i64 *>(bfac)[(size_t)q * wp + r] = fv;
+      if (based) {
+        reinterpret_cast<int *>(based)[(size_t)q * wp + r] = code;
+        reinterpret_cast<double *>(based + (size_t)(4 * K + 8) * wp)[(size_t)q * wp + r] = fd;
+      }
+    }
+    int bl = 0;  // bit length of sabs
+    while (bl < 127 && (sabs >> bl) != 0) ++bl;
+    bord[r] = i;
+    byb[r] = 62 - bl < -1 ? -1 : 62 - bl;
+    const i64 dg = lower ? ldiag[i] : udiag[i];
+    bdiag[r] = dg;
+    bdm[r] = dg == 0 ? 0 : magic_u64(dg < 0 ? 0ull - (u64)dg : (u64)dg);
+    if (based) {
+      int *dord = reinterpret_cast<int *>(based) + (size_t)K * wp;
+      dord[r] = i;
+      dord[wp + r] = -1;
+      double *ddg = reinterpret_cast<double *>(based + (size_t)(4 * K + 8) * wp + (size_t)8 * K * wp);
+      ddg[r] = lower ? 1.0 : f[diagpos[i]];
+      reinterpret_cast<u64 *>(ddg + wp)[r] = 0;
+    }
   }
 }
 
@@ -104,192 +261,81 @@ struct TrsvT<TK_FP> {
   typedef double V;
 };
 
-// row data of one position, loaded ahead of its level
-template <int KIND, int KC>
-struct RowPre {
-  typedef typename TrsvT<KIND>::V V;
-  int i;
-  int col[KC];
-  V fac[KC];
-  V diag;
-  V rhs;
-  u64 dm;  // magic multiplier of |diag| (integer kind)
-};
-
-// read-only loads issued where they are written (a prefetch must not be
-// moved next to its use)
-__device__ __forceinline__ int ldnc(const int *p) {
-  int v;
-  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ long long ldnc(const long long *p) {
-  long long v;
-  asm volatile("ld.global.nc.b64 %0, [%1];" : "=l"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ unsigned long long ldnc(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.global.nc.b64 %0, [%1];" : "=l"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ double ldnc(const double *p) {
-  double v;
-  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
 
-template <int KIND, int KC>
-__device__ __forceinline__ void row_load(RowPre<KIND, KC> &r, const Tri &T, int n, int p, int row,
-                                         const typename TrsvT<KIND>::V *in) {
-  r.i = row;
-#pragma unroll
-  for (int q = 0; q < KC; ++q) {
-    if (q < T.K) {
-      r.col[q] = ldnc(T.pcol + (size_t)q * n + p);
-      if (KIND == TK_INT) r.fac[q] = ldnc(T.pfac + (size_t)q * n + p);
-      else if (KIND == TK_FPI) r.fac[q] = (double)ldnc(T.pfac + (size_t)q * n + p);
-      else r.fac[q] = ldnc(T.pfacd + (size_t)q * n + p);
-    } else {
-      r.col[q] = -1;
-      r.fac[q] = 0;
-    }
-  }
-  if (KIND == TK_INT) {
-    r.diag = ldnc(T.pdiag + p);
-    r.dm = ldnc(T.pdm + p);
-  } else if (KIND == TK_FPI) {
-    r.diag = (double)ldnc(T.pdiag + p);
-    r.dm = 0;
-  } else {
-    r.diag = T.pdiagd ? ldnc(T.pdiagd + p) : 1.0;
-    r.dm = 0;
-  }
-  r.rhs = ldnc(in + r.i);
-}
-
-// asynchronous global -> shared copies (no register scoreboard is held while
-// they are in flight; a thread waits for its own groups)
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
+// asynchronous 8-byte global -> shared copy (a thread waits for its own
+// groups of copies)
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst)),
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)),
                "l"(__cvta_generic_to_global(src))
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
-// wait until at most n of this thread's groups are pending (n <= 3)
-__device__ __forceinline__ void cp_async_wait(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-  }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// One row of a level: y_i = (rhs_i - sum_q fac_q y_(col_q)) / diag_i.  FAST
-// when every dependency outside the chunk lies in the previous chunk (already
-// waited for) and the chunk's values are in shared memory: the register-held
-// dependencies are then fetched and multiplied without branches (padding
-// entries have factor 0).  Integer numerators are exact (int128); FP64 ones
-// subtract in the packed (CSR) order.
-template <int KIND, int KC, bool FAST>
-__device__ __forceinline__ typename TrsvT<KIND>::V trsv_row(
-    const RowPre<KIND, KC> &rr, int p, const Tri &T, int n, int lower, int first, int R,
-    bool use_smem, bool single, u64 ep, const typename TrsvT<KIND>::V *sv,
-    const typename TrsvT<KIND>::V *psv, const typename TrsvT<KIND>::V *out, unsigned *err,
-    unsigned &ev) {
-  typedef typename TrsvT<KIND>::V V;
-  V yv[KC];
-#pragma unroll
-  for (int q = 0; q < KC; ++q) {
-    const int j = rr.col[q];
-    const int pj = lower ? j : n - 1 - j;
-    if (FAST) {
-      const bool ext = j >= 0 && pj < first;
-      const int si = (j >= 0 && !ext) ? pj - first : 0;
-      // the previous chunk's values: its CTA's shared memory when it is in
-      // this cluster, else global memory
-      yv[q] = ext ? (psv ? psv[pj - first + R] : (V)__ldcg(out + j)) : sv[si];
-    } else {
-      V y = 0;
-      if (j >= 0) {
-        if (pj >= first) {
-          y = use_smem ? sv[pj - first] : (V)__ldcg(out + j);
-        } else {
-          if (!single) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (pj / R), ep | (u64)(T.lev[j] + 1), err);
-          y = (V)__ldcg(out + j);
-        }
-      }
-      yv[q] = y;
-    }
-  }
-  typedef typename std::conditional<KIND == TK_INT, i128, double>::type A;
-  A acc = (A)rr.rhs;
-  if (KIND == TK_INT) {
-    i128 sum = 0;
-#pragma unroll
-    for (int q = 0; q < KC; ++q) sum += (i128)mulw((i64)rr.fac[q], (i64)yv[q], ev);
-    acc -= (A)sum;
-  } else {
-#pragma unroll
-    for (int q = 0; q < KC; ++q)
-      if (rr.col[q] >= 0) acc = __dsub_rn((double)acc, __dmul_rn((double)rr.fac[q], (double)yv[q]));
-  }
-  // rows with more dependencies than the registers hold
-  for (int q = KC; q < T.K; ++q) {
-    const int j = T.pcol[(size_t)q * n + p];
-    if (j < 0) break;
-    V a;
-    if (KIND == TK_INT) a = T.pfac[(size_t)q * n + p];
-    else if (KIND == TK_FPI) a = (double)T.pfac[(size_t)q * n + p];
-    else a = T.pfacd[(size_t)q * n + p];
-    const int pj = lower ? j : n - 1 - j;
-    V yj;
-    if (pj >= first) {
-      yj = use_smem ? sv[pj - first] : (V)__ldcg(out + j);
-    } else {
-      if (!single) wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (pj / R), ep | (u64)(T.lev[j] + 1), err);
-      yj = (V)__ldcg(out + j);
-    }
-    if (KIND == TK_INT) acc -= (A)mulw((i64)a, (i64)yj, ev);
-    else acc = __dsub_rn((double)acc, __dmul_rn((double)a, (double)yj));
-  }
-  if (KIND == TK_INT) {
-    ev += out64((i128)acc);
-    return (V)divt_magic(wrap((i128)acc), (i64)rr.diag, rr.dm, ev);
-  }
-  if (KIND == TK_FP && lower) return (V)acc;  // unit lower factor
-  return (V)__ddiv_rn((double)acc, (double)rr.diag);
+// mbarriers and bulk copies (the async proxy)
+__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// orders this thread's earlier generic-proxy accesses of global memory (here:
+// the acquire of another chunk's progress) before its later async-proxy
+// copies from global memory
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// bytes (a multiple of 16) from 16-byte aligned global memory to 16-byte
+// aligned shared memory, completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(src)),
+               "r"(bytes)
+               : "memory");
 }
 
 // CTA-scope release / acquire on shared-memory counters
 __device__ __forceinline__ void red_release_cta(unsigned *p, unsigned v) {
-  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(p)),
-               "r"(v)
-               : "memory");
-}
-__device__ __forceinline__ void st_release_cta(unsigned *p, unsigned v) {
-  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(p)),
-               "r"(v)
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
                : "memory");
 }
 __device__ __forceinline__ unsigned ld_acquire_cta(const unsigned *p) {
   unsigned v;
-  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];"
-               : "=r"(v)
-               : "r"((unsigned)__cvta_generic_to_shared(p))
-               : "memory");
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
   return v;
 }
 
@@ -302,8 +348,9 @@ __device__ __forceinline__ u64 gtimer() {
 // The waits of a substitution CTA are bounded in time (the system's
 // p.wait_ns, 1 s unless set), nested so that a wait never expires while the
 // wait it depends on can still succeed: the waiter gives up after the bound,
-// the publisher (who waits on the compute warps, who wait on the waiter)
-// after four times.  An iteration cap backs up each bound.
+// the producer and the publisher (who wait on the compute warps, who wait on
+// the waiter and on the bulk copies) after four times.  An iteration cap
+// backs up each bound.
 #define IGM_WAIT_ITERS (1 << 28)
 
 // spin until the shared counter *p reaches at least v; false if the bound
@@ -323,54 +370,89 @@ __device__ __forceinline__ bool wait_cta(const unsigned *p, unsigned v, unsigned
   return false;
 }
 
-// Roles in a substitution CTA: IGM_TRSV_CW compute warps walk the levels;
-// the waiter warp acquires the previous chunk's progress word and joins the
-// compute warps in one named barrier per level, which both lets a level start
-// once its inputs are there and makes the previous level's shared values
-// visible; the publisher warp turns the compute warps' count of finished
-// levels into this chunk's progress word with a GPU-scope release, off the
-// compute warps' path.
+// spin until the shared counter *p reaches at least v, bounded by time only
+// (for a wait whose giving up early would leave slots unfilled: the compute
+// warps it waits on always advance, since all their own waits are bounded)
+__device__ __forceinline__ bool wait_cta_own(const unsigned *p, unsigned v, unsigned *err,
+                                             u64 limit_ns) {
+  if (ld_acquire_cta(p) >= v) return true;
+  const u64 t0 = gtimer();
+  for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+    if (ld_acquire_cta(p) >= v) return true;
+    if (it > 64) __nanosleep(32);
+    if ((it & 255) == 255 && gtimer() - t0 > limit_ns) break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+// wait for the phase of parity `parity` of a bulk-copy barrier; bounded by
+// time (a copy always completes, so expiry is an error); false if expired
+__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned parity, unsigned *err,
+                                          u64 limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const u64 t0 = gtimer();
+  for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && gtimer() - t0 > limit_ns) break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
+// Roles in a substitution CTA: IGM_TRSV_CW compute warps walk the groups,
+// one named barrier per group among them (which makes the previous group's
+// ring values visible; after it thread 0 releases the count of finished
+// groups); the waiter warp acquires the previous chunk's progress and
+// bulk-copies its values into the predecessor ring ahead of the groups that
+// read them; the publisher warp turns the count of finished groups into this
+// chunk's progress word; the block warp bulk-copies each group's packed
+// block into a slot as slots free up (and prefetches later blocks into L2);
+// the gather warp waits for each block and gathers the group's right-hand
+// sides into the slot, the group's ready barrier completing when both are
+// there.
 #define IGM_TRSV_CW 8
 #define IGM_TRSV_NC (IGM_TRSV_CW * 32)
-#define IGM_TRSV_THREADS (IGM_TRSV_NC + 64)
+#define IGM_TRSV_THREADS (IGM_TRSV_NC + 128)
+// groups ahead of the L2 prefetch of the blocks, past the slots
+#define IGM_TRSV_PFL 8
 
-// cluster-scope signalling between the CTAs of a cluster
-__device__ __forceinline__ void st_release_cluster_remote(unsigned *local_ptr, int rank,
-                                                          unsigned v) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(local_ptr), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-  asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_cta(unsigned *p, unsigned v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned ld_acquire_cluster_local(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];"
-               : "=r"(v)
-               : "r"((unsigned)__cvta_generic_to_shared(p))
+__device__ __forceinline__ void mbar_arrive(u64 *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// arrives on bar once this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive_noinc(u64 *bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-  return v;
 }
 
-// One chunk (ctile t) of a substitution.  rank/cl: the CTA's place in its
-// cluster (cl = 1: no cluster).  s_done counts finished levels x warps;
-// s_pred receives the previous chunk's finished levels when that chunk runs
-// in the same cluster.
 template <int KIND, int KC>
-__device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, int cl, int lower,
-                                           int which, int smem_rows, int smem_lev, int rmax,
-                                           int pf, int kr, unsigned *s_done_p,
-                                           unsigned *s_pred_p) {
+__global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
+    k_trsv_lv(BatchDev B, int lower, int which) {
   typedef typename TrsvT<KIND>::V V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // [values: smem_rows][ring words: (pf+1) x (kr+3) x rmax][order: smem_rows]
-  // [ring columns: (pf+1) x kr x rmax][level pointers: smem_lev+1][needs: smem_lev]
-  const int S = pf + 1;
-  V *sv = reinterpret_cast<V *>(smem_raw);
-  long long *ring64 = reinterpret_cast<long long *>(sv + smem_rows);
-  int *sord = reinterpret_cast<int *>(ring64 + (pf > 0 ? (size_t)S * (kr + 3) * rmax : 0));
-  int *ring32 = sord + smem_rows;
-  int *slptr = ring32 + (pf > 0 ? (size_t)S * kr * rmax : 0);  // level pointers (smem_lev + 1)
-  int *sneed = slptr + smem_lev + 1;  // their requirements on the previous chunk
-  unsigned &s_done = *s_done_p;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_t;
+  __shared__ unsigned s_done;  // groups the compute warps have finished
+  __shared__ __align__(8) u64 s_blk[IGM_TRSV_NA_MAX];  // a slot's block has landed
+  __shared__ __align__(8) u64 s_rdy[IGM_TRSV_NA_MAX];  // ... and its right-hand sides
+  __shared__ __align__(8) u64 s_barp[IGM_TRSV_NB];     // a group's predecessor values
+  const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
+  if (threadIdx.x == 0) {
+    s_t = (int)atomicAdd(&B.ticket[tk], 1u);
+    s_done = 0;
+    for (int k = 0; k < IGM_TRSV_NA_MAX; ++k) {
+      mbar_init(&s_blk[k], 1);
+      mbar_init(&s_rdy[k], 33);  // the gather warp's 32 copy arrivals and lane 0
+    }
+    for (int k = 0; k < IGM_TRSV_NB; ++k) mbar_init(&s_barp[k], 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const int t = s_t;
   if (t >= B.nctiles) return;
   const Tile ct = B.ctiles[t];
   const SysDev *s = B.sys[ct.sys];
@@ -378,8 +460,7 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
   if (!(sc->cyc != 0 && sc->early == 0) || !s->p.precond) return;
   const Tri T = s->tri[lower ? 0 : 1];
   const int c = ct.row0, n = s->n, R = s->chunk;
-  const int first = c * R, last = min(n, first + R);  // positions of the chunk
-  const bool use_smem = (last - first) <= smem_rows;
+  const int first = c * R;
   // vectors: line 5' (which 1) w -> yv -> w; line 1' (which 0) r -> t -> r
   const V *in;
   V *out;
@@ -399,242 +480,321 @@ __device__ __forceinline__ void trsv_chunk(const BatchDev &B, int t, int rank, i
   const bool mute = s->p.stall != 0 && c == 0;
   const int g0 = T.levb[c], nlev = T.levb[c + 1] - g0;
   const bool single = s->single_pred != 0;
-  const bool lev_smem = nlev <= smem_lev;
+  const int K = T.K;
+  const unsigned rmask = (unsigned)T.ring - 1u, pmask = (unsigned)T.pring - 1u;
   unsigned *err = &sc->err;
-  // the previous chunk (c - 1) runs in this cluster's CTA rank - 1 and keeps
-  // its values in shared memory; the next chunk (c + 1) in rank + 1
-  const bool pred_cl = cl > 1 && rank > 0 && c > 0 && single && R <= smem_rows;
-  const bool succ_cl = cl > 1 && rank < cl - 1 && t + 1 < B.nctiles &&
-                       B.ctiles[t + 1].sys == ct.sys && single && R <= smem_rows;
-  // a successor in the cluster reads this chunk's values from shared memory,
-  // except for dependencies beyond the KC held in registers, which it reads
-  // from global memory: the global stores may wait until the chunk is done
-  // only when rows have no more than KC dependencies
-  const bool late_store = succ_cl && T.K <= KC;
-  const V *psv = nullptr;
-  if (pred_cl) psv = cg::this_cluster().map_shared_rank(sv, rank - 1);
-
-  // stage the chunk's order and level data once
-  if (use_smem)
-    for (int q = threadIdx.x; q < last - first; q += blockDim.x) sord[q] = T.ord[first + q];
+  V *xbuf = reinterpret_cast<V *>(s->xbuf);
+  // factor entries of 4 bytes when they fit (the FP64 comparison solver's
+  // factors are FP64)
+  const bool f32 = KIND != TK_FP && T.fac32 != 0;
+  const int fb = f32 ? 4 : 8;
+  const unsigned char *blob = KIND == TK_FP ? T.blobd : T.blob;
+  const long long *boff = KIND == TK_FP ? T.boffd : T.boff;
+  const TrsvLayout Ly = trsv_layout(T.maxw, K, T.ring, T.pring, T.maxlev, fb);
+  const int na = (int)Ly.na;
+  // the values a row reads: own ring, predecessor ring, a zero for padding
+  V *vals = reinterpret_cast<V *>(smem);
+  V *pring = vals + T.ring;
+  if (threadIdx.x == 0) vals[T.ring + T.pring] = (V)0;
+  int *slptr = reinterpret_cast<int *>(smem + Ly.oLev);
+  int *sneed = slptr + Ly.lev + 1;
+  int *splptr = sneed + Ly.lev + 1;  // the previous chunk's group pointers
+  const bool lev_smem = Ly.lev != 0;
+  const bool pred = single && c > 0;
+  const int pg0 = pred ? T.levb[c - 1] : 0, pnlev = pred ? g0 - pg0 : 0;
+  const int pfirst = (c - 1) * R;  // first position of the previous chunk
   if (lev_smem) {
     for (int q = threadIdx.x; q <= nlev; q += blockDim.x) slptr[q] = T.lptr[g0 + q];
     for (int q = threadIdx.x; q < nlev; q += blockDim.x) sneed[q] = T.need[g0 + q];
+    for (int q = threadIdx.x; q <= pnlev; q += blockDim.x) splptr[q] = T.lptr[pg0 + q];
   }
   __syncthreads();
-#define ROW_OF(pp) (use_smem ? sord[(pp) - first] : T.ord[pp])
 #define LPTR(l) (lev_smem ? slptr[l] : T.lptr[g0 + (l)])
+#define NEED(l) (lev_smem ? sneed[l] : T.need[g0 + (l)])
+#define PLPTR(l) (lev_smem ? splptr[l] : T.lptr[pg0 + (l)])
+  auto slot = [&](int lv) { return smem + Ly.oSlots + (size_t)(lv % na) * Ly.szSlot; };
+  auto width = [&](int lv) { return LPTR(lv + 1) - LPTR(lv); };
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  if (wid == IGM_TRSV_CW) {  // waiter: one barrier per level with the compute warps
-    u64 seen = 0;  // levels of the previous chunk known to be done
-    bool dead = false;
-    for (int l = 0; l < nlev; ++l) {
-      const int nd = (single && c > 0) ? (lev_smem ? sneed[l] : T.need[g0 + l]) : 0;
-      if (lane == 0 && !dead && (u64)nd > seen && pred_cl) {
-        unsigned v = ld_acquire_cluster_local(s_pred_p);
-        if (v < (unsigned)nd) {
-          const u64 t0 = gtimer();
-          for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
-            if (it > 256) __nanosleep(32);
-            v = ld_acquire_cluster_local(s_pred_p);
-            if (v >= (unsigned)nd) break;
-            if ((it & 255) == 255 &&
-                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > wns))
-              break;
+  if (wid == IGM_TRSV_CW) {  // waiter: the previous chunk's values, ahead of their groups
+    if (lane == 0) {
+      u64 seen = 0;   // groups of the previous chunk known to be done
+      int copied = 0; // groups of the previous chunk copied into the predecessor ring
+      int hi = pfirst;  // first position not yet copied
+      // the copies of the last two groups (group, first and end position),
+      // which may still be in flight
+      int f_lb[2] = {-1, -1}, f_a[2] = {0, 0}, f_e[2] = {0, 0};
+      bool dead = false;
+      const u64 *pw = T.prog + (size_t)IGM_PROG_STRIDE * (c - 1);
+      for (int lb = 0; lb < nlev; ++lb) {
+        // the copy for group lb may overwrite values that groups up to
+        // lb - 3 read (the set-up sized the ring for that): wait until the
+        // compute warps are done with them (bounded by time only: slots
+        // must not stay unfilled)
+        if (lb >= 3 && !wait_cta_own(&s_done, (unsigned)(lb - 2), err, 8 * wns)) dead = true;
+        const int nd = pred ? NEED(lb) : 0;
+        if (!dead && (u64)nd > seen) {
+          const u64 want = ep | (u64)nd;
+          u64 v = ld_acquire64(pw);
+          if (v < want) {
+            const u64 t0 = gtimer();
+            for (int k = 0; k < IGM_WAIT_ITERS; ++k) {
+              if (k > 32) __nanosleep(16);
+              v = ld_acquire64(pw);
+              if (v >= want) break;
+              if ((k & 255) == 255 &&
+                  ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > wns))
+                break;
+            }
+          }
+          if (v < want) {  // expired: the copies still run, the result is flagged
+            atomicOr(err, ERR_TIMEOUT);
+            dead = true;
+          } else {
+            seen = v - ep;
           }
         }
-        if (v < (unsigned)nd) {
-          atomicOr(err, ERR_TIMEOUT);
-          dead = true;
-        } else {
-          seen = v;
+        // copy the previous chunk's positions up to its end of group nd into
+        // the predecessor ring (16-byte aligned pieces, split at the ring's
+        // end); one arrival per group on its barrier
+        u64 *bar = &s_barp[lb % IGM_TRSV_NB];
+        unsigned bytes = 0;
+        int a = 0, e = 0;
+        if (nd > copied) {
+          const int top = PLPTR(nd);
+          e = (top + 1) & ~1;
+          // values more than a ring behind the copy's end are never read
+          // again (the set-up sized the ring so), so one copy covers at most
+          // one ring
+          a = max(hi & ~1, e - (int)(pmask + 1u));
+          bytes = (unsigned)(e - a) * 8u;
+          hi = top;
+          copied = nd;
+          // copies are not ordered among themselves: a copy still in flight
+          // (issued for the last two groups; older ones were waited for by
+          // their groups' threads) that writes slots this one writes too --
+          // the last pair of the previous copy, which held a value not yet
+          // computed, or slots a ring apart -- must land first
+          for (int k = 0; k < 2; ++k)
+            if (f_lb[k] >= 0 && f_lb[k] >= lb - 2 &&
+                (a < f_e[k] || e - f_a[k] > (int)(pmask + 1u)))
+              mbar_wait(&s_barp[f_lb[k] % IGM_TRSV_NB], (unsigned)(f_lb[k] / IGM_TRSV_NB) & 1u,
+                        err, 4 * wns);
+          f_lb[1] = f_lb[0];
+          f_a[1] = f_a[0];
+          f_e[1] = f_e[0];
+          f_lb[0] = lb;
+          f_a[0] = a;
+          f_e[0] = e;
         }
-      } else if (lane == 0 && !dead && (u64)nd > seen) {
-        const u64 want = ep | (u64)nd;
-        u64 v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
-        if (v < want) {
-          const u64 t0 = gtimer();
-          for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
-            if (it > 32) __nanosleep(16);
-            v = ld_acquire64(T.prog + (size_t)IGM_PROG_STRIDE * (c - 1));
-            if (v >= want) break;
-            if ((it & 255) == 255 &&
-                ((*(volatile unsigned *)err & ERR_TIMEOUT) || gtimer() - t0 > wns))
-              break;
-          }
-        }
-        if (v < want) {  // expired: the compute warps finish unchecked, the result is flagged
-          atomicOr(err, ERR_TIMEOUT);
-          dead = true;
-        } else {
-          seen = v - ep;
+        if (bytes) fence_proxy_async_global();
+        mbar_expect_tx(bar, bytes);
+        while (a < e) {
+          const unsigned sl = (unsigned)a & pmask;  // even: a is
+          const int m = min(e - a, (int)(pmask + 1u - sl));
+          bulk_g2s(pring + sl, xbuf + a, (unsigned)m * 8u, bar);
+          a += m;
         }
       }
-      __syncwarp();
-      asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
+      // no copy may still be in flight when the CTA exits (the compute
+      // warps waited for every group's copies unless a wait expired)
+      for (int lb = nlev - IGM_TRSV_NB > 0 ? nlev - IGM_TRSV_NB : 0; lb < nlev; ++lb)
+        mbar_wait(&s_barp[lb % IGM_TRSV_NB], (unsigned)(lb / IGM_TRSV_NB) & 1u, err, 4 * wns);
     }
     return;
   }
   if (wid == IGM_TRSV_CW + 1) {  // publisher
     if (lane == 0) {
       for (unsigned pub = 0; pub < (unsigned)nlev;) {
-        // levels every compute warp has finished
-        if (!wait_cta(&s_done, (pub + 1) * IGM_TRSV_CW, err, 4 * wns)) break;
-        pub = ld_acquire_cta(&s_done) / IGM_TRSV_CW;
+        // groups the compute warps have finished
+        if (!wait_cta(&s_done, pub + 1, err, 4 * wns)) break;
+        pub = ld_acquire_cta(&s_done);
         if (mute) continue;
-        if (succ_cl) st_release_cluster_remote(s_pred_p, rank + 1, pub);
-        else st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
+        st_release64(T.prog + (size_t)IGM_PROG_STRIDE * c, ep | (u64)pub);
       }
     }
     return;
   }
-
-  // compute warps.  A thread's first row of a level (threads below rmax) is
-  // copied into a shared-memory ring pf levels ahead with asynchronous
-  // copies; other rows are loaded when they are computed.
-  const int tid = threadIdx.x;
-  const bool fast = single && use_smem;
-  const int kk = T.K < kr ? T.K : kr;  // dependencies this system keeps in the ring
-  unsigned ev = 0;
-  // the packed arrays of each register-held dependency
-  const int *pcq[KC];
-  const void *pfq[KC];
-#pragma unroll
-  for (int q = 0; q < KC; ++q) {
-    pcq[q] = T.pcol + (size_t)q * n;
-    if (KIND == TK_FP) pfq[q] = T.pfacd + (size_t)q * n;
-    else pfq[q] = T.pfac + (size_t)q * n;
+  if (wid == IGM_TRSV_CW + 2) {  // block warp
+    if (lane == 0) {
+      // blocks of one chunk are contiguous: each group's offset follows from
+      // the widths
+      long long off = boff[g0], poff = off;
+      int pl = 0;  // next group to prefetch into L2
+      auto bytes_of = [&](int lv) { return trsv_blk_bytes(trsv_wp(width(lv)), K, fb); };
+      auto prefetch_upto = [&](int lv) {
+        for (; pl <= lv && pl < nlev; ++pl) {
+          const unsigned b = bytes_of(pl);
+          bulk_prefetch_l2(blob + poff, b);
+          poff += b;
+        }
+      };
+      auto issue = [&](int lv) {
+        const unsigned b = bytes_of(lv);
+        u64 *bar = &s_blk[lv % na];
+        mbar_expect_tx(bar, b);
+        bulk_g2s(slot(lv), blob + off, b, bar);
+        off += b;
+      };
+      prefetch_upto(na + IGM_TRSV_PFL - 1);
+      for (int lv = 0; lv < na && lv < nlev; ++lv) issue(lv);
+      // the slot of group k - 1 takes group k - 1 + na once k groups are done
+      for (int k = 1; k - 1 + na < nlev; ++k) {
+        if (!wait_cta_own(&s_done, (unsigned)k, err, 8 * wns)) break;
+        issue(k - 1 + na);
+        prefetch_upto(k - 1 + na + IGM_TRSV_PFL);
+      }
+      // no copy may still be in flight when the CTA exits
+      for (int k = 0; k < na && k < nlev; ++k) {
+        const int lastlv = k + (nlev - 1 - k) / na * na;
+        mbar_wait(&s_blk[k], (unsigned)(lastlv / na) & 1u, err, 4 * wns);
+      }
+    }
+    return;
   }
-  auto issue = [&](int lv) {
-    if (pf == 0) return;
-    if (lv < nlev && tid < rmax) {
-      const int pn = LPTR(lv) + tid;
-      if (pn < LPTR(lv + 1)) {
-        const int sl = lv % S;
-        long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
-        int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
+  if (wid == IGM_TRSV_CW + 3) {  // gather warp: right-hand sides into each slot
+    for (int lv = 0; lv < nlev; ++lv) {
+      const int k = lv % na;
+      const bool ok = mbar_wait(&s_blk[k], (unsigned)(lv / na) & 1u, err, 4 * wns);
+      const int w = width(lv);
+      unsigned char *sl = slot(lv);
+      if (ok) {  // the block's orders are in place
+        const int *bord = reinterpret_cast<const int *>(sl) + (size_t)K * trsv_wp(w);
+        V *rhs = reinterpret_cast<V *>(sl + Ly.szBlk);
+        for (int r = lane; r < w; r += 32) cp_async8(rhs + r, in + bord[r]);
+      }
+      cp_async_arrive_noinc(&s_rdy[k]);
+      if (lane == 0) mbar_arrive(&s_rdy[k]);
+    }
+    cp_async_wait<0>();
+    return;
+  }
+
+  // compute warps.  A thread whose wait for a slot expired never reads a
+  // slot's contents again (they may be stale or never written): it keeps
+  // its barrier obligations and leaves its rows alone; the call reports
+  // IGM_ETIMEOUT.
+  const int tid = threadIdx.x;
+  unsigned ev = 0;
+  bool poisoned = false;
+  auto late = [&](int code) -> V {
+    const int pj = -1 - code;
+    if (!single && pj < first)
+      wait_prog(T.prog + (size_t)IGM_PROG_STRIDE * (pj / R),
+                ep | (u64)(T.lev[T.ord[pj]] + 1), err);
+    return (V)__ldcg(xbuf + pj);
+  };
+  int cs = 0, us = 0;  // slot of group l and its uses before l (l mod na, l / na)
+  int cb = 0, up = 0;  // barrier of group l's predecessor copy (l mod NB, l / NB)
+  for (int l = 0; l < nlev; ++l) {
+    __syncwarp();
+    // the previous group's ring values are visible
+    asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC) : "memory");
+    if (tid == 0 && l > 0) st_release_cta(&s_done, (unsigned)l);
+    const int p0 = LPTR(l), w = LPTR(l + 1) - p0;
+    if (tid < w && !poisoned &&
+        !(mbar_wait(&s_rdy[cs], (unsigned)us & 1u, err, 2 * wns) &&
+          mbar_wait(&s_barp[cb], (unsigned)up & 1u, err, 2 * wns)))
+      poisoned = true;
+    if (tid < w && !poisoned) {
+      const unsigned wp = trsv_wp(w);
+      const unsigned char *blk = smem + Ly.oSlots + (size_t)cs * Ly.szSlot;
+      const int *scode = reinterpret_cast<const int *>(blk);
+      const int *sord = scode + (size_t)K * wp;
+      const int *syb = sord + wp;
+      const unsigned char *sfac = reinterpret_cast<const unsigned char *>(syb + wp);
+      const unsigned char *sdg = sfac + (size_t)fb * K * wp;  // diagonals, then multipliers
+      const V *srhs = reinterpret_cast<const V *>(blk + Ly.szBlk);
+      for (int r = tid; r < w; r += IGM_TRSV_NC) {
+        const int row = sord[r];
+        auto dep = [&](int q) -> V {
+          const int code = scode[(size_t)q * wp + r];
+          return code >= 0 ? vals[code] : late(code);
+        };
+        auto fac = [&](int q) -> i64 {
+          return f32 ? (i64)reinterpret_cast<const int *>(sfac)[(size_t)q * wp + r]
+                     : reinterpret_cast<const i64 *>(sfac)[(size_t)q * wp + r];
+        };
+        V y;
+        if (KIND == TK_INT) {
+          i64 yv[KC], fv[KC];
+          u64 mag = 0;  // the largest |y| (as y ^ (y >> 63))
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          if (q < kk) {
-            cp_async4(r32 + q * rmax, pcq[q] + pn);
-            cp_async8(r64 + q * rmax, static_cast<const long long *>(pfq[q]) + pn);
+          for (int q = 0; q < KC; ++q) {
+            yv[q] = q < K ? (i64)dep(q) : 0;
+            fv[q] = q < K ? fac(q) : 0;
+            mag |= (u64)(yv[q] ^ (yv[q] >> 63));
+          }
+          for (int q = KC; q < K; ++q) {
+            const i64 v = (i64)dep(q);
+            mag |= (u64)(v ^ (v >> 63));
+          }
+          const i64 rhs = (i64)srhs[r];
+          const int yb = syb[r];
+          i64 num;
+          if (yb >= 0 && (mag >> yb) == 0) {
+            // every product and the sum are below 2^62 (the set-up's bound):
+            // exact in 64-bit words, no event possible; only the difference
+            // with the right-hand side may leave the range
+            i64 sum = 0;
+#pragma unroll
+            for (int q = 0; q < KC; ++q) sum += fv[q] * yv[q];
+            for (int q = KC; q < K; ++q) sum += fac(q) * (i64)dep(q);
+            num = (i64)((u64)rhs - (u64)sum);
+            ev += (((rhs ^ sum) & (rhs ^ num)) < 0);
+          } else {
+            i128 sum = 0;
+#pragma unroll
+            for (int q = 0; q < KC; ++q) sum += (i128)mulw(fv[q], yv[q], ev);
+            for (int q = KC; q < K; ++q) sum += (i128)mulw(fac(q), (i64)dep(q), ev);
+            const i128 acc = (i128)rhs - sum;
+            ev += out64(acc);
+            num = wrap(acc);
+          }
+          const i64 dg = reinterpret_cast<const i64 *>(sdg)[r];
+          const u64 dm = reinterpret_cast<const u64 *>(sdg)[(size_t)wp + r];
+          y = (V)divt_magic(num, dg, dm, ev);
+        } else {
+          // FP64: subtract in CSR order (L packed ascending, U descending);
+          // padding subtracts an exact zero
+          auto facd = [&](int q) -> double {
+            if (KIND == TK_FPI) return (double)fac(q);
+            return reinterpret_cast<const double *>(sfac)[(size_t)q * wp + r];
+          };
+          double acc = (double)srhs[r];
+          for (int k = 0; k < K; ++k) {
+            const int q = lower ? k : K - 1 - k;
+            acc = __dsub_rn(acc, __dmul_rn(facd(q), (double)dep(q)));
+          }
+          if (KIND == TK_FP && lower) {
+            y = (V)acc;  // unit lower factor
+          } else {
+            const double dg = KIND == TK_FPI ? (double)reinterpret_cast<const i64 *>(sdg)[r]
+                                             : reinterpret_cast<const double *>(sdg)[r];
+            y = (V)__ddiv_rn(acc, dg);
           }
         }
-        if (KIND != TK_FP) cp_async8(r64 + kr * rmax, T.pdiag + pn);
-        else if (T.pdiagd) cp_async8(r64 + kr * rmax, T.pdiagd + pn);
-        if (KIND == TK_INT) cp_async8(r64 + (kr + 1) * rmax, T.pdm + pn);
-        cp_async8(r64 + (kr + 2) * rmax, in + ROW_OF(pn));
+        vals[(unsigned)(p0 + r - first) & rmask] = y;
+        out[row] = y;
+        xbuf[p0 + r] = y;
       }
     }
-    cp_async_commit();
-  };
-  auto ring_row = [&](int lv, int p, RowPre<KIND, KC> &r) {
-    const int sl = lv % S;
-    const long long *r64 = ring64 + (size_t)sl * (kr + 3) * rmax + tid;
-    const int *r32 = ring32 + (size_t)sl * kr * rmax + tid;
-    r.i = ROW_OF(p);
-#pragma unroll
-    for (int q = 0; q < KC; ++q) {
-      if (q < kk) {
-        r.col[q] = r32[q * rmax];
-        const long long w = r64[q * rmax];
-        if (KIND == TK_INT) r.fac[q] = (V)w;
-        else if (KIND == TK_FPI) r.fac[q] = (V)(double)w;
-        else r.fac[q] = (V)__longlong_as_double(w);
-      } else {
-        r.col[q] = -1;
-        r.fac[q] = 0;
-      }
+    if (++cs == na) {
+      cs = 0;
+      ++us;
     }
-    const long long dw = r64[kr * rmax], rw = r64[(kr + 2) * rmax];
-    if (KIND == TK_INT) {
-      r.diag = (V)dw;
-      r.dm = (u64)r64[(kr + 1) * rmax];
-      r.rhs = (V)rw;
-    } else {
-      if (KIND == TK_FPI) r.diag = (V)(double)dw;
-      else r.diag = (V)(T.pdiagd ? __longlong_as_double(dw) : 1.0);
-      r.dm = 0;
-      r.rhs = (V)__longlong_as_double(rw);
+    if (++cb == IGM_TRSV_NB) {
+      cb = 0;
+      ++up;
     }
-  };
-  for (int l = 0; l < pf; ++l) issue(l);
-  for (int l = 0; l < nlev; ++l) {
-    const int p0 = LPTR(l), p1 = LPTR(l + 1);
-    issue(l + pf);
-    // the waiter has seen the previous chunk reach what this level reads;
-    // the previous level's shared values are visible
-    __syncwarp();
-    asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC + 32) : "memory");
-    if (pf > 0) cp_async_wait(pf);  // this thread's copies of level l have landed
-    for (int p = p0 + tid; p < p1; p += IGM_TRSV_NC) {
-      RowPre<KIND, KC> rr;
-      if (pf > 0 && p == p0 + tid && tid < rmax) ring_row(l, p, rr);
-      else row_load<KIND, KC>(rr, T, n, p, ROW_OF(p), in);
-      const V y = fast ? trsv_row<KIND, KC, true>(rr, p, T, n, lower, first, R, use_smem, single, ep,
-                                              sv, psv, out, err, ev)
-                       : trsv_row<KIND, KC, false>(rr, p, T, n, lower, first, R, use_smem, single,
-                                               ep, sv, nullptr, out, err, ev);
-      // shared slots are indexed by the row's natural position in the chunk
-      // (the order inside a level group is arbitrary)
-      if (use_smem) sv[(lower ? rr.i : n - 1 - rr.i) - first] = y;
-      if (!late_store) out[rr.i] = y;
-    }
-    // the warp's stores of the level, then one count per warp for the
-    // publisher
-    __syncwarp();
-    if (lane == 0) red_release_cta(&s_done, 1u);
   }
-  if (late_store) {
-    // the chunk's values go to global memory once, in one coalesced sweep
-    // after its last level, so the publisher's releases never wait for
-    // global stores
-    asm volatile("bar.sync 3, %0;" ::"n"(IGM_TRSV_NC) : "memory");
-    for (int q = tid; q < last - first; q += IGM_TRSV_NC)
-      out[lower ? first + q : n - 1 - (first + q)] = sv[q];
-  }
-  if (pf > 0) cp_async_wait(0);
+  __syncwarp();
+  asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC) : "memory");
+  if (tid == 0) st_release_cta(&s_done, (unsigned)nlev);
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
-#undef ROW_OF
 #undef LPTR
-}
-
-// The substitution kernel.  Without clusters each CTA takes a chunk by
-// ticket; with clusters of cl CTAs, rank 0 takes a ticket for cl consecutive
-// chunks (tickets keep every chunk's predecessor started before it), and all
-// CTAs of a cluster stay resident until the last one is done, since later
-// chunks read earlier chunks' shared memory.
-template <int KIND, int KC>
-__global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
-    k_trsv_lv(BatchDev B, int lower, int which, int smem_rows, int smem_lev, int rmax, int pf,
-              int kr, int cl) {
-  __shared__ int s_t;
-  __shared__ unsigned s_done, s_pred;
-  const int tk = which == 0 ? (lower ? 0 : 1) : (lower ? 2 : 3);
-  if (cl > 1) {
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    if (threadIdx.x == 0) {
-      if (rank == 0) s_t = (int)atomicAdd(&B.ticket[tk], 1u);
-      s_done = 0;
-      s_pred = 0;
-    }
-    cluster.sync();  // rank 0's ticket and every CTA's counters are set
-    const int t = *cluster.map_shared_rank(&s_t, 0) * cl + rank;
-    trsv_chunk<KIND, KC>(B, t, rank, cl, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
-                     &s_pred);
-    cluster.sync();  // no CTA leaves while a later chunk may read its values
-  } else {
-    if (threadIdx.x == 0) {
-      s_t = (int)atomicAdd(&B.ticket[tk], 1u);
-      s_done = 0;
-      s_pred = 0;
-    }
-    __syncthreads();
-    trsv_chunk<KIND, KC>(B, s_t, 0, 1, lower, which, smem_rows, smem_lev, rmax, pf, kr, &s_done,
-                     &s_pred);
-  }
+#undef NEED
+#undef PLPTR
 }
 
 // ---------------------------------------------------------------------------
@@ -762,12 +922,46 @@ void launch_maxdeps(int n, const int *rowptr, const int *diagpos, int lower, int
   s_maxdeps<<<grid_n(n), 256, 0, st>>>(n, rowptr, diagpos, lower, kmax);
 }
 
+void launch_chunkdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                      int R, int *dmax, cudaStream_t st) {
+  s_chunkdist<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, R, dmax);
+}
+
+void launch_regroup(int n, int R, const int *ord, int *lev, const int *levb_old,
+                    const int *lptr_old, const int *newbase, const int *levb_new, int cap,
+                    int *posof, cudaStream_t st) {
+  s_regroup<<<grid_n(n), 256, 0, st>>>(n, R, ord, lev, levb_old, lptr_old, newbase, levb_new, cap,
+                                        posof);
+}
+
+void launch_ringdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                     int R, const int *ord, const int *posof, const int *lev, const int *levb,
+                     const int *lptr, int *dmax, cudaStream_t st) {
+  s_ringdist<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, R, ord, posof, lev, levb,
+                                         lptr, dmax);
+}
+
+void launch_pringdist(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
+                      int R, const int *ord, const int *posof, const int *lev, const int *levb,
+                      const int *lptr, const int *needpm, int *dmax, cudaStream_t st) {
+  s_pringdist<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, R, ord, posof, lev, levb,
+                                          lptr, needpm, dmax);
+}
+
+void launch_facmax(int n, const int *rowptr, const int *diagpos, int lower, const i64 *fac,
+                   unsigned long long *mx, cudaStream_t st) {
+  s_facmax<<<grid_n(n), 256, 0, st>>>(n, rowptr, diagpos, lower, fac, mx);
+}
+
 void launch_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int K,
-                 const int *ord, const i64 *fac, const i64 *ldiag, const i64 *udiag,
-                 const double *f, int *pcol, i64 *pfac, i64 *pdiag, u64 *pdm,
-                 double *pfacd, double *pdiagd, cudaStream_t st) {
-  s_pack<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, K, ord, fac, ldiag, udiag, f,
-                                     pcol, pfac, pdiag, pdm, pfacd, pdiagd);
+                 int R, int single, int ring, int pring, int fac32, const int *ord,
+                 const int *posof, const int *lev, const int *levb, const int *lptr,
+                 const long long *boff, const long long *boffd, const i64 *fac, const i64 *ldiag,
+                 const i64 *udiag, const double *f, unsigned char *blob, unsigned char *blobd,
+                 cudaStream_t st) {
+  s_pack<<<grid_n(n), 256, 0, st>>>(n, rowptr, col, diagpos, lower, K, R, single, ring, pring,
+                                     fac32, ord, posof, lev, levb, lptr, boff, boffd, fac, ldiag,
+                                     udiag, f, blob, blobd);
 }
 
 void launch_need(int n, const int *rowptr, const int *col, const int *diagpos, int lower, int R,
@@ -782,78 +976,27 @@ void launch_ilu0_lv(int n, const int *rowptr, const int *col, const int *diagpos
                                                  epoch, err);
 }
 
-// shared memory: a chunk's values and order if the chunk fits in 200 KB,
-// its level pointers and requirements if they fit in the rest, then as deep
-// a ring of prefetched rows (up to three levels ahead) as the remainder holds
-static int smem_rows_for(int bytes_per) { return (200 * 1024) / bytes_per; }
-#define IGM_TRSV_SMEM_MAX (226 * 1024)
+// the widest group a factor with K dependencies per row may have: every slot
+// of the substitution kernel must fit in its shared memory with rings of the
+// largest size
+int trsv_group_cap(int K) {
+  int W = 4096;
+  while (W > 8 && trsv_layout(W, K, IGM_TRSV_RING_MAX, IGM_TRSV_RING_MAX, 0, 8,
+                              IGM_TRSV_NA_MIN).total + 8 * 1024 > IGM_TRSV_SMEM)
+    W -= 8;
+  return W;
+}
 
 template <int KIND, int KC>
-static void launch_lv(const BatchDev &B, int lower, int which, int max_chunk, cudaStream_t st) {
+static void launch_lv(const BatchDev &B, int lower, int which, cudaStream_t st) {
   if (B.nctiles <= 0) return;
-  const int bper = 8 + 4;  // a value and an order entry per row
-  int rows = smem_rows_for(bper);
-  if (rows > max_chunk) rows = max_chunk;
-  size_t sm = (size_t)rows * bper;
-  int lev = B.trsv_maxlev;
-  if (sm + (size_t)(2 * lev + 1) * sizeof(int) > IGM_TRSV_SMEM_MAX) lev = 0;
-  sm += (size_t)(2 * lev + 1) * sizeof(int);
-  const int kr = B.trsv_maxk < KC ? (B.trsv_maxk > 0 ? B.trsv_maxk : 1) : KC;
-  const int rmax = B.trsv_maxw < IGM_TRSV_NC ? B.trsv_maxw : IGM_TRSV_NC;
-  const size_t per_slot = (size_t)rmax * ((kr + 3) * 8 + kr * 4);
-  int pf = 0;
-  for (int d = 3; d >= 1; --d)
-    if (sm + (size_t)(d + 1) * per_slot <= IGM_TRSV_SMEM_MAX) {
-      pf = d;
-      break;
-    }
-  if (pf > 0) sm += (size_t)(pf + 1) * per_slot;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_trsv_lv<KIND, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         IGM_TRSV_SMEM_MAX);
+                         IGM_TRSV_SMEM);
     attr_set = true;
   }
-  // clusters of consecutive chunks when the GPU can co-schedule them (4 by
-  // default: larger clusters are harder to place and measured slower)
-  int cl = B.trsv_cluster;
-  if (cl == 0) {
-    cl = 1;
-    for (int want = 4; want >= 2; want /= 2) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3(want);
-      q.blockDim = dim3(IGM_TRSV_THREADS);
-      q.dynamicSmemBytes = sm;
-      cudaLaunchAttribute qa[1];
-      qa[0].id = cudaLaunchAttributeClusterDimension;
-      qa[0].val.clusterDim.x = want;
-      qa[0].val.clusterDim.y = 1;
-      qa[0].val.clusterDim.z = 1;
-      q.attrs = qa;
-      q.numAttrs = 1;
-      int nclus = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclus, k_trsv_lv<KIND, KC>, &q) == cudaSuccess && nclus >= 1) {
-        cl = want;
-        break;
-      }
-      cudaGetLastError();
-    }
-  }
-  const int G = (B.nctiles + cl - 1) / cl * cl;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(G);
-  cfg.blockDim = dim3(IGM_TRSV_THREADS);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cl;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = cl > 1 ? 1 : 0;
-  note_launch(cudaLaunchKernelEx(&cfg, k_trsv_lv<KIND, KC>, B, lower, which, rows, lev, rmax, pf,
-                                 kr, cl));
+  k_trsv_lv<KIND, KC><<<B.nctiles, IGM_TRSV_THREADS, IGM_TRSV_SMEM, st>>>(B, lower, which);
 }
 
 void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaStream_t st) {
@@ -864,17 +1007,16 @@ void launch_trsv_color(const BatchDev &B, int kind, int lower, int which, cudaSt
   }
 }
 
-void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, int max_chunk,
-                    cudaStream_t st) {
+void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, cudaStream_t st) {
   if (B.max_colors > 0) launch_trsv_color(B, kind, lower, which, st);
   if (B.trsv_maxk <= IGM_TRSV_KC_SMALL) {
-    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
-    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
-    else launch_lv<TK_FP, IGM_TRSV_KC_SMALL>(B, lower, which, max_chunk, st);
+    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_SMALL>(B, lower, which, st);
+    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_SMALL>(B, lower, which, st);
+    else launch_lv<TK_FP, IGM_TRSV_KC_SMALL>(B, lower, which, st);
   } else {
-    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
-    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
-    else launch_lv<TK_FP, IGM_TRSV_KC_LARGE>(B, lower, which, max_chunk, st);
+    if (kind == TK_INT) launch_lv<TK_INT, IGM_TRSV_KC_LARGE>(B, lower, which, st);
+    else if (kind == TK_FPI) launch_lv<TK_FPI, IGM_TRSV_KC_LARGE>(B, lower, which, st);
+    else launch_lv<TK_FP, IGM_TRSV_KC_LARGE>(B, lower, which, st);
   }
 }
 
