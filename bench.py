@@ -3,14 +3,17 @@
 
 Metric: refined solves per second to a relative residual of 1e-10 (Fig. 1
 of Iwashita, Suzuki, Fukaya, ScalA'20 with the int-GMRES(m) inner solve of
-Fig. 2).  Default workload: 3D convection-diffusion, 7-point stencil on a
-128^3 grid (n = 2,097,152, nnz = 14,581,760), per-cell convection
-U[-50, 50], log-normal diffusion (sigma 1), b ~ U[-1, 1], integer ILU(0)
-(Sec. VI) and GMRES(50), synthetic data from a fixed seed.
+Fig. 2).  Default workload, the largest single-GPU one: 3D heterogeneous
+diffusion-convection, 27-point stencil on a 200^3 grid (n = 8,000,000,
+nnz = 213,847,192), log-normal diffusion (sigma 2.5), convection
+U[-100, 100], b ~ U[-1, 1], integer ILU(0) (Sec. VI) and GMRES(60),
+synthetic data from a fixed seed.  The same line carries the 128^3 7-point
+workload (GMRES(50), ILU(0)) as a secondary measurement.
 
 One step = one ir_solve of the whole system (setup done once, inputs
-resident in HBM).  The working set (matrix, factors, basis: ~2 GB) is far
-larger than L2, so no flush is needed between steps.
+resident in HBM).  The working set (matrix, factors, basis: ~20 GB, ~2 GB
+for the secondary) is far larger than L2, so no flush is needed between
+steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -56,7 +59,9 @@ WORKLOADS = {
     "cfg4": dict(desc="3D heterogeneous diffusion-convection 27-pt 200^3 (n=8,000,000, "
                       "nnz~216M), log-normal diffusion sigma 2.5, convection U[-100,100], "
                       "ILU(0) int-GMRES(60), FP64 refinement to 1e-10",
-                 gen=lambda: W.config4(), precond=1, m=60),
+                 gen=lambda: W.config4(), precond=1, m=60,
+                 # the oracle's bounded sample: the same generator on a 60^3 grid
+                 sample=lambda: W.config4(N=60, seed=4), sample_desc="27-pt 60^3"),
     "cfg3": dict(desc="serving stream: Poisson arrivals 2k req/s, 2D 5-pt / 3D 7-pt / 3D "
                       "27-pt convection-diffusion, sides U[16,160], Peclet log-U[0.1,100], "
                       "tol 1e-8 or 1e-10, 150 GB budget, continuous batching", m=30),
@@ -69,7 +74,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg4", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 128^3 7-point secondary measurement")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -169,15 +176,17 @@ def job_throughput(local_ms: float, steps: int, dist=None, device="cpu") -> tupl
 
 def algorithmic_bytes(kind: str, n: int, nnz: int, nnz_l: int, val_bytes: int,
                       m: int, terms: int = 0) -> float:
-    """Bytes the method must move per launch.  SpMV: nnz ((s+1) b_val + 4)
-    + 4(n+1) + 16n (s correction terms, v_j in, w out).  Arnoldi step
-    j = m-1: each of the m basis vectors once (8n each), w in and v_m out
-    (8n each).  One triangular solve: (nnz_tri + n) 12 + 16n.  FP64
-    residual: nnz 12 + 4(n+1) + 24n."""
+    """Bytes the method must move per launch, counted as the hot-path scope
+    counts them (what the method needs, not what a layout happens to move):
+    SpMV nnz ((s+1) b_val + 4) + 4(n+1) + 4n (s correction terms; the basis
+    vector v_j read as int32 words: the upper bits of a Q30 basis entry are
+    zero, Sec. V-D).  Arnoldi step j = m-1: the m basis vectors read once
+    (4n each, w kept on chip) and v_m written (4n).  One triangular solve:
+    (nnz_tri + n) 12 + 16n.  FP64 residual: nnz 12 + 4(n+1) + 24n."""
     if kind == "spmv":
-        return nnz * ((terms + 1) * val_bytes + 4) + 4 * (n + 1) + 16 * n
+        return nnz * ((terms + 1) * val_bytes + 4) + 4 * (n + 1) + 4 * n
     if kind == "arnoldi":
-        return 8.0 * n * (m + 2)
+        return 4.0 * n * (m + 1)
     if kind in ("trsv_l", "trsv_u"):
         return (nnz_l + n) * 12 + 16 * n
     if kind == "resid":
@@ -207,6 +216,34 @@ def traffic_for(kernel: str, workload: str):
 
 
 # ---------------------------------------------------------------------------
+def cpu_baseline_scaled(wl, sysw, refinements: int):
+    """The oracle, single-threaded, on a bounded sample for a workload too
+    large to set up on one core within the budget: a complete refined solve
+    of the same generator on a smaller grid, scaled to the full system by
+    the work of a solve (refinements x m Arnoldi steps of 3 nnz products --
+    SpMV and the two substitutions -- plus (m+3)/2 basis vectors of n rows
+    on average, and the set-up's nnz)."""
+    import oracle
+    oracle.build()
+    sm = wl["sample"]()
+    m = wl["m"]
+    P = oracle.Params.table5(m=m) if wl["precond"] else oracle.Params.table4(m=m)
+    t0 = time.perf_counter()
+    x, ro = oracle.ir_solve(sm.rowptr, sm.col, sm.val, sm.b, P)
+    dt = time.perf_counter() - t0
+
+    def work(nnz, n, refs):
+        return refs * m * (3.0 * nnz + 0.5 * (m + 3) * n) + nnz
+
+    scale = work(sysw.nnz, sysw.n, refinements) / work(sm.nnz, sm.n, ro.refinements)
+    per_solve = dt * scale
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"one complete oracle solve ({ro.refinements} refinements, {dt:.1f} s) of "
+                      f"the same generator on a {wl['sample_desc']} grid (n={sm.n}, "
+                      f"nnz={sm.nnz}), scaled x{scale:.0f} by the work of a solve to the full "
+                      f"system ({refinements} refinements)"}
+
+
 def cpu_baseline(sysw, precond: int, m: int, refinements: int, budget_s: float = 30.0):
     """The oracle, single-threaded, on a bounded sample: its set-up plus one
     inner solve of the full system (one of the `refinements` the full solve
@@ -239,7 +276,20 @@ def run_reference(args, wl):
     oracle.build()
     P = oracle.Params.table5(m=wl["m"]) if wl["precond"] else oracle.Params.table4(m=wl["m"])
     refinements = wl.get("refinements", 0)
-    if sysw.n <= 50000:
+    if "sample" in wl:
+        # too large to set up on one core within minutes: complete solves of
+        # the same generator on a smaller grid, scaled by the work of a solve
+        steps = max(1, min(args.steps, 3))
+        vals, dts = [], []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            cb = cpu_baseline_scaled(wl, sysw, refinements)
+            dts.append(time.perf_counter() - t0)
+            vals.append(cb["value"])
+        value = statistics.median(vals)
+        dt = sum(dts)
+        sample = cb["sample"]
+    elif sysw.n <= 50000:
         # small workload: whole refined solves
         steps = args.steps
         t0 = time.perf_counter()
@@ -312,6 +362,7 @@ def run_ours(args, wl):
     xh = torch.empty(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     solver = L.Solver(rp, cl, vl, P, stream=stream)
+    ws_bytes = solver.device_bytes()
 
     def barrier():
         if dist is not None:
@@ -381,7 +432,7 @@ def run_ours(args, wl):
         Pf = P.replace(inner=1)
         sf = L.Solver(rp, cl, vl, Pf, stream=stream)
         _, rf = sf.ir_solve(bh, xh, stream=stream)
-        kf = max(1, min(args.steps, 3))
+        kf = max(1, min(args.steps, 3 if n < 4_000_000 else 1))
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -398,7 +449,7 @@ def run_ours(args, wl):
     # the multicolour order (a GPU-motivated reordering of the preconditioner,
     # not the paper's natural order) on the same workload, for comparison
     variant = None
-    if not args.no_fp64 and args.order == 0 and precond != 0:
+    if not args.no_fp64 and args.order == 0 and precond != 0 and n < 4_000_000:
         Pm = P.replace(order=1)
         sm_ = L.Solver(rp, cl, vl, Pm, stream=stream)
         _, rm = sm_.ir_solve(bh, xh, stream=stream)
@@ -458,7 +509,8 @@ def run_ours(args, wl):
                        "shifts_start": [P.beta7, P.beta8, P.beta10, P.beta13, P.beta15],
                        "shift_retries": rep["shift_retries"],
                        "shifts_final": list(rep["beta_final"]),
-                       "l2": "working set (~2 GB) > L2, no flush",
+                       "l2": f"working set (~{ws_bytes / 1e9:.0f} GB) > L2 "
+                             "(129 MB), no flush",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(step_ms, 50)),
             "p99_ms": float(np.percentile(step_ms, 99)),
@@ -467,10 +519,57 @@ def run_ours(args, wl):
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
             "fp64_gmres": fp64, "multicolour_variant": variant}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(sysw, wl["precond"], wl["m"], refinements)
+        if "sample" in wl:
+            line["cpu_baseline"] = cpu_baseline_scaled(wl, sysw, refinements)
+        else:
+            line["cpu_baseline"] = cpu_baseline(sysw, wl["precond"], wl["m"], refinements)
+    if args.workload == "cfg4" and not args.no_secondary:
+        line["secondary"] = secondary_cfg1(L, dev, stream, world, args.terms)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def secondary_cfg1(L, dev, stream, world, terms, steps=3, warmup=2):
+    """The 128^3 7-point workload (ILU(0), GMRES(50)) measured the same way
+    as the headline: refined solves/s over `steps` solves after `warmup`,
+    and the per-kernel times with their algorithmic bandwidth."""
+    import torch
+    import ctypes as C
+    wl = WORKLOADS["cfg1"]
+    sysw = wl["gen"]()
+    n, nnz, m = sysw.n, sysw.nnz, wl["m"]
+    P = L.params_default(1, m)
+    rp, cl, vl, bh = [torch.from_numpy(a).to(dev) for a in (sysw.rowptr, sysw.col, sysw.val,
+                                                              sysw.b)]
+    xh = torch.empty(n, dtype=torch.float64, device=dev)
+    sv = L.Solver(rp, cl, vl, P, stream=stream)
+    for _ in range(warmup):
+        _, rep = sv.ir_solve(bh, xh, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        _, rep = sv.ir_solve(bh, xh, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    assert rep["status"] == "ok" and rep["relres"] < 1e-10, rep
+    buf = (C.c_double * 5)()
+    if L.load().igm_time_kernels(sv.handle, 3, buf, stream.cuda_stream) != 0:
+        raise RuntimeError(L.load().igm_last_error().decode())
+    peak, _ = peak_hbm()
+    kern = {}
+    for k, name in enumerate(KNAMES):
+        if buf[k] < 0:
+            continue
+        gbs = algorithmic_bytes(name, n, nnz, (nnz - n) // 2, 8, m, terms) / (buf[k] * 1e6)
+        kern[name] = {"ms_per_launch": round(buf[k], 5), "algorithmic_GBs": round(gbs, 1),
+                      "frac_of_peak": round(gbs / peak, 4)}
+    sv.close()
+    return {"workload": wl["desc"], "value": world * 1000.0 / ms, "unit": "solves/s",
+            "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "refinements": rep["refinements"], "relres": rep["relres"], "kernels": kern}
 
 
 def run_batched(args, wl):
@@ -593,7 +692,7 @@ def main():
 # refinements a full solve of each workload takes (identical for the oracle
 # and the CUDA path, which agree bit for bit); used only to extrapolate the
 # reference arm's bounded sample
-REFINEMENTS = {"cfg1": 6, "cfg0": 9}
+REFINEMENTS = {"cfg1": 6, "cfg0": 9, "cfg4": 4}
 
 if __name__ == "__main__":
     main()

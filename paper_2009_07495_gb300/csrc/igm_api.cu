@@ -302,13 +302,16 @@ static void permute_host(int n, const int *rp, const int *cl, const double *v,
   }
 }
 
-// Rows per substitution chunk.  At least the bandwidth of the triangular
-// factors, so that every chunk depends on its predecessor only, and a
-// multiple (two or more) of the matrix's row period P (for a natural-order
-// stencil the grid plane, N^2 in 3D), so that chunks start on plane
-// boundaries: then a chunk's first rows need only early levels of the
-// previous chunk and consecutive chunks pipeline; at least 1024 rows; with a
-// bandwidth too large for that (fewer than 8 chunks), about one chunk per SM.
+// Rows per substitution chunk.  A multiple of the matrix's row period P (for
+// a natural-order stencil the grid plane, N^2 in 3D), so that chunks start
+// on plane boundaries: then a chunk's first rows need only early levels of
+// the previous chunk and consecutive chunks pipeline; at least 1024 rows.
+// The set-up first tries `periods` planes per chunk (2 for rows of up to 8
+// dependencies, 1 for longer ones: measured best on 7- and 27-point grids of
+// 128^3 and 200^3) and keeps it when every chunk reads only its predecessor;
+// otherwise the chunk is at least the factors' bandwidth, which guarantees
+// that.  With a bandwidth too large for that (fewer than 8 chunks), about one
+// chunk per SM.
 // The row period of a banded matrix: among 64 rows spread over the middle
 // half, the one with the most dependencies farther than half the lower
 // bandwidth gives the median of those far offsets (N^2 for 7- and 27-point 3D
@@ -335,18 +338,22 @@ int row_period(int n, const int *rp, const int *cl, int bw) {
   return best[best.size() / 2];
 }
 
-int auto_chunk(int n, int bw, int P) {
+// periods: rows per chunk in periods (planes) when the chunks only need to
+// read their predecessor (checked by the caller), 0 for the bandwidth rule
+int auto_chunk(int n, int bw, int P, int periods) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long r;
   if (P < 1 || P > bw) P = bw;
   if (bw >= 1 && (long long)bw * 8 <= n) {
-    // two periods (planes) per chunk at least: fewer chunk hand-offs on the
-    // critical path, groups still narrow (measured best on 7- and 27-point
-    // grids of 128^3 and 200^3)
-    r = 2 * P;
-    while (r < bw || r < 1024) r += P;
+    if (periods > 0) {
+      r = (long long)periods * P;
+      while (r < 1024) r += P;
+    } else {
+      r = P;
+      while (r < bw || r < 1024) r += P;
+    }
   } else {
     r = ((long long)n + sms - 1) / sms;
     r = (r + 1023) / 1024 * 1024;
@@ -687,18 +694,34 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
     CKH(cudaMemcpyAsync(hbw, bwd, sizeof(hbw), cudaMemcpyDeviceToHost, s));
     CKH(cudaStreamSynchronize(s));
     const int bw = std::max(hbw[0], hbw[1]);
-    R = params->trsv_chunk > 0 ? params->trsv_chunk : auto_chunk(n, bw, row_period(n, rp, cl, hbw[0]));
-    nch = (n + R - 1) / R;
     // single: every chunk of both factors reads only itself and its
     // predecessor (exact check over all dependencies)
-    {
+    auto reads_pred_only = [&](int Rc, int &res) -> igm_status {
       int hcd[2] = {0, 0};
-      CKH(cudaMemsetAsync(bwd, 0, 2 * sizeof(int), s));
-      launch_chunkdist(n, rp, cl, dp, 1, R, bwd, s);
-      launch_chunkdist(n, rp, cl, dp, 0, R, bwd + 1, s);
-      CKH(cudaMemcpyAsync(hcd, bwd, sizeof(hcd), cudaMemcpyDeviceToHost, s));
-      CKH(cudaStreamSynchronize(s));
-      single = std::max(hcd[0], hcd[1]) <= 1 ? 1 : 0;
+      CK(cudaMemsetAsync(bwd, 0, 2 * sizeof(int), s));
+      launch_chunkdist(n, rp, cl, dp, 1, Rc, bwd, s);
+      launch_chunkdist(n, rp, cl, dp, 0, Rc, bwd + 1, s);
+      CK(cudaMemcpyAsync(hcd, bwd, sizeof(hcd), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      res = std::max(hcd[0], hcd[1]) <= 1 ? 1 : 0;
+      return IGM_OK;
+    };
+    if (params->trsv_chunk > 0) {
+      R = params->trsv_chunk;
+    } else {
+      const int P = row_period(n, rp, cl, hbw[0]);
+      R = auto_chunk(n, bw, P, std::max(hbw[2], hbw[3]) > 8 ? 1 : 2);
+      int ok = 0;
+      if (reads_pred_only(R, ok) != IGM_OK) {
+        int_gmres_destroy(h);
+        return IGM_ECUDA;
+      }
+      if (!ok) R = auto_chunk(n, bw, P, 0);
+    }
+    nch = (n + R - 1) / R;
+    if (reads_pred_only(R, single) != IGM_OK) {
+      int_gmres_destroy(h);
+      return IGM_ECUDA;
     }
     // the predecessor copies read up to one position past the last (their
     // 16-byte rounding)

@@ -95,6 +95,21 @@ __device__ __forceinline__ u64 udiv_magic(u64 n, u64 d, u64 m) {
   return (t + ((n - t) >> (l < 1 ? l : 1))) >> (l > 1 ? l - 1 : 0);
 }
 
+// the same with l = ceil_log2_u64(|d|) given (precomputed with m)
+__device__ __forceinline__ u64 udiv_magic_l(u64 n, u64 m, int l) {
+  const u64 t = __umul64hi(m, n);
+  return (t + ((n - t) >> (l < 1 ? l : 1))) >> (l > 1 ? l - 1 : 0);
+}
+
+// a / d truncated toward zero for d != 0, m = magic_u64(|d|), l its shift:
+// the same result and events as divt
+__device__ __forceinline__ i64 divt_magic_l(i64 a, i64 d, u64 m, int l, unsigned &ev) {
+  ev += (a == INT64_MIN && d == -1);
+  const u64 ua = a < 0 ? 0ull - (u64)a : (u64)a;
+  const u64 uq = udiv_magic_l(ua, m, l);
+  return (i64)(((a < 0) != (d < 0)) ? 0ull - uq : uq);
+}
+
 // a / d truncated toward zero for d != 0, m = magic_u64(|d|): the same result
 // and events as divt
 __device__ __forceinline__ i64 divt_magic(i64 a, i64 d, u64 m, unsigned &ev) {

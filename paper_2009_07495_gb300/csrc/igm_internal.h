@@ -100,9 +100,15 @@ struct SysScal {
 
 // Packed block of one group of w rows (wp = w rounded up to a multiple of
 // 4), everything a row needs but its right-hand side and dependency values,
-// each array 16-byte aligned: codes [K][wp] int32, orders [wp] int32, bounds
-// [wp] int32, factors [K][wp] (fb bytes), diagonals [wp] (8 bytes),
-// division multipliers [wp] u64.
+// each array 16-byte aligned: codes [K][wp] int32, orders [wp] int32, row
+// words [wp] int32 (IGM_ROW_*), factors [K][wp] (fb bytes), diagonals [wp]
+// (8 bytes), division multipliers [wp] u64.
+// A row word: bits 0-6 hold 1 + the exactness bound (0: none), bits 8-14 the
+// shift of the division by the diagonal, bit 15 is set when a dependency of
+// the row is read late (code < 0).
+#define IGM_ROW_BOUND(wd) (((wd) & 0x7f) - 1)
+#define IGM_ROW_SHIFT(wd) (((wd) >> 8) & 0x7f)
+#define IGM_ROW_LATE 0x8000
 __host__ __device__ inline unsigned trsv_wp(int w) { return ((unsigned)(w < 1 ? 1 : w) + 3u) & ~3u; }
 __host__ __device__ inline unsigned trsv_blk_bytes(unsigned wp, int K, int fb) {
   const unsigned k = (unsigned)(K < 0 ? 0 : K);

@@ -152,9 +152,10 @@ __global__ void s_facmax(int n, const int *rowptr, const int *diagpos, int lower
 // chunk-local position mod ring; values of the previous chunk (single = 1,
 // every dependency in this chunk or the previous one) at ring + their
 // position mod pring; padding at the zero (ring + pring); the rest as late
-// reads.  Factors as int32 when fac32.  Bound: with S = sum_q |fac_q| of the
-// row, every |y_q| <= 2^bound keeps each product and the sum below 2^62 in
-// magnitude (62 - bit length of S; -1 when no such bound exists).  blobd
+// reads.  Factors as int32 when fac32.  The row word (IGM_ROW_*): the bound
+// (with S = sum_q |fac_q| of the row, every |y_q| <= 2^bound keeps each
+// product and the sum below 2^62 in magnitude: 62 - bit length of S, none
+// when no such bound exists), the division shift, the late flag.  blobd
 // (FP64 comparison solver, may be NULL): the same rows with FP64 factors
 // and diagonals (1 for the unit lower factor), offsets boffd.
 __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diagpos, int lower,
@@ -183,6 +184,7 @@ __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diag
     const int k1 = lower ? diagpos[i] : rowptr[i + 1];
     const int cnt = k1 - k0;
     u128 sabs = 0;
+    bool late = false;
     for (int q = 0; q < K; ++q) {
       int code = zero;
       i64 fv = 0;
@@ -196,6 +198,7 @@ __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diag
         fv = fac[k];
         if (f) fd = f[k];
         sabs += (u128)(fv < 0 ? 0ull - (u64)fv : (u64)fv);
+        late |= code < 0;
       }
       bcode[(size_t)q * wp + r] = code;
       if (fac32) reinterpret_cast<int *>(bfac)[(size_t)q * wp + r] = (int)fv;
@@ -208,14 +211,16 @@ __global__ void s_pack(int n, const int *rowptr, const int *col, const int *diag
     int bl = 0;  // bit length of sabs
     while (bl < 127 && (sabs >> bl) != 0) ++bl;
     bord[r] = i;
-    byb[r] = 62 - bl < -1 ? -1 : 62 - bl;
     const i64 dg = lower ? ldiag[i] : udiag[i];
+    const u64 adg = dg < 0 ? 0ull - (u64)dg : (u64)dg;
+    const int bound = 62 - bl < -1 ? -1 : 62 - bl;
+    byb[r] = (bound + 1) | (ceil_log2_u64(adg) << 8) | (late ? IGM_ROW_LATE : 0);
     bdiag[r] = dg;
-    bdm[r] = dg == 0 ? 0 : magic_u64(dg < 0 ? 0ull - (u64)dg : (u64)dg);
+    bdm[r] = dg == 0 ? 0 : magic_u64(adg);
     if (based) {
       int *dord = reinterpret_cast<int *>(based) + (size_t)K * wp;
       dord[r] = i;
-      dord[wp + r] = -1;
+      dord[wp + r] = late ? IGM_ROW_LATE : 0;
       double *ddg = reinterpret_cast<double *>(based + (size_t)(4 * K + 8) * wp + (size_t)8 * K * wp);
       ddg[r] = lower ? 1.0 : f[diagpos[i]];
       reinterpret_cast<u64 *>(ddg + wp)[r] = 0;
@@ -707,10 +712,15 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
       const V *srhs = reinterpret_cast<const V *>(blk + Ly.szBlk);
       for (int r = tid; r < w; r += IGM_TRSV_NC) {
         const int row = sord[r];
+        const int wd = syb[r];
+        // rows whose dependencies are all in shared memory (the common case)
+        // fetch them without branches, so all the loads issue together
+        const bool onchip = (wd & IGM_ROW_LATE) == 0;
         auto dep = [&](int q) -> V {
           const int code = scode[(size_t)q * wp + r];
           return code >= 0 ? vals[code] : late(code);
         };
+        auto dep_on = [&](int q) -> V { return vals[scode[(size_t)q * wp + r]]; };
         auto fac = [&](int q) -> i64 {
           return f32 ? (i64)reinterpret_cast<const int *>(sfac)[(size_t)q * wp + r]
                      : reinterpret_cast<const i64 *>(sfac)[(size_t)q * wp + r];
@@ -719,18 +729,24 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
         if (KIND == TK_INT) {
           i64 yv[KC], fv[KC];
           u64 mag = 0;  // the largest |y| (as y ^ (y >> 63))
+          if (onchip) {
+#pragma unroll
+            for (int q = 0; q < KC; ++q) yv[q] = q < K ? (i64)dep_on(q) : 0;
+          } else {
+#pragma unroll
+            for (int q = 0; q < KC; ++q) yv[q] = q < K ? (i64)dep(q) : 0;
+          }
 #pragma unroll
           for (int q = 0; q < KC; ++q) {
-            yv[q] = q < K ? (i64)dep(q) : 0;
             fv[q] = q < K ? fac(q) : 0;
             mag |= (u64)(yv[q] ^ (yv[q] >> 63));
           }
           for (int q = KC; q < K; ++q) {
-            const i64 v = (i64)dep(q);
+            const i64 v = onchip ? (i64)dep_on(q) : (i64)dep(q);
             mag |= (u64)(v ^ (v >> 63));
           }
           const i64 rhs = (i64)srhs[r];
-          const int yb = syb[r];
+          const int yb = IGM_ROW_BOUND(wd);
           i64 num;
           if (yb >= 0 && (mag >> yb) == 0) {
             // every product and the sum are below 2^62 (the set-up's bound):
@@ -739,21 +755,23 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
             i64 sum = 0;
 #pragma unroll
             for (int q = 0; q < KC; ++q) sum += fv[q] * yv[q];
-            for (int q = KC; q < K; ++q) sum += fac(q) * (i64)dep(q);
+            for (int q = KC; q < K; ++q)
+              sum += fac(q) * (onchip ? (i64)dep_on(q) : (i64)dep(q));
             num = (i64)((u64)rhs - (u64)sum);
             ev += (((rhs ^ sum) & (rhs ^ num)) < 0);
           } else {
             i128 sum = 0;
 #pragma unroll
             for (int q = 0; q < KC; ++q) sum += (i128)mulw(fv[q], yv[q], ev);
-            for (int q = KC; q < K; ++q) sum += (i128)mulw(fac(q), (i64)dep(q), ev);
+            for (int q = KC; q < K; ++q)
+              sum += (i128)mulw(fac(q), onchip ? (i64)dep_on(q) : (i64)dep(q), ev);
             const i128 acc = (i128)rhs - sum;
             ev += out64(acc);
             num = wrap(acc);
           }
           const i64 dg = reinterpret_cast<const i64 *>(sdg)[r];
           const u64 dm = reinterpret_cast<const u64 *>(sdg)[(size_t)wp + r];
-          y = (V)divt_magic(num, dg, dm, ev);
+          y = (V)divt_magic_l(num, dg, dm, IGM_ROW_SHIFT(wd), ev);
         } else {
           // FP64: subtract in CSR order (L packed ascending, U descending);
           // padding subtracts an exact zero
@@ -764,7 +782,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
           double acc = (double)srhs[r];
           for (int k = 0; k < K; ++k) {
             const int q = lower ? k : K - 1 - k;
-            acc = __dsub_rn(acc, __dmul_rn(facd(q), (double)dep(q)));
+            acc = __dsub_rn(acc, __dmul_rn(facd(q), (double)(onchip ? dep_on(q) : dep(q))));
           }
           if (KIND == TK_FP && lower) {
             y = (V)acc;  // unit lower factor
