@@ -112,9 +112,10 @@ typedef struct {
   /* Launch-configuration knobs (the results do not depend on them; tests use
      them to reach every code path on small systems). */
   int mgs_wmax;  /* rows of w one CTA of the Arnoldi step (lines 6-11) may
-                    keep in shared memory: 0 automatic (20,480), -1 none (w
-                    stays in global memory), k > 0 at most k rows.  In a
-                    batch the first system's value applies.               */
+                    keep in shared memory: 0 automatic (26,624), -1 none (w
+                    stays in global memory), k > 0 at most k rows; a CTA's
+                    further rows keep w in global memory.  In a batch the
+                    first system's value applies.                         */
   int wait_us;   /* bound of each device wait of the line-1'/5' substitutions
                     in microseconds (0: 1 s); an expired wait ends the call
                     with IGM_ETIMEOUT                                      */

@@ -99,21 +99,21 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   int maxg = persistent_grid(ST);
   std::vector<int> sysn(ns);
   for (int s = 0; s < ns; ++s) sysn[s] = hs[s]->n;
-  int mgs_g = 1, mgs_wrows = 0;
+  int mgs_g = 1, mgs_wrows = 0, mgs_rows = 0;
   std::vector<int> mptr;
   std::vector<Tile> mseg;
   std::vector<int> sys_seg;
   mgs_plan(sysn, persistent_grid(1 << 30), hs[0]->prm.mgs_wmax, mgs_g, mptr, mseg, mgs_wrows,
-           sys_seg);
+           mgs_rows, sys_seg);
   const int MS = (int)mseg.size();
-  int *d_mptr, *d_sysseg;
+  int *d_mptr, *d_sysseg, *d_mact;
   Tile *d_mseg;
   long long *d_mh;
   u64 *d_mpart;
   b->arena.want(&d_tiles, T);
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
   b->arena.want(&d_stiles, ST);
-  b->arena.want(&d_bar, 2);
+  b->arena.want(&d_bar, 4);
   b->arena.want(&d_cpart, 3 * (size_t)maxg * ns);
   b->arena.want(&d_snt, ns);
   b->arena.want(&d_sp, ns);
@@ -124,7 +124,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   b->arena.want(&d_mptr, mgs_g + 1);
   b->arena.want(&d_mseg, MS > 0 ? MS : 1);
   b->arena.want(&d_mh, MS > 0 ? MS : 1);
-  b->arena.want(&d_mpart, 4 * (size_t)(MS > 0 ? MS : 1));
+  b->arena.want(&d_mpart, 8 * (size_t)(MS > 0 ? MS : 1));
+  b->arena.want(&d_mact, MS > 0 ? MS : 1);
   b->arena.want(&d_sysseg, ns + 1);
   if (b->arena.commit() != cudaSuccess) {
     cudaGetLastError();
@@ -138,7 +139,8 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   CK(cudaMemcpy(d_sp, sp.data(), sizeof(SysDev *) * ns, cudaMemcpyHostToDevice));
   CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
   CK(cudaMemset(d_nact, 0, sizeof(int)));
-  CK(cudaMemset(d_bar, 0, 2 * sizeof(unsigned)));
+  CK(cudaMemset(d_bar, 0, 4 * sizeof(unsigned)));
+  CK(cudaMemset(d_mpart, 0, 8 * sizeof(u64) * (size_t)(MS > 0 ? MS : 1)));
   CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (mgs_g + 1), cudaMemcpyHostToDevice));
   if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sysseg, sys_seg.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
@@ -166,8 +168,10 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.mseg_h = d_mh;
   B.nseg = MS;
   B.mpart = d_mpart;
+  B.mseg_act = d_mact;
   B.sys_seg = d_sysseg;
   B.mgs_wrows = mgs_wrows;
+  B.mgs_rows = mgs_rows;
   B.trsv_maxk = maxk;
   B.max_colors = max_colors;
   B.max_ns = 0;
@@ -518,6 +522,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   int *rp, *cl, *dp, *lfl = nullptr, *ufl = nullptr;
   double *ahat, *a, *dd, *f = nullptr, *b, *bh, *xt, *r, *t, *xk, *yfp;
   i64 *abar, *fac = nullptr, *ld = nullptr, *ud = nullptr, *w, *yv, *V, *H, *cs, *sn, *g;
+  int *V32;
   int *bwd = nullptr;
   size_t nz = nnz > 0 ? nnz : 1;
   // the row pointers on the host: checked here (monotone, 0 .. nnz) and used
@@ -585,6 +590,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   A.want(&w, n);
   A.want(&yv, n);
   A.want(&V, (size_t)(m + 1) * n);
+  A.want(&V32, (size_t)(m + 1) * n);
   A.want(&H, (size_t)(m + 1) * m);
   A.want(&cs, m);
   A.want(&sn, m);
@@ -973,6 +979,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   d.w = w;
   d.yv = yv;
   d.V = V;
+  d.V32 = V32;
   d.H = H;
   d.cs = cs;
   d.sn = sn;
@@ -985,6 +992,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   CKH(cudaMemcpyAsync(&h->d_sc->seq, &seq0, sizeof(int), cudaMemcpyHostToDevice, s));
   CKH(cudaMemsetAsync(H, 0, sizeof(i64) * (size_t)(m + 1) * m, s));
   CKH(cudaMemsetAsync(V, 0, sizeof(i64) * (size_t)(m + 1) * n, s));
+  CKH(cudaMemsetAsync(V32, 0, sizeof(int) * (size_t)(m + 1) * n, s));
   CKH(cudaStreamSynchronize(s));
   igm_status bs = build_batch({h}, &h->solo);
   if (bs) {
@@ -1061,7 +1069,7 @@ long long handle_bytes_estimate(int n, int nnz, const igm_params *p) {
   r += 12 * Z + 12 * N + N / 4 + 8;                 // SELL-32 copy of abar (estimate)
   r += (long long)p->s * (16 * Z + 8 * N) + (p->s > 0 ? 8 * Z : 0);  // correction terms
   if (p->precond) r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
-  r += 8 * N * 8 + 8 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
+  r += 8 * N * 8 + 12 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
   return r + 64 * 256 + (long long)sizeof(SysScal) + sizeof(SysDev);
 }
 

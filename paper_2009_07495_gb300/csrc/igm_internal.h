@@ -62,6 +62,8 @@ struct SysScal {
   int retries;             // inner solves discarded so far
   int retry;               // 1: the inner solve that just ran is discarded
   int beta[5];             // their shifts in use (a copy of SysDev::p)
+  int vwide;               // a basis entry of this inner solve left int32:
+                           // readers use the int64 copy of the basis
 };
 
 // Schedule and packed data of one triangular factor.  Positions p = 0..n-1
@@ -195,6 +197,7 @@ struct SysDev {
   int *lflag, *uflag;           // per-row ready flags (set-up, line 1' none)
   double *b, *bh, *xt, *r, *t, *xk;
   i64 *w, *yv, *V;
+  int *V32;                     // the basis as int32 words (read unless sc->vwide)
   i64 *xbuf;                    // substitution results in position order
   i64 *H, *cs, *sn, *g;
   double *yfp;
@@ -223,7 +226,9 @@ struct BatchDev {
   double *partd;           // ntiles
   unsigned *ticket;        // 4 dynamic-ticket counters
   int *nact;               // systems still refining
-  unsigned *bar;           // grid barrier: [0] arrivals, [1] generation
+  unsigned *bar;           // grid barrier: [0] arrivals, [1] generation;
+                           // integer Arnoldi step: [2] launch epoch, [3]
+                           // CTAs finished in this launch
   double *cpart;           // 3 slots x maxG x nsys FP64 per-CTA partials
   int maxg;                // CTAs of the persistent kernels
   // integer Arnoldi step: CTA c sweeps the segments
@@ -234,10 +239,13 @@ struct BatchDev {
   const Tile *mseg;
   i64 *mseg_h;             // per segment: the coefficient of the next pass
   int nseg;                // segments in all
-  u64 *mpart;              // 2 slots (pass parity) x nseg {lo, hi}: a pass's
-                           // exact int128 sum over each segment
+  u64 *mpart;              // 2 slots (pass parity) x nseg x 4 words: a
+                           // pass's exact sum over each segment, tagged
+  int *mseg_act;           // per segment beyond a CTA's descriptor cache:
+                           // active | narrow << 1 at the launch's start
   const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
-  int mgs_wrows;           // rows of w each CTA keeps in shared memory (0: global)
+  int mgs_wrows;           // rows each CTA keeps resident in shared memory
+  int mgs_rows;            // most rows of a CTA
   int trsv_maxk;           // most strict entries of one factor row
   int max_ns;              // most correction terms of eq. (AA) of a system
   int max_colors;          // most colours of a multicolour-ordered system

@@ -10,6 +10,7 @@
 // memory.  Small batches (every row in one CTA) run a one-CTA variant
 // without the grid barrier.
 #include <algorithm>
+#include <type_traits>
 
 #include "igm_dev.cuh"
 #include "igm_launch.h"
@@ -92,35 +93,52 @@ __device__ __forceinline__ void mgs_cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// a pass's int128 sum over one segment: 2 slots (pass parity) x segments
-__device__ __forceinline__ u64 *mpart_at(const BatchDev &B, int i, int g) {
-  return B.mpart + 2 * ((size_t)(i & 1) * B.nseg + g);
-}
-
-// an int128 {lo, hi} pair (16-byte aligned) read from L2
-__device__ __forceinline__ i128 acc_load(const u64 *a) {
-  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(a));
-  return (i128)(((u128)v.y << 64) | (u128)v.x);
-}
-
 __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
   return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
 }
 
 #define IGM_RPT 4           // rows in flight per thread
-#define IGM_MSEG_CACHE 64   // segment descriptors a CTA keeps in shared memory
-#define IGM_MGS_WMAX 20480  // rows of w a CTA may keep in shared memory (160 KB)
+#define IGM_MSEG_CACHE 64   // segments of the one-CTA mode (descriptors in shared memory)
+#define IGM_MGS_GCACHE 32   // segment descriptors a CTA of the grid mode keeps in shared memory
+// CTA rows of the grid mode resident in shared memory: w (int64) and two
+// int32 basis vectors, 16 bytes a row (220 KB)
+#define IGM_MGS_WMAX 14080
+#define IGM_MGS_ROWB 16
 
-// the step kernel's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows
-// in all, each system one segment of it (ns segments), every segment
-// descriptor cached in shared memory
+// L2 eviction priorities for the rows of w that live in global memory: kept
+// (evict_last) from pass to pass, dropped (evict_first) at their last read
+__device__ __forceinline__ u64 l2_policy_keep() {
+  u64 p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ u64 l2_policy_drop() {
+  u64 p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ i64 ld_l2hint(const i64 *a, u64 pol) {
+  i64 v;
+  asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_l2hint(i64 *a, i64 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol)
+               : "memory");
+}
+
+// the step's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows in
+// all, every row of w in shared memory, each system one segment of it (ns
+// segments), every segment descriptor cached in shared memory
 __host__ __device__ __forceinline__ bool mgs_one_cta(const BatchDev &B, int ns) {
-  return B.mgs_g == 1 && B.mgs_wrows > 0 && B.mgs_wrows <= IGM_MGS_BLOCK && ns <= IGM_MSEG_CACHE;
+  return B.mgs_g == 1 && B.mgs_rows > 0 && B.mgs_rows <= IGM_MGS_BLOCK &&
+         B.mgs_wrows == B.mgs_rows && ns <= IGM_MSEG_CACHE;
 }
 
 // a segment as the step kernel sees it: its system's arrays and shifts
 struct MSegC {
-  i64 *V;  // basis of the system
+  i64 *V;        // basis of the system
+  int *V32;      // the same as int32 words
   i64 *w;        // the segment's first row of w
   i64 *H;
   SysScal *sc;
@@ -128,6 +146,7 @@ struct MSegC {
   int df, b7, b8, b10, b11a, b11b;
   int first;   // holds row 0 of its system: records h_{i,j} and its events
   int active;  // the system takes this step
+  int narrow;  // every basis entry of this inner solve fits int32 so far
 };
 
 __device__ __forceinline__ void mseg_make(const BatchDev &B, int g, int j, MSegC &c) {
@@ -135,6 +154,7 @@ __device__ __forceinline__ void mseg_make(const BatchDev &B, int g, int j, MSegC
   const SysDev *s = B.sys[t.sys];
   const SysParams &P = s->p;
   c.V = s->V;
+  c.V32 = s->V32;
   c.w = s->w + t.row0;
   c.H = s->H;
   c.sc = s->sc;
@@ -152,6 +172,7 @@ __device__ __forceinline__ void mseg_make(const BatchDev &B, int g, int j, MSegC
   c.b11b = P.b11b;
   c.first = t.row0 == 0;
   c.active = m_step(s, j);
+  c.narrow = s->sc->vwide == 0;
 }
 
 // after the barrier of pass i: the exact total of the pass; h_{i,j} (line 7)
@@ -181,219 +202,442 @@ __device__ __forceinline__ void givens_tail(const BatchDev &B, const MSegC &c, i
   givens_col(s, c.sc, j, hj1);
 }
 
-// the exact total of pass i over every segment of c's system, summed by one
-// warp from the segments' sums (valid in lane 0)
-__device__ __forceinline__ i128 mseg_sum(const BatchDev &B, const MSegC &c, int i) {
-  const int lane = threadIdx.x & 31;
-  const int lo = B.sys_seg[c.sys], hi = B.sys_seg[c.sys + 1];
-  i128 t = 0;
-  // up to 256 segments per round, all loads in flight together
-  for (int g0 = lo + lane; g0 < hi; g0 += 32 * 8) {
-    i128 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int g = g0 + 32 * u;
-      v[u] = g < hi ? acc_load(mpart_at(B, i, g)) : (i128)0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t += v[u];
-  }
-  return warp_sum_i128(t);
-}
+// ---------------------------------------------------------------------------
+// one-CTA mode
+// ---------------------------------------------------------------------------
 
-// Every CTA owns the same rows in every pass (a balanced partition of all
-// systems' rows, planned on the host); when they fit, its rows of w stay in
-// shared memory from pass 0 to line 11, so a pass reads only the two basis
-// vectors it needs (v_i from HBM, v_{i-1} mostly from L2).
-template <bool ONE>
-__global__ void __launch_bounds__(ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK, 1)
-    k_mgs_step(BatchDev B, int j) {
-  constexpr int BS = ONE ? IGM_MGS_ONE_BLOCK : IGM_MGS_BLOCK;  // threads
-  extern __shared__ i64 sw[];  // this CTA's rows of w (B.mgs_wrows > 0)
-  __shared__ MSegC s_seg[IGM_MSEG_CACHE + 1];
+// One CTA of IGM_MGS_ONE_BLOCK threads holds every row of every system
+// (small batches, mgs_one_cta): each system is one segment of it, w stays in
+// shared memory, the pass totals stay in shared memory and a block barrier
+// ends each pass; the basis vectors are staged in shared memory (v_{i+1}
+// copied asynchronously during pass i, so no pass waits on a global load).
+__global__ void __launch_bounds__(IGM_MGS_ONE_BLOCK, 1) k_mgs_one(BatchDev B, int j) {
+  constexpr int BS = IGM_MGS_ONE_BLOCK;
+  extern __shared__ i64 sw[];  // every row of w
+  __shared__ MSegC s_seg[IGM_MSEG_CACHE];
   __shared__ i64 s_h[IGM_MSEG_CACHE];
-  __shared__ i128 s_tot[ONE ? IGM_MSEG_CACHE : 1];   // pass totals (one-CTA mode)
-  __shared__ i64 s_v[ONE ? 3 : 1][ONE ? IGM_MGS_BLOCK : 1];  // v_{i-1}, v_i, v_{i+1}
-  unsigned *err0 = &B.sys[0]->sc->err;
-  const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
-  const bool wsm = B.mgs_wrows > 0;
-  // ONE: one CTA of IGM_MGS_ONE_BLOCK threads holds every row of every
-  // system (small systems, mgs_one_cta): each system is one segment of it,
-  // its pass totals stay in shared memory, a block barrier replaces the grid
-  // barrier, the basis vectors are staged in shared memory (v_{i+1} copied
-  // asynchronously during pass i, so no pass waits on a global load); fewer
-  // threads keep the per-pass reductions short
-  constexpr bool one = ONE;
-  for (int k = threadIdx.x; k < ns && k < IGM_MSEG_CACHE; k += blockDim.x)
-    mseg_make(B, g0 + k, j, s_seg[k]);
+  __shared__ i128 s_tot[IGM_MSEG_CACHE];
+  __shared__ i64 s_v[3][IGM_MGS_BLOCK];  // v_{i-1}, v_i, v_{i+1}
+  const int ns = B.mseg_ptr[1];
+  for (int k = threadIdx.x; k < ns; k += BS) mseg_make(B, k, j, s_seg[k]);
   __syncthreads();
-  // one-CTA mode: stage v_i into s_v[i % 3] (i <= j)
+  // stage v_i into s_v[i % 3]
   auto stage = [&](int i) {
     for (int k = 0; k < ns; ++k) {
       const MSegC &c = s_seg[k];
       if (!c.active) continue;
       const i64 *src = c.V + (size_t)i * c.n + c.row0;
       i64 *dst = &s_v[i % 3][c.off];
-      for (int q = threadIdx.x; q < c.nrows; q += blockDim.x) mgs_cp_async8(dst + q, src + q);
+      for (int q = threadIdx.x; q < c.nrows; q += BS) mgs_cp_async8(dst + q, src + q);
     }
     mgs_cp_async_commit();
   };
-  if (one) {
-    stage(0);
-    mgs_cp_async_wait_all();
-    __syncthreads();
-  }
+  stage(0);
+  mgs_cp_async_wait_all();
+  __syncthreads();
   for (int i = 0; i <= j + 1; ++i) {
-    if (one && i + 1 <= j) stage(i + 1);
-    // grid mode: pull this CTA's rows of v_{i+1} into L2 while pass i runs
-    // and waits at its barrier, so pass i+1 streams them from L2
-    if (!one && i + 1 <= j)
-      for (int k = 0; k < ns && k < IGM_MSEG_CACHE; ++k) {
-        const MSegC &c = s_seg[k];
-        if (!c.active) continue;
-        const char *base = (const char *)(c.V + (size_t)(i + 1) * c.n + c.row0);
-        const size_t bytes = (size_t)c.nrows * sizeof(i64);
-        for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
-      }
+    if (i + 1 <= j) stage(i + 1);
     for (int k = 0; k < ns; ++k) {
-      if (k >= IGM_MSEG_CACHE) {  // descriptor beyond the cache: one spare slot
-        __syncthreads();
-        if (threadIdx.x == 0) mseg_make(B, g0 + k, j, s_seg[IGM_MSEG_CACHE]);
-        __syncthreads();
-      }
-      const MSegC &c = s_seg[k < IGM_MSEG_CACHE ? k : IGM_MSEG_CACHE];
+      const MSegC &c = s_seg[k];
       if (!c.active) continue;
-      const i64 hs = i == 0 ? 0 : (k < IGM_MSEG_CACHE ? s_h[k] : B.mseg_h[g0 + k]);
+      const i64 hs = i == 0 ? 0 : s_h[k];
       const int nr = c.nrows;
-      const i64 *vp = one ? &s_v[(i + 2) % 3][c.off]
-                          : c.V + (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
-      const i64 *vi = one ? &s_v[i % 3][c.off] : c.V + (size_t)(i <= j ? i : 0) * c.n + c.row0;
-      i64 *wg = c.w, *ws = sw + c.off;
+      const i64 *vp = &s_v[(i + 2) % 3][c.off], *vi = &s_v[i % 3][c.off];
+      const i64 *wg = c.w;
+      i64 *ws = sw + c.off;
       const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
-      // line 8's coefficient as a 32-bit value when it fits: the product
-      // with a basis entry that fits too is one 32x32 -> 64-bit multiply,
-      // exact and never out of range (same word, no event)
       const bool hs32 = hs == (i64)(int)hs;
       i128 part = 0;
       unsigned evA = 0, evB = 0;
-      for (int q0 = threadIdx.x; q0 < nr; q0 += IGM_RPT * BS) {
-        // all loads of the thread's rows first (memory-level parallelism)
-        i64 wv[IGM_RPT], pv[IGM_RPT], qv[IGM_RPT];
-#pragma unroll
-        for (int u = 0; u < IGM_RPT; ++u) {
-          const int q = q0 + u * BS;
-          const bool ok = q < nr;
-          wv[u] = ok ? ((wsm && i > 0) ? ws[q] : wg[q]) : 0;
-          pv[u] = (ok && i > 0) ? vp[q] : 0;
-          qv[u] = (ok && i <= j) ? vi[q] : 0;
+      for (int q = threadIdx.x; q < nr; q += BS) {
+        i64 wl = i > 0 ? ws[q] : wg[q];
+        if (i > 0) {
+          const i64 pv = vp[q];
+          const i64 pr = (hs32 && pv == (i64)(int)pv) ? (i64)(int)hs * (i64)(int)pv
+                                                      : mulw(hs, pv, evB);
+          wl = subw(wl, pr >> s8, evB);
         }
-#pragma unroll
-        for (int u = 0; u < IGM_RPT; ++u) {
-          const int q = q0 + u * BS;
-          if (q >= nr) continue;
-          i64 wl = wv[u];
-          if (i > 0) {
-            const i64 pr = (hs32 && pv[u] == (i64)(int)pv[u])
-                               ? (i64)(int)hs * (i64)(int)pv[u]
-                               : mulw(hs, pv[u], evB);
-            wl = subw(wl, pr >> s8, evB);
-          }
-          if (wsm) ws[q] = wl;
-          else if (i > 0) wg[q] = wl;
-          // lines 7 / 10: a 32x32 -> 64-bit multiply when both factors fit
-          // (exact, never out of range: the same word, no event)
-          if (i <= j) {
-            const i64 a = wl >> s7, b = qv[u];
-            part += (i128)((a == (i64)(int)a && b == (i64)(int)b) ? (i64)(int)a * (i64)(int)b
-                                                                  : mulw(a, b, evA));
-          } else {
-            const i64 a = wl >> s10;
-            part += (i128)(a == (i64)(int)a ? (i64)(int)a * (i64)(int)a : mulw(a, a, evA));
-          }
+        ws[q] = wl;
+        if (i <= j) {
+          const i64 a = wl >> s7, b = vi[q];
+          part += (i128)((a == (i64)(int)a && b == (i64)(int)b) ? (i64)(int)a * (i64)(int)b
+                                                                : mulw(a, b, evA));
+        } else {
+          const i64 a = wl >> s10;
+          part += (i128)(a == (i64)(int)a ? (i64)(int)a * (i64)(int)a : mulw(a, a, evA));
         }
       }
       flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
       flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
       part = block_sum_i128(part);
-      if (threadIdx.x == 0) {
-        if (one) {
-          s_tot[k] = part;
-        } else {  // slot i & 1 was last read before barrier i-1
-          u64 *pp = mpart_at(B, i, g0 + k);
-          pp[0] = (u64)(u128)part;
-          pp[1] = (u64)((u128)part >> 64);
-        }
-      }
+      if (threadIdx.x == 0) s_tot[k] = part;
     }
-    if constexpr (ONE) {
-      __syncthreads();
-      for (int k = threadIdx.x; k < ns; k += blockDim.x)
-        if (s_seg[k].active) s_h[k] = mseg_coef(s_seg[k], s_tot[k], i, j);
-    } else {
-      if (!grid_sync(B.bar, err0)) return;
-      // one warp per segment: its system's total from all segment sums
-      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int k = wid; k < ns; k += BS / 32) {
-        if (k < IGM_MSEG_CACHE) {
-          if (!s_seg[k].active) continue;
-          const i128 tot = mseg_sum(B, s_seg[k], i);
-          if (lane == 0) s_h[k] = mseg_coef(s_seg[k], tot, i, j);
-        } else {
-          MSegC c;
-          mseg_make(B, g0 + k, j, c);
-          if (!c.active) continue;
-          const i128 tot = mseg_sum(B, c, i);
-          if (lane == 0) B.mseg_h[g0 + k] = mseg_coef(c, tot, i, j);
-        }
-      }
-    }
-    if (one) mgs_cp_async_wait_all();  // v_{i+1} is in place for pass i+1
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += BS)
+      if (s_seg[k].active) s_h[k] = mseg_coef(s_seg[k], s_tot[k], i, j);
+    mgs_cp_async_wait_all();  // v_{i+1} is in place for pass i+1
     __syncthreads();
   }
   // line 11 for every system whose divisor is non-zero
   for (int k = 0; k < ns; ++k) {
-    if (k >= IGM_MSEG_CACHE) {
-      __syncthreads();
-      if (threadIdx.x == 0) mseg_make(B, g0 + k, j, s_seg[IGM_MSEG_CACHE]);
-      __syncthreads();
-    }
-    const MSegC &c = s_seg[k < IGM_MSEG_CACHE ? k : IGM_MSEG_CACHE];
+    const MSegC &c = s_seg[k];
     if (!c.active) continue;
-    const i64 hn = k < IGM_MSEG_CACHE ? s_h[k] : B.mseg_h[g0 + k];
+    const i64 hn = s_h[k];
     if (shr(hn, c.b11b) == 0) continue;
     i64 *vn = c.V + (size_t)(j + 1) * c.n + c.row0;
-    const i64 *wg = c.w, *ws = sw + c.off;
+    int *vn32 = c.V32 + (size_t)(j + 1) * c.n + c.row0;
+    const i64 *ws = sw + c.off;
     unsigned ev = 0, evr = 0;
-    for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * BS) {
-      i64 wv[IGM_RPT];
-#pragma unroll
-      for (int u = 0; u < IGM_RPT; ++u) {
-        const int q = q0 + u * BS;
-        wv[u] = q < c.nrows ? (wsm ? ws[q] : wg[q]) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < IGM_RPT; ++u) {
-        const int q = q0 + u * BS;
-        if (q >= c.nrows) continue;
-        const i64 v = fx_div(wv[u], hn, c.b11a, c.b11b, c.df, ev);
-        evr += (v < INT32_MIN || v > INT32_MAX);
-        vn[q] = v;
-      }
+    for (int q = threadIdx.x; q < c.nrows; q += BS) {
+      const i64 v = fx_div(ws[q], hn, c.b11a, c.b11b, c.df, ev);
+      evr += (v < INT32_MIN || v > INT32_MAX);
+      vn[q] = v;
+      vn32[q] = (int)v;
     }
     flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
+    if (__syncthreads_or(evr != 0) && threadIdx.x == 0) atomicOr(&c.sc->vwide, 1);
     flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
   }
-  // lines 10 (store) and 12-19, one thread per system, after line 11: the
-  // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
+  // lines 10 (store) and 12-19, one thread per system
   __syncthreads();
+  for (int k = threadIdx.x; k < ns; k += BS)
+    if (s_seg[k].active && s_seg[k].first) givens_tail(B, s_seg[k], j, s_h[k]);
+}
+
+// ---------------------------------------------------------------------------
+// grid mode
+// ---------------------------------------------------------------------------
+
+// The exact sum of a pass over one segment travels as three 64-bit words,
+// each (32 bits of the sum << 32) | tag, tag = (launch epoch << 8) | (pass
+// + 1): a word is read whole or not at all (single-copy atomicity of aligned
+// 64-bit accesses), so a reader that sees the current tag in all three has
+// the sum, with no fence and no barrier.  |sum| < 2^95 (at most 2^31 rows of
+// int64 products), so 96 bits hold it.  Slot of segment g for pass parity
+// p: 4 words (32-byte aligned) at mpart[(p * nseg + g) * 4].
+__device__ __forceinline__ u64 *mslot(const BatchDev &B, int par, int g) {
+  return B.mpart + ((size_t)par * B.nseg + g) * 4;
+}
+
+__device__ __forceinline__ void mslot_put(u64 *sl, i128 v, unsigned tag) {
+  const u128 u = (u128)v;
+  const u64 w0 = ((u64)(unsigned)u << 32) | tag;
+  const u64 w1 = ((u64)(unsigned)(u >> 32) << 32) | tag;
+  const u64 w2 = ((u64)(unsigned)(u >> 64) << 32) | tag;
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(sl), "l"(w0), "l"(w1)
+               : "memory");
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(sl + 2), "l"(w2) : "memory");
+}
+
+__device__ __forceinline__ void mslot_load(const u64 *sl, u64 &w0, u64 &w1, u64 &w2) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
+               : "=l"(w0), "=l"(w1)
+               : "l"(sl)
+               : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w2) : "l"(sl + 2) : "memory");
+}
+
+__device__ __forceinline__ i128 mslot_value(u64 w0, u64 w1, u64 w2) {
+  const i128 hi = (i128)(int)(unsigned)(w2 >> 32);
+  return (i128)(((u128)hi << 64) | ((u128)(w1 >> 32) << 32) | (u128)(w0 >> 32));
+}
+
+// The exact total of a pass over every segment of system `sys`, gathered
+// by the whole CTA from the segments' tagged slots, one slot per thread (a
+// system has at most one segment per CTA); valid in thread 0.  False (in
+// every thread) when a slot did not carry the tag within the wait bound or
+// a CTA has reported an expired wait.
+__device__ bool mseg_total(const BatchDev &B, int sys, int par, unsigned tag,
+                           const unsigned *err0, i128 &tot) {
+  const int lo = B.sys_seg[sys], hi = B.sys_seg[sys + 1];
+  i128 t = 0;
+  bool ok = true;
+  for (int g = lo + threadIdx.x; g < hi && ok; g += blockDim.x) {
+    for (int it = 0;; ++it) {
+      u64 w0, w1, w2;
+      mslot_load(mslot(B, par, g), w0, w1, w2);
+      if ((unsigned)w0 == tag && (unsigned)w1 == tag && (unsigned)w2 == tag) {
+        t += mslot_value(w0, w1, w2);
+        break;
+      }
+      if (it > IGM_SPIN_MAX || ((it & 255) == 255 && (ld_relaxed_u32(err0) & ERR_TIMEOUT))) {
+        ok = false;
+        break;
+      }
+      if (it > 32) __nanosleep(32);
+    }
+  }
+  tot = block_sum_i128(t);
+  return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ bool fits32(int) { return true; }
+__device__ __forceinline__ bool fits32(i64 x) { return x == (i64)(int)x; }
+
+// asynchronous 4-byte copy global -> shared (the resident basis rows)
+__device__ __forceinline__ void mgs_cp_async4(int *dst, const int *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+// Grid mode: every CTA owns the same rows in every pass (a balanced partition
+// of all systems' rows, planned on the host).  The first B.mgs_wrows of them
+// are resident in shared memory: w from pass 0 to line 11, and (while every
+// basis entry of the inner solve fits int32) the int32 words of v_{i-1} and
+// v_i in two buffers; v_{i+1} is copied into the buffer of v_{i-1} while
+// the pass's sums travel, each thread copying the rows it alone reads, so a
+// pass over resident rows reads nothing from global memory.  Further rows
+// keep w in global memory (held in L2 by eviction priority) and read the
+// basis from global memory.  There is no grid barrier: each CTA publishes
+// its tagged sum of the pass per segment and reads those of its systems'
+// segments, so a CTA waits only for the CTAs that share a system with it.
+__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j) {
+  constexpr int BS = IGM_MGS_BLOCK;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int S = B.mgs_wrows;  // resident rows of this CTA
+  i64 *sw = reinterpret_cast<i64 *>(smem);        // w of the resident rows
+  int *sv = reinterpret_cast<int *>(sw + S);      // 2 x S basis words
+  __shared__ MSegC s_seg[IGM_MGS_GCACHE + 1];  // + one slot for the others in turn
+  __shared__ i64 s_h[IGM_MGS_GCACHE];
+  __shared__ unsigned s_epoch;
+  __shared__ int s_fail;
+  unsigned *err0 = &B.sys[0]->sc->err;
+  const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
+  // descriptors; segments beyond the cache keep their step flags (taken
+  // now, before this CTA publishes anything) in mseg_act
   for (int k = threadIdx.x; k < ns; k += BS) {
-    if (k < IGM_MSEG_CACHE) {
-      if (s_seg[k].active && s_seg[k].first) givens_tail(B, s_seg[k], j, s_h[k]);
+    if (k < IGM_MGS_GCACHE) {
+      mseg_make(B, g0 + k, j, s_seg[k]);
     } else {
       MSegC c;
       mseg_make(B, g0 + k, j, c);
-      if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
+      B.mseg_act[g0 + k] = c.active | (c.narrow << 1);
+    }
+  }
+  if (threadIdx.x == 0) {
+    s_epoch = ld_relaxed_u32(B.bar + 2);
+    s_fail = 0;
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  // a segment's descriptor with the flags taken at the start (into c)
+  auto seg_make = [&](int k, MSegC &c) {
+    mseg_make(B, g0 + k, j, c);
+    const int f = B.mseg_act[g0 + k];
+    c.active = f & 1;
+    c.narrow = f >> 1;
+  };
+  // the descriptor of segment k in shared memory (all threads call it in
+  // step): beyond the cache, thread 0 builds it in the spare slot
+  auto seg = [&](int k) -> const MSegC & {
+    if (k < IGM_MGS_GCACHE) return s_seg[k];
+    __syncthreads();
+    if (threadIdx.x == 0) seg_make(k, s_seg[IGM_MGS_GCACHE]);
+    __syncthreads();
+    return s_seg[IGM_MGS_GCACHE];
+  };
+  // resident rows of a segment: w (qw) and the basis (qv: only while narrow)
+  auto res_w = [&](const MSegC &c) { return min(max(S - c.off, 0), c.nrows); };
+  auto res_v = [&](const MSegC &c) { return c.narrow ? res_w(c) : 0; };
+  // copy v_i of the resident rows into buffer i & 1 (each thread its rows)
+  auto stage = [&](int i) {
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      const int qv = res_v(c);
+      const int *src = c.V32 + (size_t)i * c.n + c.row0;
+      int *dst = sv + (size_t)(i & 1) * S + c.off;
+      for (int q = threadIdx.x; q < qv; q += BS) mgs_cp_async4(dst + q, src + q);
+    }
+    mgs_cp_async_commit();
+  };
+  stage(0);
+  for (int i = 0; i <= j + 1; ++i) {
+    const unsigned tag = (epoch << 8) | (unsigned)(i + 1);
+    mgs_cp_async_wait_all();  // this thread's rows of v_i are in place
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      const int nr = c.nrows, qw = res_w(c), qv = res_v(c);
+      // pull the global rows of v_{i+1} into L2 while this pass runs
+      if (i + 1 <= j) {
+        const size_t o = (size_t)(i + 1) * c.n + c.row0 + qv;
+        const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
+        const size_t bytes = (size_t)(nr - qv) * (c.narrow ? sizeof(int) : sizeof(i64));
+        for (size_t a = (size_t)threadIdx.x * 128; a < bytes; a += (size_t)BS * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(base + a));
+      }
+      const i64 hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
+      i64 *wg = c.w, *ws = sw + c.off;
+      const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
+      // line 8's coefficient as a 32-bit value when it fits: its product
+      // with a basis entry that fits too is one 32x32 -> 64-bit multiply,
+      // exact and never out of range (same word, no event)
+      const bool hs32 = hs == (i64)(int)hs;
+      i128 part = 0;
+      unsigned evA = 0, evB = 0;
+      // line 8 (i > 0) and the line-7 (i <= j) or line-10 (i = j + 1) term of
+      // one row; returns the updated w
+      auto row = [&](i64 wl, auto pv, auto qvv) -> i64 {
+        if (i > 0) {
+          const i64 pr = (hs32 && fits32(pv)) ? (i64)(int)hs * (i64)(int)pv
+                                              : mulw(hs, (i64)pv, evB);
+          wl = subw(wl, pr >> s8, evB);
+        }
+        if (i <= j) {
+          const i64 a = wl >> s7;
+          part += (i128)((fits32(a) && fits32(qvv)) ? (i64)(int)a * (i64)(int)qvv
+                                                    : mulw(a, (i64)qvv, evA));
+        } else {
+          const i64 a = wl >> s10;
+          part += (i128)(fits32(a) ? (i64)(int)a * (i64)(int)a : mulw(a, a, evA));
+        }
+        return wl;
+      };
+      // resident rows: everything in shared memory (w from global at pass 0)
+      {
+        const int *vps = sv + (size_t)((i + 1) & 1) * S + c.off;
+        const int *vis = sv + (size_t)(i & 1) * S + c.off;
+        for (int q0 = threadIdx.x; q0 < qv; q0 += IGM_RPT * BS) {
+          i64 wv[IGM_RPT];
+          int pv[IGM_RPT], qq[IGM_RPT];
+#pragma unroll
+          for (int u = 0; u < IGM_RPT; ++u) {
+            const int q = q0 + u * BS;
+            const bool ok = q < qv;
+            wv[u] = !ok ? 0 : i > 0 ? ws[q] : wg[q];
+            pv[u] = (ok && i > 0) ? vps[q] : 0;
+            qq[u] = (ok && i <= j) ? vis[q] : 0;
+          }
+#pragma unroll
+          for (int u = 0; u < IGM_RPT; ++u) {
+            const int q = q0 + u * BS;
+            if (q < qv) ws[q] = row(wv[u], pv[u], qq[u]);
+          }
+        }
+      }
+      // further rows: the basis from global memory (the int32 copy while
+      // narrow); w in shared memory below qw, else in global memory
+      auto sweep = [&](auto nar_tag, const auto *vp, const auto *vi) {
+        constexpr bool NAR = decltype(nar_tag)::value;
+        using VT = std::conditional_t<NAR, int, i64>;
+        for (int q0 = qv + threadIdx.x; q0 < nr; q0 += IGM_RPT * BS) {
+          const u64 keep = l2_policy_keep();
+          i64 wv[IGM_RPT];
+          VT pv[IGM_RPT], qq[IGM_RPT];
+#pragma unroll
+          for (int u = 0; u < IGM_RPT; ++u) {
+            const int q = q0 + u * BS;
+            const bool ok = q < nr;
+            wv[u] = !ok ? 0 : (i > 0 && q < qw) ? ws[q] : ld_l2hint(wg + q, keep);
+            pv[u] = (ok && i > 0) ? vp[q] : 0;
+            qq[u] = (ok && i <= j) ? vi[q] : 0;
+          }
+#pragma unroll
+          for (int u = 0; u < IGM_RPT; ++u) {
+            const int q = q0 + u * BS;
+            if (q >= nr) continue;
+            const i64 wl = row(wv[u], pv[u], qq[u]);
+            if (q < qw) ws[q] = wl;
+            else if (i > 0) st_l2hint(wg + q, wl, keep);
+          }
+        }
+      };
+      if (qv < nr) {
+        const size_t op = (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
+        const size_t oi = (size_t)(i <= j ? i : 0) * c.n + c.row0;
+        if (c.narrow) sweep(std::true_type{}, c.V32 + op, c.V32 + oi);
+        else sweep(std::false_type{}, c.V + op, c.V + oi);
+      }
+      flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
+      flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+      part = block_sum_i128(part);
+      if (threadIdx.x == 0) mslot_put(mslot(B, i & 1, g0 + k), part, tag);
+    }
+    // every thread's reads of pass i are behind the block barriers of the
+    // sums: v_{i+1} may overwrite the buffer of v_{i-1}
+    if (i + 1 <= j) stage(i + 1);
+    // each segment's coefficient from its system's total (tagged slots)
+    for (int k = 0; k < ns && !s_fail; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      i128 tot;
+      if (!mseg_total(B, c.sys, i & 1, tag, err0, tot)) {
+        if (threadIdx.x == 0) s_fail = 1;
+        __syncthreads();
+        break;
+      }
+      if (threadIdx.x == 0) {
+        const i64 h = mseg_coef(c, tot, i, j);
+        if (k < IGM_MGS_GCACHE) s_h[k] = h;
+        else B.mseg_h[g0 + k] = h;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+  }
+  if (s_fail) {
+    mgs_cp_async_wait_all();
+    if (threadIdx.x == 0) atomicOr(err0, ERR_TIMEOUT);
+  } else {
+    // line 11 for every system whose divisor is non-zero
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      const i64 hn = k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k];
+      if (shr(hn, c.b11b) == 0) continue;
+      const int qw = res_w(c);
+      i64 *vn = c.V + (size_t)(j + 1) * c.n + c.row0;
+      int *vn32 = c.V32 + (size_t)(j + 1) * c.n + c.row0;
+      const i64 *wg = c.w, *ws = sw + c.off;
+      unsigned ev = 0, evr = 0;
+      for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * BS) {
+        const u64 drop = l2_policy_drop();
+        i64 wv[IGM_RPT];
+#pragma unroll
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * BS;
+          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : ld_l2hint(wg + q, drop);
+        }
+#pragma unroll
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * BS;
+          if (q >= c.nrows) continue;
+          const i64 v = fx_div(wv[u], hn, c.b11a, c.b11b, c.df, ev);
+          evr += (v < INT32_MIN || v > INT32_MAX);
+          vn[q] = v;
+          vn32[q] = (int)v;
+        }
+      }
+      flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
+      // an entry outside int32: the readers of the next steps (SpMV, these
+      // passes, the update) switch to the int64 copy for this inner solve
+      if (__syncthreads_or(evr != 0) && threadIdx.x == 0) atomicOr(&c.sc->vwide, 1);
+      flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
+    }
+    // lines 10 (store) and 12-19, one thread per system, after line 11: the
+    // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += BS) {
+      if (k < IGM_MGS_GCACHE) {
+        if (s_seg[k].active && s_seg[k].first) givens_tail(B, s_seg[k], j, s_h[k]);
+      } else {
+        MSegC c;
+        seg_make(k, c);
+        if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
+      }
+    }
+  }
+  // the last CTA to finish moves the launch epoch on (every CTA of this
+  // launch read it before publishing anything)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned done = atom_add_acq_rel_u32(B.bar + 3, 1u);
+    if (done == gridDim.x - 1) {
+      st_relaxed_u32(B.bar + 3, 0u);
+      st_relaxed_u32(B.bar + 2, epoch + 1u);
     }
   }
 }
@@ -522,12 +766,12 @@ int persistent_grid(int ntiles) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     // co-resident CTAs with the most dynamic shared memory a plan may give
-    // the integer step (every row of w in shared memory)
-    cudaFuncSetAttribute(k_mgs_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         IGM_MGS_WMAX * (int)sizeof(i64));
+    // the integer step (IGM_MGS_WMAX resident rows)
+    cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IGM_MGS_WMAX * IGM_MGS_ROWB);
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step<false>, IGM_MGS_BLOCK,
-                                                      IGM_MGS_WMAX * sizeof(i64)) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_grid, IGM_MGS_BLOCK,
+                                                      IGM_MGS_WMAX * IGM_MGS_ROWB) != cudaSuccess)
       a = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0) !=
         cudaSuccess)
@@ -551,9 +795,9 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
 }
 
 void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::vector<int> &ptr,
-              std::vector<Tile> &seg, int &wrows, std::vector<int> &sys_seg) {
-  // rows of w a CTA may keep in shared memory: 0 automatic, -1 none, k > 0
-  // at most k (never above what the kernel reserves)
+              std::vector<Tile> &seg, int &wrows, int &rows, std::vector<int> &sys_seg) {
+  // rows a CTA may keep resident in shared memory: 0 automatic, -1 none,
+  // k > 0 at most k (never above what the kernel reserves)
   const int cap = wmax == 0 ? IGM_MGS_WMAX : wmax < 0 ? 0 : std::min(wmax, IGM_MGS_WMAX);
   long long N = 0;
   for (int v : n) N += v;
@@ -578,7 +822,8 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::ve
     maxrows = std::max(maxrows, off);
   }
   ptr[G] = (int)seg.size();
-  wrows = maxrows <= cap ? maxrows : 0;
+  wrows = std::min(maxrows, cap);
+  rows = maxrows;
   // segments run in system order: system s owns [sys_seg[s], sys_seg[s+1])
   sys_seg.assign(n.size() + 1, (int)seg.size());
   for (int g = (int)seg.size() - 1; g >= 0; --g) sys_seg[seg[g].sys] = g;
@@ -586,22 +831,21 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::ve
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   if (mgs_one_cta(B, B.nsys)) {
-    // one CTA, no grid barrier
-    k_mgs_step<true><<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
+    k_mgs_one<<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
     return;
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mgs_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         IGM_MGS_WMAX * (int)sizeof(i64));
+    cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IGM_MGS_WMAX * IGM_MGS_ROWB);
     attr = true;
   }
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};
-  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_step<false>, dim3(G),
-                                          dim3(IGM_MGS_BLOCK), args,
-                                          (size_t)B.mgs_wrows * sizeof(i64), st));
+  // cooperative: every CTA resident at once (CTAs wait for each other's sums)
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid, dim3(G), dim3(IGM_MGS_BLOCK),
+                                          args, (size_t)B.mgs_wrows * IGM_MGS_ROWB, st));
 }
 
 }  // namespace igm

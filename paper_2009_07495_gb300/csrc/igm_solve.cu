@@ -57,6 +57,7 @@ __global__ void k_init_scal(BatchDev B, int mode) {
   }
   sc->retries = 0;
   sc->retry = 0;
+  sc->vwide = 0;
   for (int k = 0; k < IGM_NEV; ++k) sc->ev[k] = 0;
   sc->status = 5;  // IGM_ENOCONV until the test of Fig. 1 passes
   sc->active = mode == 0 ? 1 : 0;
@@ -246,6 +247,7 @@ __global__ void k_rhs(BatchDev B) {
     const int line[5] = {IGM_EV_L7, IGM_EV_L8, IGM_EV_L10, IGM_EV_L13, IGM_EV_L15};
     for (int t = 0; t < 5; ++t) sc->ev0[t] = sc->ev[line[t]];
     sc->retry = 0;
+    sc->vwide = 0;
   }
   double gam = sc->gamma;
   TILE_LOOP(i) s->r[i] = __ddiv_rn(s->r[i], gam);
@@ -260,7 +262,10 @@ __global__ void k_arm(BatchDev B) {
   Tile tl = B.tiles[blockIdx.x];
   const SysDev *s = B.sys[tl.sys];
   if (!g_cyc(s->sc)) return;
-  if (blockIdx.x == tl.first && threadIdx.x == 0) s->sc->seq += 1;
+  if (blockIdx.x == tl.first && threadIdx.x == 0) {
+    s->sc->seq += 1;
+    s->sc->vwide = 0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -273,14 +278,17 @@ __global__ void k_cast_v1(BatchDev B) {
   if (!g_step(sc)) return;
   const int df = s->p.df;
   double nu = sc->nu;
-  unsigned ev = 0;
+  unsigned ev = 0, wide = 0;
   TILE_LOOP(l) {
     double v = scalbn(__ddiv_rn(s->r[l], nu), df);
     i64 q = 0;
     if (fabs(v) < 9223372036854775808.0) q = __double2ll_rz(v);
     else ev += 1;
     s->V[l] = q;
+    s->V32[l] = (int)q;
+    wide |= q != (i64)(int)q;
   }
+  if (__syncthreads_or(wide) && threadIdx.x == 0) atomicOr(&sc->vwide, 1);
   if (blockIdx.x == tl.first && threadIdx.x == 0) {
     s->g[0] = (i64)1 << df;
     for (int k = 1; k <= s->p.m; ++k) s->g[k] = 0;
@@ -305,6 +313,9 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   if (!g_step(sc) || j >= s->p.m) return;
   if (blockIdx.x == tl.first && threadIdx.x == 0) sc->seq += 1;
   const i64 *vj = s->V + (size_t)j * s->n;
+  const int *vj32 = s->V32 + (size_t)j * s->n;
+  // the basis as int32 words unless an entry of this inner solve left int32
+  const bool narrow = sc->vwide == 0;
   const long long *sptr = s->sptr;
   const i64 *sval = s->sval;
   const int *scol = s->scol;
@@ -337,8 +348,13 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
           c[u] = ok ? __ldcs(pc + 32 * (k0 + u)) : i;
         }
         i64 x[8];
+        if (narrow) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
+          for (int u = 0; u < 8; ++u) x[u] = vj32[c[u]];
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
       }
@@ -410,12 +426,16 @@ __global__ void k_update(BatchDev B) {
   for (int i = threadIdx.x; i < jeff; i += blockDim.x) s_y[i] = s->yfp[i];
   __syncthreads();
   // y_i (v_il 2^-df): the scaled basis entry is exact, built with integer
-  // operations (GB300's FP64 rate is low)
+  // operations (GB300's FP64 rate is low); the basis as int32 words unless an
+  // entry of this inner solve left int32
+  const bool narrow = sc->vwide == 0;
   TILE_LOOP(l) {
     double acc = ir ? 0.0 : s->xk[l];
 #pragma unroll 8
-    for (int i = 0; i < jeff; ++i)
-      acc = __dadd_rn(acc, __dmul_rn(s_y[i], i2d_scaled(s->V[(size_t)i * n + l], df)));
+    for (int i = 0; i < jeff; ++i) {
+      const i64 v = narrow ? (i64)s->V32[(size_t)i * n + l] : s->V[(size_t)i * n + l];
+      acc = __dadd_rn(acc, __dmul_rn(s_y[i], i2d_scaled(v, df)));
+    }
     if (ir) s->xt[l] = __dadd_rn(s->xt[l], __dmul_rn(gam, acc));
     else s->xk[l] = acc;
   }

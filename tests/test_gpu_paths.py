@@ -1,6 +1,8 @@
 """GPU parity on the paths the small cases do not reach: the Arnoldi step
-with w in global memory (the path of systems with more than 152 x 20,480
-rows, forced here on small systems by params.mgs_wmax), the 27-point
+with w in global memory (the path of CTAs with more than 26,624 rows,
+forced here on small systems by params.mgs_wmax), basis entries outside
+int32 (d_f > 30: the readers switch from the int32 copy of the basis to
+the int64 one), the 27-point
 sigma = 2.5 / convection +-100 coefficient regime of the largest
 configuration, a batch shaped like the batched configuration (64 systems,
 n log-uniform up to 64k), and the bounded waits of the substitutions
@@ -95,6 +97,45 @@ def test_arnoldi_global_w_bit_exact(L, orc, name, sf, prec, m, wmax):
     solver.close()
     ro = _check_ir(L, orc, s, P)
     assert ro.status == "ok"
+
+
+# (preconditioned, d_f, shift offset on every tuned line, mgs_wmax, basis
+# entries outside int32 at line 11): short solves cut by overflow breakdowns
+# and full ones where the basis leaves int32 partway (d_f = 34 with shifts
+# raised by 4 gives 2 such entries late in the 30 steps)
+WIDE = [(0, 31, 0, 500, False), (0, 32, 2, -1, False), (0, 34, 0, 0, True),
+        (1, 33, 1, -1, True), (1, 34, 4, 500, True)]
+
+
+@pytest.mark.parametrize("prec,df,dd,wmax,wide", WIDE,
+                         ids=[f"p{c[0]}_df{c[1]}_dd{c[2]}_w{c[3]}" for c in WIDE])
+def test_wide_basis_bit_exact(L, orc, prec, df, dd, wmax, wide):
+    """With d_f > 30 a basis entry (at most 2^d_f in magnitude) can leave
+    int32, which the kernels detect (at line 2 or line 11) and answer by
+    reading the int64 copy of the basis for the rest of the inner solve:
+    the basis, Hessenberg matrix, rotations, x and every overflow count equal
+    the oracle's bit for bit, line 11's basis entries outside int32 are
+    counted alike, and the refinement loop agrees."""
+    s = W.small_cd2d(60) if prec else W.banded_random(6000, np.random.default_rng(320))
+    P = L.params_default(prec, 30)
+    P.df = df
+    for f in ("beta7", "beta8", "beta10", "beta11a", "beta11b", "beta13", "beta15",
+              "beta16a", "beta16b"):
+        setattr(P, f, getattr(P, f) + dd)
+    P.mgs_wmax = wmax
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    bk = d["b"] / np.abs(d["b"]).max()
+    x0 = np.zeros(s.n)
+    o = orc.int_gmres(_oparams(orc, P), d, bk, x0)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    _compare_inner(solver.state(), o)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    assert (o["ev"][10] > 0) == wide
+    solver.close()
+    _check_ir(L, orc, s, P)
 
 
 def test_arnoldi_global_w_batched_equals_solo(L, orc):
