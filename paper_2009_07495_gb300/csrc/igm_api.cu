@@ -590,7 +590,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
   A.want(&w, n);
   A.want(&yv, n);
   A.want(&V, (size_t)(m + 1) * n);
-  A.want(&V32, (size_t)(m + 1) * n);
+  A.want(&V32, (size_t)(m + 1) * n + 4);  // + the tail of a 16-byte copy
   A.want(&H, (size_t)(m + 1) * m);
   A.want(&cs, m);
   A.want(&sn, m);

@@ -447,4 +447,74 @@ static __device__ __noinline__ void givens_col(const SysDev *s, SysScal *sc, int
   if (e17) atomicAdd(&sc->ev[IGM_EV_L17], (u64)e17);
 }
 
+
+// ---------------------------------------------------------------------------
+// shared-memory addresses, mbarriers and bulk copies (the async proxy)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// bytes (a multiple of 16) from 16-byte aligned global memory to 16-byte
+// aligned shared memory, completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ u64 gtimer() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// orders this thread's earlier generic-proxy accesses of shared memory
+// before its later async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// iteration bound of the time-bounded waits (the time limit ends them first)
+#define IGM_WAIT_ITERS (1 << 28)
+
+// wait for the phase of parity `parity` of a bulk-copy barrier; bounded by
+// time (a copy always completes, so expiry is an error); false if expired
+__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned parity, unsigned *err,
+                                          u64 limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const u64 t0 = gtimer();
+  for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && gtimer() - t0 > limit_ns) break;
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+
 }  // namespace igm

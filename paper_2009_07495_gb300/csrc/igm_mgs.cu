@@ -101,31 +101,10 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
 #define IGM_MSEG_CACHE 64   // segments of the one-CTA mode (descriptors in shared memory)
 #define IGM_MGS_GCACHE 32   // segment descriptors a CTA of the grid mode keeps in shared memory
 // CTA rows of the grid mode resident in shared memory: w (int64) and two
-// int32 basis vectors, 16 bytes a row (220 KB)
-#define IGM_MGS_WMAX 14080
+// int32 basis vectors, 16 bytes a row (218 KB)
+#define IGM_MGS_WMAX 13952
 #define IGM_MGS_ROWB 16
 
-// L2 eviction priorities for the rows of w that live in global memory: kept
-// (evict_last) from pass to pass, dropped (evict_first) at their last read
-__device__ __forceinline__ u64 l2_policy_keep() {
-  u64 p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ u64 l2_policy_drop() {
-  u64 p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ i64 ld_l2hint(const i64 *a, u64 pol) {
-  i64 v;
-  asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ void st_l2hint(i64 *a, i64 v, u64 pol) {
-  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol)
-               : "memory");
-}
 
 // the step's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows in
 // all, every row of w in shared memory, each system one segment of it (ns
@@ -374,34 +353,155 @@ __device__ bool mseg_total(const BatchDev &B, int sys, int par, unsigned tag,
 __device__ __forceinline__ bool fits32(int) { return true; }
 __device__ __forceinline__ bool fits32(i64 x) { return x == (i64)(int)x; }
 
-// asynchronous 4-byte copy global -> shared (the resident basis rows)
-__device__ __forceinline__ void mgs_cp_async4(int *dst, const int *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
+// Pass work on IGM_RPT rows of a segment whose values are loaded (w in wv,
+// v_{i-1} in pv, v_i in qv; rows past the end hold zeros, which change
+// nothing and raise no event).  MODE 0: pass 0 (line 7 with v_0); 1:
+// 0 < i <= j (line 8 with h_{i-1,j}, line 7 with v_i); 2: i = j + 1 (line 8
+// with h_{j,j}, line 10).  HS32: line 8's coefficient fits int32.  The
+// products of lines 7 / 10 are taken as 32x32 -> 64-bit multiplies (exact,
+// never out of range: the same word, no event) and redone with the general
+// wrapped product only when a factor leaves int32, so the common case has
+// no branch per row.  wv returns the updated w.
+template <int MODE, bool HS32, int R, typename VT>
+__device__ __forceinline__ void rows_pass(i64 (&wv)[R], const VT (&pv)[R], const VT (&qv)[R],
+                                          i64 hs, int s8, int sA, i128 &part, unsigned &evA,
+                                          unsigned &evB) {
+  i64 pr[R];
+  bool fast = true;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (MODE > 0) {
+      i64 p;
+      if (HS32 && sizeof(VT) == 4) p = (i64)(int)hs * (i64)pv[u];
+      else p = mulw(hs, (i64)pv[u], evB);
+      wv[u] = subw(wv[u], p >> s8, evB);
+    }
+    const i64 a = wv[u] >> sA;
+    const i64 b = MODE == 2 ? a : (i64)qv[u];
+    fast = fast && fits32(a) && fits32(b);
+    pr[u] = (i64)(int)a * (i64)(int)b;
+  }
+  if (!fast) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const i64 a = wv[u] >> sA;
+      const i64 b = MODE == 2 ? a : (i64)qv[u];
+      if (!(fits32(a) && fits32(b))) pr[u] = mulw(a, b, evA);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) part += (i128)pr[u];
 }
+
+// a segment's pass in the grid mode (see k_mgs_grid)
+struct MPass {
+  i64 hs;
+  int s8, sA;
+  int qv, qw, nr;     // resident basis rows, resident w rows, rows
+  i64 *wg, *ws;       // w in global memory (segment) and in shared memory
+  const int *vps, *vis;  // resident v_{i-1}, v_i (shared memory)
+};
+
+// resident rows [0, qv): w, v_{i-1} and v_i in shared memory (w from global
+// memory at pass 0, stored into shared memory); each thread the rows
+// q = threadIdx.x (mod IGM_MGS_BLOCK)
+template <int MODE, bool HS32>
+__device__ __forceinline__ void pass_res(const MPass &P, i128 &part, unsigned &evA,
+                                         unsigned &evB) {
+  for (int q0 = threadIdx.x; q0 < P.qv; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+    i64 wv[IGM_RPT];
+    int pv[IGM_RPT], qq[IGM_RPT];
+#pragma unroll
+    for (int u = 0; u < IGM_RPT; ++u) {
+      const int q = q0 + u * IGM_MGS_BLOCK;
+      const bool ok = q < P.qv;
+      wv[u] = !ok ? 0 : MODE == 0 ? P.wg[q] : P.ws[q];
+      pv[u] = (MODE > 0 && ok) ? P.vps[q] : 0;
+      qq[u] = (MODE < 2 && ok) ? P.vis[q] : 0;
+    }
+    rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
+#pragma unroll
+    for (int u = 0; u < IGM_RPT; ++u) {
+      const int q = q0 + u * IGM_MGS_BLOCK;
+      if (q < P.qv) P.ws[q] = wv[u];
+    }
+  }
+}
+
+// further rows [qv, nr): the basis from global memory (VT int: the int32
+// copy, IGM_RPT rows in flight a thread; int64: half as many), w in shared
+// memory below qw, else in global memory
+template <int MODE, bool HS32, typename VT>
+__device__ __forceinline__ void pass_glob(const MPass &P, const VT *vp, const VT *vi, i128 &part,
+                                          unsigned &evA, unsigned &evB) {
+  constexpr int R = sizeof(VT) == 4 ? IGM_RPT : IGM_RPT / 2;
+  for (int q0 = P.qv + threadIdx.x; q0 < P.nr; q0 += R * IGM_MGS_BLOCK) {
+    i64 wv[R];
+    VT pv[R], qq[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int q = q0 + u * IGM_MGS_BLOCK;
+      const bool ok = q < P.nr;
+      wv[u] = !ok ? 0 : (MODE > 0 && q < P.qw) ? P.ws[q] : P.wg[q];
+      pv[u] = (MODE > 0 && ok) ? vp[q] : 0;
+      qq[u] = (MODE < 2 && ok) ? vi[q] : 0;
+    }
+    rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int q = q0 + u * IGM_MGS_BLOCK;
+      if (q >= P.nr) continue;
+      if (q < P.qw) P.ws[q] = wv[u];
+      else if (MODE > 0) P.wg[q] = wv[u];
+    }
+  }
+}
+
+template <int MODE, bool HS32>
+__device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, int j,
+                                         i128 &part, unsigned &evA, unsigned &evB) {
+  pass_res<MODE, HS32>(P, part, evA, evB);
+  if (P.qv < P.nr) {
+    const size_t op = (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
+    const size_t oi = (size_t)(i <= j ? i : 0) * c.n + c.row0;
+    if (c.narrow) pass_glob<MODE, HS32, int>(P, c.V32 + op, c.V32 + oi, part, evA, evB);
+    else pass_glob<MODE, HS32, i64>(P, c.V + op, c.V + oi, part, evA, evB);
+  }
+}
+
+// resident basis buffers: per pass parity IGM_MGS_WMAX rows plus room for
+// each cached segment's alignment (a bulk copy starts on a 16-byte boundary
+// of the basis vector, up to 3 words before the segment's first row)
+#define IGM_MGS_VPAD (12 * IGM_MGS_GCACHE + 8)
+// layout of the dynamic shared memory for S resident rows: w (8 S bytes),
+// then at a 16-byte boundary two basis buffers of IGM_MGS_VB(S) words
+#define IGM_MGS_VOFF(S) (((size_t)(S) * 8 + 15) & ~(size_t)15)
+#define IGM_MGS_VB(S) ((((S) + 3) & ~3) + IGM_MGS_VPAD)
+#define IGM_MGS_SMEM(S) (IGM_MGS_VOFF(S) + 2 * sizeof(int) * (size_t)IGM_MGS_VB(S))
 
 // Grid mode: every CTA owns the same rows in every pass (a balanced partition
 // of all systems' rows, planned on the host).  The first B.mgs_wrows of them
-// are resident in shared memory: w from pass 0 to line 11, and (while every
-// basis entry of the inner solve fits int32) the int32 words of v_{i-1} and
-// v_i in two buffers; v_{i+1} is copied into the buffer of v_{i-1} while
-// the pass's sums travel, each thread copying the rows it alone reads, so a
-// pass over resident rows reads nothing from global memory.  Further rows
-// keep w in global memory (held in L2 by eviction priority) and read the
-// basis from global memory.  There is no grid barrier: each CTA publishes
-// its tagged sum of the pass per segment and reads those of its systems'
-// segments, so a CTA waits only for the CTAs that share a system with it.
+// (in segments among the first IGM_MGS_GCACHE) are resident in shared
+// memory: w from pass 0 to line 11, and (while every basis entry of the
+// inner solve fits int32) the int32 words of v_{i-1} and v_i in two
+// buffers; v_{i+1} is bulk-copied into the buffer of v_{i-1} while the
+// pass's sums travel, so a pass over resident rows reads nothing from global
+// memory.  Further rows keep w in global memory and read the basis from
+// global memory (the next vector prefetched into L2 during the pass).  There is no grid
+// barrier: each CTA publishes its tagged sum of the pass per segment and
+// reads those of its systems' segments, so a CTA waits only for the CTAs
+// that share a system with it.
 __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j) {
   constexpr int BS = IGM_MGS_BLOCK;
   extern __shared__ __align__(16) unsigned char smem[];
   const int S = B.mgs_wrows;  // resident rows of this CTA
-  i64 *sw = reinterpret_cast<i64 *>(smem);        // w of the resident rows
-  int *sv = reinterpret_cast<int *>(sw + S);      // 2 x S basis words
+  i64 *sw = reinterpret_cast<i64 *>(smem);                    // w of the resident rows
+  int *sv = reinterpret_cast<int *>(smem + IGM_MGS_VOFF(S));  // 2 basis buffers
+  const int vb = IGM_MGS_VB(S);                               // words of one
   __shared__ MSegC s_seg[IGM_MGS_GCACHE + 1];  // + one slot for the others in turn
   __shared__ i64 s_h[IGM_MGS_GCACHE];
-  __shared__ unsigned s_epoch;
+  __shared__ __align__(8) u64 s_vbar[2];  // bulk copies into basis buffer 0 / 1
+  __shared__ unsigned s_epoch, s_vbytes;
   __shared__ int s_fail;
   unsigned *err0 = &B.sys[0]->sc->err;
   const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
@@ -419,6 +519,9 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
   if (threadIdx.x == 0) {
     s_epoch = ld_relaxed_u32(B.bar + 2);
     s_fail = 0;
+    mbar_init(&s_vbar[0], 1);
+    mbar_init(&s_vbar[1], 1);
+    fence_mbar_init();
   }
   __syncthreads();
   const unsigned epoch = s_epoch;
@@ -438,127 +541,100 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     __syncthreads();
     return s_seg[IGM_MGS_GCACHE];
   };
-  // resident rows of a segment: w (qw) and the basis (qv: only while narrow)
+  // resident rows of segment k: w (res_w) and the basis (res_v: cached
+  // segments while narrow)
   auto res_w = [&](const MSegC &c) { return min(max(S - c.off, 0), c.nrows); };
-  auto res_v = [&](const MSegC &c) { return c.narrow ? res_w(c) : 0; };
-  // copy v_i of the resident rows into buffer i & 1 (each thread its rows)
-  auto stage = [&](int i) {
-    for (int k = 0; k < ns; ++k) {
-      const MSegC &c = seg(k);
-      if (!c.active) continue;
-      const int qv = res_v(c);
-      const int *src = c.V32 + (size_t)i * c.n + c.row0;
-      int *dst = sv + (size_t)(i & 1) * S + c.off;
-      for (int q = threadIdx.x; q < qv; q += BS) mgs_cp_async4(dst + q, src + q);
-    }
-    mgs_cp_async_commit();
+  auto res_v = [&](const MSegC &c, int k) {
+    return (k < IGM_MGS_GCACHE && c.narrow) ? res_w(c) : 0;
   };
-  stage(0);
+  // where vector i of cached segment k starts in its basis buffer: at a
+  // 16-byte aligned offset, plus the vector's misalignment
+  auto vbase = [&](const MSegC &c, int k, int i) -> int * {
+    return sv + (size_t)(i & 1) * vb + ((c.off + 3) & ~3) + 12 * k +
+           (int)(((size_t)i * c.n + c.row0) & 3);
+  };
+  // bulk-copy v_i of every resident segment into buffer i & 1 (thread 0,
+  // after a block barrier behind the last reads of that buffer)
+  auto stage = [&](int i) {
+    unsigned bytes = 0;
+    for (int k = 0; k < ns && k < IGM_MGS_GCACHE; ++k) {
+      const MSegC &c = s_seg[k];
+      const int qv = c.active ? res_v(c, k) : 0;
+      if (qv == 0) continue;
+      const size_t e0 = (size_t)i * c.n + c.row0;
+      const int pad = (int)(e0 & 3);
+      bytes += 4u * (unsigned)((pad + qv + 3) & ~3);
+    }
+    s_vbytes = bytes;
+    if (bytes == 0) return;
+    fence_proxy_async();
+    mbar_expect_tx(&s_vbar[i & 1], bytes);
+    for (int k = 0; k < ns && k < IGM_MGS_GCACHE; ++k) {
+      const MSegC &c = s_seg[k];
+      const int qv = c.active ? res_v(c, k) : 0;
+      if (qv == 0) continue;
+      const size_t e0 = (size_t)i * c.n + c.row0;
+      const int pad = (int)(e0 & 3);
+      bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)((pad + qv + 3) & ~3),
+               &s_vbar[i & 1]);
+    }
+  };
+  if (threadIdx.x == 0) stage(0);
+  __syncthreads();
+  const bool vst = s_vbytes != 0;  // the same for every vector
+  int staged = 0;                  // the last vector copied
   for (int i = 0; i <= j + 1; ++i) {
     const unsigned tag = (epoch << 8) | (unsigned)(i + 1);
-    mgs_cp_async_wait_all();  // this thread's rows of v_i are in place
+    // v_i of the resident rows is in place (v_{i-1} already was)
+    if (vst && i <= j && !mbar_wait(&s_vbar[i & 1], (unsigned)(i >> 1) & 1u, err0, 1000000000ull))
+      s_fail = 1;
     for (int k = 0; k < ns; ++k) {
       const MSegC &c = seg(k);
       if (!c.active) continue;
-      const int nr = c.nrows, qw = res_w(c), qv = res_v(c);
+      MPass P;
+      P.nr = c.nrows;
+      P.qw = res_w(c);
+      P.qv = res_v(c, k);
       // pull the global rows of v_{i+1} into L2 while this pass runs
-      if (i + 1 <= j) {
-        const size_t o = (size_t)(i + 1) * c.n + c.row0 + qv;
+      if (i + 1 <= j && P.qv < P.nr) {
+        const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
         const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
-        const size_t bytes = (size_t)(nr - qv) * (c.narrow ? sizeof(int) : sizeof(i64));
+        const size_t bytes = (size_t)(P.nr - P.qv) * (c.narrow ? sizeof(int) : sizeof(i64));
         for (size_t a = (size_t)threadIdx.x * 128; a < bytes; a += (size_t)BS * 128)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(base + a));
       }
-      const i64 hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
-      i64 *wg = c.w, *ws = sw + c.off;
-      const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
-      // line 8's coefficient as a 32-bit value when it fits: its product
-      // with a basis entry that fits too is one 32x32 -> 64-bit multiply,
-      // exact and never out of range (same word, no event)
-      const bool hs32 = hs == (i64)(int)hs;
+      P.hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
+      P.wg = c.w;
+      P.ws = sw + c.off;
+      P.s8 = shc(c.df - c.b8);
+      P.sA = i <= j ? shc(c.b7) : shc(c.b10);
+      if (P.qv > 0) {
+        P.vps = vbase(c, k, i > 0 ? i - 1 : 0);
+        P.vis = vbase(c, k, i <= j ? i : 0);
+      }
+      const bool hs32 = P.hs == (i64)(int)P.hs;
       i128 part = 0;
       unsigned evA = 0, evB = 0;
-      // line 8 (i > 0) and the line-7 (i <= j) or line-10 (i = j + 1) term of
-      // one row; returns the updated w
-      auto row = [&](i64 wl, auto pv, auto qvv) -> i64 {
-        if (i > 0) {
-          const i64 pr = (hs32 && fits32(pv)) ? (i64)(int)hs * (i64)(int)pv
-                                              : mulw(hs, (i64)pv, evB);
-          wl = subw(wl, pr >> s8, evB);
-        }
-        if (i <= j) {
-          const i64 a = wl >> s7;
-          part += (i128)((fits32(a) && fits32(qvv)) ? (i64)(int)a * (i64)(int)qvv
-                                                    : mulw(a, (i64)qvv, evA));
-        } else {
-          const i64 a = wl >> s10;
-          part += (i128)(fits32(a) ? (i64)(int)a * (i64)(int)a : mulw(a, a, evA));
-        }
-        return wl;
-      };
-      // resident rows: everything in shared memory (w from global at pass 0)
-      {
-        const int *vps = sv + (size_t)((i + 1) & 1) * S + c.off;
-        const int *vis = sv + (size_t)(i & 1) * S + c.off;
-        for (int q0 = threadIdx.x; q0 < qv; q0 += IGM_RPT * BS) {
-          i64 wv[IGM_RPT];
-          int pv[IGM_RPT], qq[IGM_RPT];
-#pragma unroll
-          for (int u = 0; u < IGM_RPT; ++u) {
-            const int q = q0 + u * BS;
-            const bool ok = q < qv;
-            wv[u] = !ok ? 0 : i > 0 ? ws[q] : wg[q];
-            pv[u] = (ok && i > 0) ? vps[q] : 0;
-            qq[u] = (ok && i <= j) ? vis[q] : 0;
-          }
-#pragma unroll
-          for (int u = 0; u < IGM_RPT; ++u) {
-            const int q = q0 + u * BS;
-            if (q < qv) ws[q] = row(wv[u], pv[u], qq[u]);
-          }
-        }
-      }
-      // further rows: the basis from global memory (the int32 copy while
-      // narrow); w in shared memory below qw, else in global memory
-      auto sweep = [&](auto nar_tag, const auto *vp, const auto *vi) {
-        constexpr bool NAR = decltype(nar_tag)::value;
-        using VT = std::conditional_t<NAR, int, i64>;
-        for (int q0 = qv + threadIdx.x; q0 < nr; q0 += IGM_RPT * BS) {
-          const u64 keep = l2_policy_keep();
-          i64 wv[IGM_RPT];
-          VT pv[IGM_RPT], qq[IGM_RPT];
-#pragma unroll
-          for (int u = 0; u < IGM_RPT; ++u) {
-            const int q = q0 + u * BS;
-            const bool ok = q < nr;
-            wv[u] = !ok ? 0 : (i > 0 && q < qw) ? ws[q] : ld_l2hint(wg + q, keep);
-            pv[u] = (ok && i > 0) ? vp[q] : 0;
-            qq[u] = (ok && i <= j) ? vi[q] : 0;
-          }
-#pragma unroll
-          for (int u = 0; u < IGM_RPT; ++u) {
-            const int q = q0 + u * BS;
-            if (q >= nr) continue;
-            const i64 wl = row(wv[u], pv[u], qq[u]);
-            if (q < qw) ws[q] = wl;
-            else if (i > 0) st_l2hint(wg + q, wl, keep);
-          }
-        }
-      };
-      if (qv < nr) {
-        const size_t op = (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
-        const size_t oi = (size_t)(i <= j ? i : 0) * c.n + c.row0;
-        if (c.narrow) sweep(std::true_type{}, c.V32 + op, c.V32 + oi);
-        else sweep(std::false_type{}, c.V + op, c.V + oi);
+      if (i == 0) pass_seg<0, true>(P, c, i, j, part, evA, evB);
+      else if (i <= j) {
+        if (hs32) pass_seg<1, true>(P, c, i, j, part, evA, evB);
+        else pass_seg<1, false>(P, c, i, j, part, evA, evB);
+      } else {
+        if (hs32) pass_seg<2, true>(P, c, i, j, part, evA, evB);
+        else pass_seg<2, false>(P, c, i, j, part, evA, evB);
       }
       flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
       flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
       part = block_sum_i128(part);
       if (threadIdx.x == 0) mslot_put(mslot(B, i & 1, g0 + k), part, tag);
     }
-    // every thread's reads of pass i are behind the block barriers of the
-    // sums: v_{i+1} may overwrite the buffer of v_{i-1}
-    if (i + 1 <= j) stage(i + 1);
+    // every read of pass i is behind the block barriers of the sums: v_{i+1}
+    // may overwrite the buffer of v_{i-1}
+    __syncthreads();
+    if (vst && i + 1 <= j && !s_fail) {
+      if (threadIdx.x == 0) stage(i + 1);
+      staged = i + 1;
+    }
     // each segment's coefficient from its system's total (tagged slots)
     for (int k = 0; k < ns && !s_fail; ++k) {
       const MSegC &c = seg(k);
@@ -579,7 +655,8 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     if (s_fail) break;
   }
   if (s_fail) {
-    mgs_cp_async_wait_all();
+    // the copy in flight lands before the CTA leaves (bounded again)
+    if (vst) mbar_wait(&s_vbar[staged & 1], (unsigned)(staged >> 1) & 1u, err0, 1000000000ull);
     if (threadIdx.x == 0) atomicOr(err0, ERR_TIMEOUT);
   } else {
     // line 11 for every system whose divisor is non-zero
@@ -594,12 +671,11 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
       const i64 *wg = c.w, *ws = sw + c.off;
       unsigned ev = 0, evr = 0;
       for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * BS) {
-        const u64 drop = l2_policy_drop();
         i64 wv[IGM_RPT];
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
           const int q = q0 + u * BS;
-          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : ld_l2hint(wg + q, drop);
+          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : wg[q];
         }
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
@@ -768,10 +844,10 @@ int persistent_grid(int ntiles) {
     // co-resident CTAs with the most dynamic shared memory a plan may give
     // the integer step (IGM_MGS_WMAX resident rows)
     cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         IGM_MGS_WMAX * IGM_MGS_ROWB);
+                         (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
     int a = 0, b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_grid, IGM_MGS_BLOCK,
-                                                      IGM_MGS_WMAX * IGM_MGS_ROWB) != cudaSuccess)
+                                                      IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0) !=
         cudaSuccess)
@@ -837,7 +913,7 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         IGM_MGS_WMAX * IGM_MGS_ROWB);
+                         (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
     attr = true;
   }
   int G = B.mgs_g;
@@ -845,7 +921,7 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   void *args[] = {&b, &j};
   // cooperative: every CTA resident at once (CTAs wait for each other's sums)
   note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid, dim3(G), dim3(IGM_MGS_BLOCK),
-                                          args, (size_t)B.mgs_wrows * IGM_MGS_ROWB, st));
+                                          args, IGM_MGS_SMEM(B.mgs_wrows), st));
 }
 
 }  // namespace igm

@@ -266,9 +266,6 @@ struct TrsvT<TK_FP> {
   typedef double V;
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
 
 // asynchronous 8-byte global -> shared copy (a thread waits for its own
 // groups of copies)
@@ -285,47 +282,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// mbarriers and bulk copies (the async proxy)
-__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(u64 *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 // orders this thread's earlier generic-proxy accesses of global memory (here:
 // the acquire of another chunk's progress) before its later async-proxy
 // copies from global memory
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// bytes (a multiple of 16) from 16-byte aligned global memory to 16-byte
-// aligned shared memory, completing on bar
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(src)),
@@ -344,11 +305,6 @@ __device__ __forceinline__ unsigned ld_acquire_cta(const unsigned *p) {
   return v;
 }
 
-__device__ __forceinline__ u64 gtimer() {
-  u64 t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // The waits of a substitution CTA are bounded in time (the system's
 // p.wait_ns, 1 s unless set), nested so that a wait never expires while the
@@ -356,7 +312,6 @@ __device__ __forceinline__ u64 gtimer() {
 // the producer and the publisher (who wait on the compute warps, who wait on
 // the waiter and on the bulk copies) after four times.  An iteration cap
 // backs up each bound.
-#define IGM_WAIT_ITERS (1 << 28)
 
 // spin until the shared counter *p reaches at least v; false if the bound
 // expired or another wait of the system already timed out
@@ -391,19 +346,6 @@ __device__ __forceinline__ bool wait_cta_own(const unsigned *p, unsigned v, unsi
   return false;
 }
 
-// wait for the phase of parity `parity` of a bulk-copy barrier; bounded by
-// time (a copy always completes, so expiry is an error); false if expired
-__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned parity, unsigned *err,
-                                          u64 limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const u64 t0 = gtimer();
-  for (int it = 0; it < IGM_WAIT_ITERS; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255) == 255 && gtimer() - t0 > limit_ns) break;
-  }
-  atomicOr(err, ERR_TIMEOUT);
-  return false;
-}
 
 // Roles in a substitution CTA: IGM_TRSV_CW compute warps walk the groups,
 // one named barrier per group among them (which makes the previous group's
