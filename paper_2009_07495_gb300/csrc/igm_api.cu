@@ -1068,7 +1068,15 @@ long long handle_bytes_estimate(int n, int nnz, const igm_params *p) {
   r += 8 * Z * 3 + 8 * N;                           // ahat, a, abar, d
   r += 12 * Z + 12 * N + N / 4 + 8;                 // SELL-32 copy of abar (estimate)
   r += (long long)p->s * (16 * Z + 8 * N) + (p->s > 0 ? 8 * Z : 0);  // correction terms
-  if (p->precond) r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
+  if (p->precond) {
+    r += 8 * Z * 2 + 8 * N * 2 + 4 * N * 8 + 16 * N + 8 * N;
+    // the substitutions' packed group blocks, both triangles: per row 12
+    // bytes a strict entry (row length bounded by the mean, rounded up, plus
+    // the padding of the longest rows) and 24 bytes of row data; the FP64
+    // comparison solver keeps an FP64 copy
+    const long long K = (Z + N - 1) / N + 4;
+    r += 2 * N * (12 * K + 24) + (p->inner == 1 ? 2 * N * (8 * K + 8) : 0);
+  }
   r += 8 * N * 8 + 12 * N * (m + 1) + 8 * (m + 1) * m + 8 * 4 * (m + 1);
   return r + 64 * 256 + (long long)sizeof(SysScal) + sizeof(SysDev);
 }

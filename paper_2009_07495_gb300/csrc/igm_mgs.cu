@@ -10,6 +10,7 @@
 // memory.  Small batches (every row in one CTA) run a one-CTA variant
 // without the grid barrier.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "igm_dev.cuh"
@@ -835,9 +836,10 @@ __global__ void f_givens_step(BatchDev B, int j, int G) {
 }
 
 static int g_mgs_blocks_per_sm = -1, g_num_sms = 0;
+static std::once_flag g_mgs_once;
 
 int persistent_grid(int ntiles) {
-  if (g_mgs_blocks_per_sm < 0) {
+  std::call_once(g_mgs_once, [] {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -855,7 +857,7 @@ int persistent_grid(int ntiles) {
     cudaGetLastError();
     g_mgs_blocks_per_sm = a < b ? a : b;
     if (g_mgs_blocks_per_sm < 1) g_mgs_blocks_per_sm = 1;
-  }
+  });
   int G = g_num_sms * g_mgs_blocks_per_sm;
   if (G > ntiles) G = ntiles;
   return G < 1 ? 1 : G;
@@ -910,12 +912,7 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
     k_mgs_one<<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
     return;
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
-    attr = true;
-  }
+  persistent_grid(1);  // sets the kernel's shared-memory attribute once
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};

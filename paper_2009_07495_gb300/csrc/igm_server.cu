@@ -1,13 +1,16 @@
 // igm_server.cu -- serving runtime: continuous batching of independent
 // refinement solves (Fig. 1 with int-GMRES) on one GPU.
 //
-// Requests are queued on the host; a worker thread admits them in arrival
-// order while the device memory held by admitted systems stays within the
-// budget, sets each up on the device and keeps its state resident.  Each
-// round runs the convergence test of Fig. 1 and one inner solve of Fig. 2
-// for all active systems in the same kernels (a batch over their tiles);
-// systems admitted during a round join the next one, converged systems are
-// finalised and release their memory after the round.
+// Requests are queued on the host.  An admission thread takes them in
+// arrival order while the device memory held by admitted systems stays
+// within the budget and sets each up on the device on its own stream, so
+// set-up overlaps the rounds; a set-up system waits in the ready list.  The
+// round thread runs rounds: each round runs the convergence test of Fig. 1
+// and one inner solve of Fig. 2 for all active systems in the same kernels
+// (a batch over their tiles); ready systems join at the next round,
+// converged systems are finalised and release their memory after the round.
+// Every system's state stays resident on the device from set-up to its
+// last round.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -46,12 +49,16 @@ struct igm_server_s {
   std::condition_variable cv_work, cv_done;
   std::deque<Request *> queue;
   std::map<long long, Request *> all;
-  std::vector<Request *> active;
+  std::vector<Request *> active;   // in the rounds (round thread only)
+  std::vector<Request *> ready;    // set up, joining at the next round
+  int admitting = 0;               // requests in set-up, ready or active
+  double est_scale = 1.0;          // largest footprint / estimate seen so far
   long long next_id = 1, used = 0;
   igm_server_stats st{};
   bool stop = false;
-  std::thread worker;
-  cudaStream_t stream = nullptr;
+  std::thread worker, admitter;
+  cudaStream_t stream = nullptr;   // rounds
+  cudaStream_t astream = nullptr;  // set-up
   int dev = 0;
   Batch *batch = nullptr;
   bool dirty = true;
@@ -60,6 +67,16 @@ struct igm_server_s {
 };
 
 namespace {
+
+// a request's device memory and admission slot are free again
+void release(igm_server_s *S, Request *r) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->used -= r->bytes;
+    S->admitting--;
+  }
+  S->cv_work.notify_all();
+}
 
 void finish(igm_server_s *S, Request *r, igm_status st) {
   std::lock_guard<std::mutex> lk(S->mu);
@@ -72,17 +89,18 @@ void finish(igm_server_s *S, Request *r, igm_status st) {
   S->cv_done.notify_all();
 }
 
-// set-up and Fig. 1 initialisation of one admitted request
+// set-up and Fig. 1 initialisation of one admitted request (admission
+// thread, on its stream)
 igm_status admit(igm_server_s *S, Request *r) {
   igm_status st = int_gmres_setup(r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(),
-                                  &r->prm, S->stream, &r->h);
+                                  &r->prm, S->astream, &r->h);
   if (st) return st;
   r->bytes = int_gmres_device_bytes(r->h);
-  st = load_vec(r->h, r->h->hs.bh, r->b.data(), S->stream);
+  st = load_vec(r->h, r->h->hs.bh, r->b.data(), S->astream);
   if (st) return st;
-  st = ir_init_host(r->h->solo, S->stream);
+  st = ir_init_host(r->h->solo, S->astream);
   if (st) return st;
-  CK(cudaStreamSynchronize(S->stream));
+  CK(cudaStreamSynchronize(S->astream));
   // the host copies of the matrix are no longer needed
   std::vector<int>().swap(r->rowptr);
   std::vector<int>().swap(r->col);
@@ -149,10 +167,7 @@ igm_status round(igm_server_s *S) {
     }
     int_gmres_destroy(r->h);
     r->h = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      S->used -= r->bytes;
-    }
+    release(S, r);
     finish(S, r, fs);
     S->dirty = true;
   }
@@ -160,48 +175,77 @@ igm_status round(igm_server_s *S) {
   return IGM_OK;
 }
 
+// a request's device footprint before set-up: the host estimate, scaled by
+// the largest footprint / estimate ratio of the systems set up so far
+// (called with the lock held)
+long long estimate(const igm_server_s *S, const Request *r) {
+  return (long long)((double)handle_bytes_estimate(r->n, r->nnz, &r->prm) * S->est_scale) + 1;
+}
+
+// Admission thread: in arrival order, while the budget (and max_active)
+// allows; the first request is admitted whenever nothing else is resident.
+void admit_main(igm_server_s *S) {
+  cudaSetDevice(S->dev);
+  cudaStreamCreateWithFlags(&S->astream, cudaStreamNonBlocking);
+  for (;;) {
+    Request *r = nullptr;
+    long long est = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] {
+        if (S->stop) return true;
+        if (S->queue.empty()) return false;
+        if (S->cfg.max_active > 0 && S->admitting >= S->cfg.max_active) return false;
+        const Request *q = S->queue.front();
+        return S->admitting == 0 ||
+               S->used + estimate(S, q) <= S->cfg.budget_bytes;
+      });
+      if (S->stop) break;
+      r = S->queue.front();
+      S->queue.pop_front();
+      est = estimate(S, r);
+      S->used += est;
+      S->admitting++;
+    }
+    igm_status st = admit(S, r);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->used += (st ? 0 : r->bytes) - est;
+      if (S->used > S->st.peak_bytes) S->st.peak_bytes = S->used;
+      const double raw = (double)handle_bytes_estimate(r->n, r->nnz, &r->prm);
+      if (!st && r->bytes > raw * S->est_scale) S->est_scale = r->bytes / raw;
+      if (!st) S->ready.push_back(r);
+    }
+    if (st) {
+      if (r->h) int_gmres_destroy(r->h);
+      r->h = nullptr;
+      r->bytes = 0;
+      release(S, r);
+      finish(S, r, st);
+      continue;
+    }
+    S->cv_work.notify_all();
+  }
+  cudaStreamSynchronize(S->astream);
+  cudaStreamDestroy(S->astream);
+}
+
+// Round thread: ready systems join, then one round over the active set.
 void worker_main(igm_server_s *S) {
   cudaSetDevice(S->dev);
   cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   for (;;) {
-    // admission by memory budget, in arrival order
-    for (;;) {
-      Request *r = nullptr;
-      {
-        std::unique_lock<std::mutex> lk(S->mu);
-        if (S->stop) break;
-        if (S->queue.empty() && S->active.empty())
-          S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-        if (S->stop || S->queue.empty()) break;
-        if (S->cfg.max_active > 0 && (int)S->active.size() >= S->cfg.max_active) break;
-        Request *q = S->queue.front();
-        long long need = handle_bytes_estimate(q->n, q->nnz, &q->prm);
-        if (!S->active.empty() && S->used + need > S->cfg.budget_bytes) break;
-        S->queue.pop_front();
-        S->used += need;
-        r = q;
-      }
-      long long est = handle_bytes_estimate(r->n, r->nnz, &r->prm);
-      igm_status st = admit(S, r);
-      {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->used += (st ? 0 : r->bytes) - est;
-        if (S->used > S->st.peak_bytes) S->st.peak_bytes = S->used;
-      }
-      if (st) {
-        if (r->h) int_gmres_destroy(r->h);
-        r->h = nullptr;
-        finish(S, r, st);
-        continue;
-      }
-      S->active.push_back(r);
-      S->dirty = true;
-    }
     {
-      std::lock_guard<std::mutex> lk(S->mu);
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->active.empty())
+        S->cv_work.wait(lk, [&] { return S->stop || !S->ready.empty(); });
       if (S->stop) break;
+      if (!S->ready.empty()) {
+        for (Request *r : S->ready) S->active.push_back(r);
+        S->ready.clear();
+        S->dirty = true;
+      }
     }
-    if (S->active.empty()) continue;
     auto t0 = clk::now();
     igm_status st = round(S);
     S->st.busy_s += std::chrono::duration<double>(clk::now() - t0).count();
@@ -209,10 +253,7 @@ void worker_main(igm_server_s *S) {
       for (Request *r : S->active) {
         if (r->h) int_gmres_destroy(r->h);
         r->h = nullptr;
-        {
-          std::lock_guard<std::mutex> lk(S->mu);
-          S->used -= r->bytes;
-        }
+        release(S, r);
         finish(S, r, st);
       }
       S->active.clear();
@@ -243,6 +284,7 @@ igm_status igm_server_create(const igm_server_config *cfg, igm_server *out) {
   S->cfg = *cfg;
   cudaGetDevice(&S->dev);
   S->worker = std::thread(worker_main, S);
+  S->admitter = std::thread(admit_main, S);
   *out = S;
   return IGM_OK;
 }
@@ -275,7 +317,7 @@ igm_status igm_server_submit(igm_server S, int n, int nnz, const int *rowptr, co
     S->queue.push_back(r);
     S->st.submitted++;
   }
-  S->cv_work.notify_one();
+  S->cv_work.notify_all();
   *id = r->id;
   return IGM_OK;
 }
@@ -319,7 +361,11 @@ void igm_server_destroy(igm_server S) {
     S->stop = true;
   }
   S->cv_work.notify_all();
+  if (S->admitter.joinable()) S->admitter.join();
   if (S->worker.joinable()) S->worker.join();
+  for (Request *r : S->ready)
+    if (r->h) int_gmres_destroy(r->h);
+  S->ready.clear();
   for (auto &kv : S->all) delete kv.second;
   delete S;
 }

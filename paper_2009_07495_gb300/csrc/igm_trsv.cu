@@ -16,6 +16,7 @@
 // right-hand sides and far values with cp.async two groups ahead, once a
 // waiter warp has seen the previous chunk reach the groups they need.  A
 // publisher warp releases the chunk's progress after each group.
+#include <mutex>
 #include <type_traits>
 
 #include "igm_dev.cuh"
@@ -950,12 +951,11 @@ int trsv_group_cap(int K) {
 template <int KIND, int KC>
 static void launch_lv(const BatchDev &B, int lower, int which, cudaStream_t st) {
   if (B.nctiles <= 0) return;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_trsv_lv<KIND, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          IGM_TRSV_SMEM);
-    attr_set = true;
-  }
+  });
   k_trsv_lv<KIND, KC><<<B.nctiles, IGM_TRSV_THREADS, IGM_TRSV_SMEM, st>>>(B, lower, which);
 }
 
