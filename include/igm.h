@@ -123,7 +123,20 @@ typedef struct {
                     every substitution never signals its progress, so the
                     next chunk's wait expires and the call returns
                     IGM_ETIMEOUT (0 in normal use)                         */
-  int reserved[4];
+  int fuse_steps;/* integer systems without preconditioner and correction
+                    terms: Arnoldi steps (lines 5-19 each) per persistent
+                    launch; 0 chosen by the autotuner, -1 one SpMV launch
+                    and one Arnoldi launch per step, k > 0 k steps         */
+  int plan_snap; /* partition of the rows over the Arnoldi CTAs: 0 chosen
+                    by the autotuner, -1 equal shares, k in 1..100 a share
+                    boundary inside a system moves to the system's nearer
+                    end when within k % of a share.  The autotuner (fused
+                    systems only; the first refinement call of a batch or
+                    handle) times the m steps of one inner solve for each
+                    choice left to it and keeps the fastest; the results do
+                    not depend on either knob.  In a batch the first
+                    system's values apply.                                 */
+  int reserved[2];
 } igm_params;
 
 #define IGM_MAX_M 128
@@ -143,6 +156,9 @@ typedef struct {
   int shift_retries;          /* inner solves discarded by shift_tune       */
   int beta_final[5];          /* beta7, beta8, beta10, beta13, beta15 at the
                                  end of the solve                           */
+  int fuse_steps;             /* launch configuration the solve ran with:
+                                 Arnoldi steps per fused launch (0 none)    */
+  int plan_snap;              /* ... and the partition's snap (0 equal)     */
 } igm_report;
 
 /* Fills p with the paper's settings: d_f = 30 (Sec. VII-B); precond = 0:

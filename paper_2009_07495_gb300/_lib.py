@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("max_refine", C.c_int), ("inner", C.c_int),
                 ("trsv_chunk", C.c_int), ("trsv_cluster", C.c_int), ("s", C.c_int),
                 ("order", C.c_int), ("shift_tune", C.c_int), ("mgs_wmax", C.c_int),
-                ("wait_us", C.c_int), ("test_stall", C.c_int), ("reserved", C.c_int * 4)]
+                ("wait_us", C.c_int), ("test_stall", C.c_int), ("fuse_steps", C.c_int),
+                ("plan_snap", C.c_int), ("reserved", C.c_int * 2)]
 
     def replace(self, **kw) -> "Params":
         p = Params()
@@ -56,7 +57,8 @@ class Report(C.Structure):
                 ("inner_steps", C.c_int), ("breakdowns", C.c_int), ("status", C.c_int),
                 ("relres", C.c_double), ("relres_unscaled", C.c_double),
                 ("gamma_hist", C.c_double * 64), ("relres_hist", C.c_double * 65),
-                ("shift_retries", C.c_int), ("beta_final", C.c_int * 5)]
+                ("shift_retries", C.c_int), ("beta_final", C.c_int * 5),
+                ("fuse_steps", C.c_int), ("plan_snap", C.c_int)]
 
     def as_dict(self) -> dict:
         k = self.refinements
@@ -66,7 +68,8 @@ class Report(C.Structure):
                     ev=np.array(self.ev[:], dtype=np.int64),
                     gamma_hist=np.array(self.gamma_hist[:min(k, 64)]),
                     relres_hist=np.array(self.relres_hist[:min(k + 1, 65)]),
-                    shift_retries=self.shift_retries, beta_final=tuple(self.beta_final[:]))
+                    shift_retries=self.shift_retries, beta_final=tuple(self.beta_final[:]),
+                    fuse_steps=self.fuse_steps, plan_snap=self.plan_snap)
 
 
 class ServerConfig(C.Structure):

@@ -53,6 +53,58 @@ std::vector<Batch *> g_batches;  // cached multi-system batches
 
 }  // namespace
 
+// The Arnoldi step's partition of the batch's rows over the persistent CTAs
+// (mgs_plan with the given snap), in its own arena, installed in b->bd.
+igm_status set_plan(Batch *b, int snap) {
+  const int ns = (int)b->hs.size();
+  std::vector<int> sysn(ns);
+  for (int s = 0; s < ns; ++s) sysn[s] = b->hs[s]->n;
+  int G = 1, wrows = 0, rows = 0;
+  std::vector<int> mptr, sys_seg;
+  std::vector<Tile> mseg;
+  mgs_plan(sysn, persistent_grid(1 << 30), b->hs[0]->prm.mgs_wmax, snap, G, mptr, mseg, wrows,
+           rows, sys_seg);
+  const int MS = (int)mseg.size();
+  Arena a;
+  int *d_mptr, *d_sysseg, *d_mact;
+  Tile *d_mseg;
+  long long *d_mh;
+  u64 *d_mpart;
+  unsigned *d_mvtag;
+  a.want(&d_mptr, G + 1);
+  a.want(&d_mseg, MS > 0 ? MS : 1);
+  a.want(&d_mh, MS > 0 ? MS : 1);
+  a.want(&d_mpart, 8 * (size_t)(MS > 0 ? MS : 1));
+  a.want(&d_mact, MS > 0 ? MS : 1);
+  a.want(&d_mvtag, MS > 0 ? MS : 1);
+  a.want(&d_sysseg, ns + 1);
+  if (a.commit() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IGM_EOOM, "Arnoldi plan arena");
+  }
+  CK(cudaMemset(d_mpart, 0, 8 * sizeof(u64) * (size_t)(MS > 0 ? MS : 1)));
+  CK(cudaMemset(d_mvtag, 0, sizeof(unsigned) * (size_t)(MS > 0 ? MS : 1)));
+  CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice));
+  if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_sysseg, sys_seg.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+  b->plan_arena.release();
+  b->plan_arena = a;
+  b->snap = snap;
+  BatchDev &B = b->bd;
+  B.mgs_g = G;
+  B.mseg_ptr = d_mptr;
+  B.mseg = d_mseg;
+  B.mseg_h = d_mh;
+  B.nseg = MS;
+  B.mpart = d_mpart;
+  B.mseg_act = d_mact;
+  B.mvtag = d_mvtag;
+  B.sys_seg = d_sysseg;
+  B.mgs_wrows = wrows;
+  B.mgs_rows = rows;
+  return IGM_OK;
+}
+
 igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   Batch *b = new Batch();
   b->hs = hs;
@@ -97,19 +149,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   unsigned *d_ticket, *d_bar;
   double *d_cpart;
   int maxg = persistent_grid(ST);
-  std::vector<int> sysn(ns);
-  for (int s = 0; s < ns; ++s) sysn[s] = hs[s]->n;
-  int mgs_g = 1, mgs_wrows = 0, mgs_rows = 0;
-  std::vector<int> mptr;
-  std::vector<Tile> mseg;
-  std::vector<int> sys_seg;
-  mgs_plan(sysn, persistent_grid(1 << 30), hs[0]->prm.mgs_wmax, mgs_g, mptr, mseg, mgs_wrows,
-           mgs_rows, sys_seg);
-  const int MS = (int)mseg.size();
-  int *d_mptr, *d_sysseg, *d_mact;
-  Tile *d_mseg;
-  long long *d_mh;
-  u64 *d_mpart;
   b->arena.want(&d_tiles, T);
   b->arena.want(&d_ctiles, CT > 0 ? CT : 1);
   b->arena.want(&d_stiles, ST);
@@ -121,12 +160,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   b->arena.want(&d_partd, T);
   b->arena.want(&d_ticket, 4);
   b->arena.want(&d_nact, 1);
-  b->arena.want(&d_mptr, mgs_g + 1);
-  b->arena.want(&d_mseg, MS > 0 ? MS : 1);
-  b->arena.want(&d_mh, MS > 0 ? MS : 1);
-  b->arena.want(&d_mpart, 8 * (size_t)(MS > 0 ? MS : 1));
-  b->arena.want(&d_mact, MS > 0 ? MS : 1);
-  b->arena.want(&d_sysseg, ns + 1);
   if (b->arena.commit() != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -140,10 +173,6 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   CK(cudaMemset(d_ticket, 0, 4 * sizeof(unsigned)));
   CK(cudaMemset(d_nact, 0, sizeof(int)));
   CK(cudaMemset(d_bar, 0, 4 * sizeof(unsigned)));
-  CK(cudaMemset(d_mpart, 0, 8 * sizeof(u64) * (size_t)(MS > 0 ? MS : 1)));
-  CK(cudaMemcpy(d_mptr, mptr.data(), sizeof(int) * (mgs_g + 1), cudaMemcpyHostToDevice));
-  if (MS > 0) CK(cudaMemcpy(d_mseg, mseg.data(), sizeof(Tile) * MS, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_sysseg, sys_seg.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
   BatchDev &B = b->bd;
   B = BatchDev{};
   B.nsys = ns;
@@ -162,20 +191,25 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.bar = d_bar;
   B.cpart = d_cpart;
   B.maxg = maxg;
-  B.mgs_g = mgs_g;
-  B.mseg_ptr = d_mptr;
-  B.mseg = d_mseg;
-  B.mseg_h = d_mh;
-  B.nseg = MS;
-  B.mpart = d_mpart;
-  B.mseg_act = d_mact;
-  B.sys_seg = d_sysseg;
-  B.mgs_wrows = mgs_wrows;
-  B.mgs_rows = mgs_rows;
   B.trsv_maxk = maxk;
   B.max_colors = max_colors;
   B.max_ns = 0;
   for (auto hh : hs) B.max_ns = std::max(B.max_ns, hh->hs.ns);
+  // the fused Arnoldi kernel (line 5 inside): integer systems without
+  // preconditioner and without correction terms
+  b->fuse_ok = b->inner == 0 && !b->any_ilu && B.max_ns == 0;
+  {
+    const int snap = hs[0]->prm.plan_snap;
+    igm_status st = set_plan(b, snap > 0 ? snap : 0);
+    if (st) {
+      delete b;
+      return st;
+    }
+  }
+  const int fs = hs[0]->prm.fuse_steps;
+  B.fuse = (!b->fuse_ok || fs < 0 || mgs_one_cta(B, ns)) ? 0 : fs > 0 ? std::min(fs, b->m) : b->m;
+  // launch configuration left to the autotuner (results do not depend on it)
+  b->tune = b->fuse_ok && !mgs_one_cta(B, ns) && (fs == 0 || hs[0]->prm.plan_snap == 0);
   CK(cudaMallocHost((void **)&b->h_nact, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   *out = b;
@@ -199,6 +233,13 @@ void enqueue_inner(Batch *b, cudaStream_t st) {
   launch_max(B, VEC_R, 2, st);
   launch_norm(B, VEC_R, ACT_NU, 2, st);
   launch_cast_v1(B, st);
+  if (B.fuse > 0) {  // lines 5-19 of every step in persistent launches of B.fuse steps
+    for (int j0 = 0; j0 < b->m; j0 += B.fuse)
+      launch_mgs_fused(B, j0, std::min(b->m, j0 + B.fuse), st);
+    launch_backsub(B, st);
+    launch_update(B, st);
+    return;
+  }
   for (int j = 0; j < b->m; ++j) {
     launch_spmv(B, j, st);
     if (b->any_ilu) {  // line 5'
@@ -388,6 +429,9 @@ igm_status check_params(const igm_params *p) {
   if (p->mgs_wmax < -1) return fail(IGM_EINVAL, "mgs_wmax must be -1, 0 or positive");
   if (p->wait_us < 0) return fail(IGM_EINVAL, "wait_us must be >= 0");
   if (p->test_stall != 0 && p->test_stall != 1) return fail(IGM_EINVAL, "test_stall must be 0 or 1");
+  if (p->fuse_steps < -1) return fail(IGM_EINVAL, "fuse_steps must be -1, 0 or positive");
+  if (p->plan_snap < -1 || p->plan_snap > 100)
+    return fail(IGM_EINVAL, "plan_snap must be -1, 0 or 1 ... 100");
   if (!(p->trsv_cluster == 0 || p->trsv_cluster == 1 || p->trsv_cluster == 2 ||
         p->trsv_cluster == 4 || p->trsv_cluster == 8))
     return fail(IGM_EINVAL, "trsv_cluster must be 0, 1, 2, 4 or 8");
@@ -1085,9 +1129,99 @@ namespace {
 
 // Fig. 1 over a batch: b = D^-1 bh, norms, then {test, inner solve} until
 // every system has converged or reached max_refine.
+// device error flags of a batch (the grid kernels report in the first
+// system's flags)
+igm_status check_errors(Batch *b, cudaStream_t s) {
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, &b->hs[0]->d_sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return e ? err_status(e) : IGM_OK;
+}
+
+// The autotuner: for every launch configuration left open (plan snap,
+// steps per fused launch), set up the first inner solve of Fig. 1 from the
+// loaded right-hand sides (x = 0) and time its m Arnoldi steps (lines 5-19)
+// with CUDA events; keep the fastest.  The integer results are the same for
+// every configuration, and the refinement loop that follows starts again
+// from its own set-up (k_init_scal resets every counter the trial touched).
+igm_status tune_batch(Batch *b, cudaStream_t s) {
+  if (!b->tune) return IGM_OK;
+  b->tune = false;
+  const igm_params &P = b->hs[0]->prm;
+  const int m = b->m, ns = (int)b->hs.size();
+  std::vector<int> snaps, fuses;
+  if (P.plan_snap == 0) snaps = {0, 25, 50};
+  else snaps = {P.plan_snap > 0 ? P.plan_snap : 0};
+  if (P.fuse_steps == 0) {
+    for (int f : {m, (m + 1) / 2, 10, 5, 0})
+      if (std::find(fuses.begin(), fuses.end(), std::min(f, m)) == fuses.end())
+        fuses.push_back(std::min(f, m));
+  } else {
+    fuses = {P.fuse_steps < 0 ? 0 : std::min(P.fuse_steps, m)};
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_snap = b->snap, best_fuse = b->bd.fuse;
+  igm_status st = IGM_OK;
+  for (int snap : snaps) {
+    if (snap != b->snap && (st = set_plan(b, snap))) break;
+    const BatchDev &B = b->bd;
+    if (mgs_one_cta(B, ns)) continue;
+    for (int f : fuses) {
+      b->bd.fuse = f;
+      if ((st = ir_init_host(b, s))) break;
+      launch_resid(B, 0, s);
+      launch_norm(B, VEC_R, ACT_RHO, 1, s);
+      launch_rhs(B, s);
+      launch_max(B, VEC_R, 2, s);
+      launch_norm(B, VEC_R, ACT_NU, 2, s);
+      launch_cast_v1(B, s);
+      CK(cudaEventRecord(e0, s));
+      if (f > 0) {
+        for (int j0 = 0; j0 < m; j0 += f) launch_mgs_fused(B, j0, std::min(m, j0 + f), s);
+      } else {
+        for (int j = 0; j < m; ++j) {
+          launch_spmv(B, j, s);
+          launch_mgs_step(B, j, s);
+        }
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      CKL();
+      if ((st = check_errors(b, s))) break;
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_snap = snap;
+        best_fuse = f;
+      }
+    }
+    if (st) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  if (best_snap != b->snap && (st = set_plan(b, best_snap))) return st;
+  b->bd.fuse = mgs_one_cta(b->bd, ns) ? 0 : best_fuse;
+  // the captured graphs hold the batch descriptor by value
+  if (b->g_check) cudaGraphExecDestroy(b->g_check);
+  if (b->g_cycle) cudaGraphExecDestroy(b->g_cycle);
+  b->g_check = b->g_cycle = nullptr;
+  return IGM_OK;
+}
+
 igm_status run_ir(Batch *b, cudaStream_t s) {
   const BatchDev &B = b->bd;
-  igm_status st = capture_graphs(b);
+  igm_status st = tune_batch(b, s);
+  if (st) return st;
+  for (igm_handle h : b->hs) {
+    h->ran_fuse = B.fuse;
+    h->ran_snap = b->snap;
+  }
+  st = capture_graphs(b);
   if (st) return st;
   st = ir_init_host(b, s);
   if (st) return st;
@@ -1114,6 +1248,10 @@ igm_status collect_host(igm_handle h, igm_report *rep, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   e = sc.err;
   fill_report(sc, rep);
+  if (rep) {
+    rep->fuse_steps = h->ran_fuse;
+    rep->plan_snap = h->ran_snap;
+  }
   if (e) {
     igm_status st = err_status(e);
     if (rep) rep->status = st;
@@ -1204,7 +1342,11 @@ igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_repor
   launch_arm(B, s);
   enqueue_inner(b, s);
   CKL();
-  g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) + (long long)b->m * (4 + (b->any_ilu ? 2 : 0));
+  h->ran_fuse = B.fuse;
+  h->ran_snap = b->snap;
+  g_launches += 3 + 5 + (b->any_ilu ? 2 : 0) +
+                (B.fuse > 0 ? (long long)(b->m + B.fuse - 1) / B.fuse
+                            : (long long)b->m * (4 + (b->any_ilu ? 2 : 0)));
   {
     igm_status ss = store_vec(h, xk, h->hs.xk, s);
     if (ss) return ss;

@@ -500,6 +500,12 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// orders this thread's earlier generic-proxy accesses of global memory
+// before its later async-proxy (bulk copy) accesses of global memory
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // iteration bound of the time-bounded waits (the time limit ends them first)
 #define IGM_WAIT_ITERS (1 << 28)
 

@@ -75,6 +75,7 @@ struct igm_handle_s {
   Batch *solo = nullptr;  // batch of one, with its captured graphs
   int *perm = nullptr;    // multicolour order: perm[new] = old (device)
   double *ptmp = nullptr; // staging vector of the permutation (device)
+  int ran_fuse = 0, ran_snap = 0;  // launch configuration of the last solve
 };
 
 // right-hand sides in, solutions out, in the caller's row order
@@ -85,7 +86,11 @@ struct Batch {
   std::vector<igm_handle> hs;
   long long nodes_check = 0, nodes_cycle = 0;
   int m = 0, any_ilu = 0, inner = 0, max_chunk = 0;
+  int fuse_ok = 0;        // the fused Arnoldi kernel applies
+  int snap = 0;           // the Arnoldi plan's snap (mgs_plan)
+  bool tune = false;      // the autotuner still has to choose
   Arena arena;
+  Arena plan_arena;       // the Arnoldi step's plan (set_plan)
   BatchDev bd{};
   int *h_nact = nullptr;  // pinned
   cudaStream_t cap = nullptr;
@@ -96,6 +101,7 @@ struct Batch {
     if (cap) cudaStreamDestroy(cap);
     if (h_nact) cudaFreeHost(h_nact);
     arena.release();
+    plan_arena.release();
   }
 };
 
@@ -103,6 +109,7 @@ struct Batch {
 // shared helpers (igm_api.cu)
 extern thread_local std::string g_err;
 igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out);
+igm_status set_plan(Batch *b, int snap);
 igm_status fail(igm_status st, const char *fmt, ...);
 extern std::atomic<long long> g_launches;
 void enqueue_inner_host(Batch *b, cudaStream_t st);

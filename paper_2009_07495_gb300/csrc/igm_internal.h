@@ -242,7 +242,10 @@ struct BatchDev {
   u64 *mpart;              // 2 slots (pass parity) x nseg x 4 words: a
                            // pass's exact sum over each segment, tagged
   int *mseg_act;           // per segment beyond a CTA's descriptor cache:
-                           // active | narrow << 1 at the launch's start
+                           // active | narrow << 1 of the current step
+  unsigned *mvtag;         // per segment: the last step whose basis rows
+                           // the fused Arnoldi kernel published (tagged)
+  int fuse;                // steps per fused Arnoldi launch (0: not fused)
   const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
   int mgs_wrows;           // rows each CTA keeps resident in shared memory
   int mgs_rows;            // most rows of a CTA
@@ -255,5 +258,20 @@ struct BatchDev {
 enum Vec : int { VEC_B = 0, VEC_R = 1, VEC_BH = 2 };
 // what the last CTA does with a finished norm
 enum NormAct : int { ACT_NB = 0, ACT_RHO = 1, ACT_NU = 2, ACT_NBH = 3, ACT_UNSC = 4 };
+
+// Arnoldi step (lines 6-19): one CTA per SM of IGM_MGS_BLOCK threads in the
+// grid mode; the one-CTA mode runs IGM_MGS_ONE_BLOCK threads (IGM_RPT rows
+// a thread) over at most IGM_MSEG_CACHE systems
+#define IGM_MGS_BLOCK 1024
+#define IGM_MGS_ONE_BLOCK 256
+#define IGM_MSEG_CACHE 64
+
+// the step's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows in
+// all, every row of w in shared memory, each system one segment of it (ns
+// segments), every segment descriptor cached in shared memory
+__host__ __device__ __forceinline__ bool mgs_one_cta(const BatchDev &B, int ns) {
+  return B.mgs_g == 1 && B.mgs_rows > 0 && B.mgs_rows <= IGM_MGS_BLOCK &&
+         B.mgs_wrows == B.mgs_rows && ns <= IGM_MSEG_CACHE;
+}
 
 }  // namespace igm

@@ -18,10 +18,6 @@
 
 namespace igm {
 
-// one CTA per SM: few grid-barrier arrivals, many rows in flight per CTA
-#define IGM_MGS_BLOCK 1024
-// threads of the one-CTA mode (at most IGM_MGS_BLOCK rows: IGM_RPT per thread)
-#define IGM_MGS_ONE_BLOCK 256
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
   unsigned v;
@@ -99,7 +95,6 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
 }
 
 #define IGM_RPT 4           // rows in flight per thread
-#define IGM_MSEG_CACHE 64   // segments of the one-CTA mode (descriptors in shared memory)
 #define IGM_MGS_GCACHE 32   // segment descriptors a CTA of the grid mode keeps in shared memory
 // CTA rows of the grid mode resident in shared memory: w (int64) and two
 // int32 basis vectors, 16 bytes a row (218 KB)
@@ -107,13 +102,7 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
 #define IGM_MGS_ROWB 16
 
 
-// the step's one-CTA mode: one CTA holding at most IGM_MGS_BLOCK rows in
-// all, every row of w in shared memory, each system one segment of it (ns
-// segments), every segment descriptor cached in shared memory
-__host__ __device__ __forceinline__ bool mgs_one_cta(const BatchDev &B, int ns) {
-  return B.mgs_g == 1 && B.mgs_rows > 0 && B.mgs_rows <= IGM_MGS_BLOCK &&
-         B.mgs_wrows == B.mgs_rows && ns <= IGM_MSEG_CACHE;
-}
+
 
 // a segment as the step kernel sees it: its system's arrays and shifts
 struct MSegC {
@@ -399,13 +388,14 @@ struct MPass {
   i64 hs;
   int s8, sA;
   int qv, qw, nr;     // resident basis rows, resident w rows, rows
+  bool w0s;           // line 5 left w of the resident rows in shared memory
   i64 *wg, *ws;       // w in global memory (segment) and in shared memory
   const int *vps, *vis;  // resident v_{i-1}, v_i (shared memory)
 };
 
-// resident rows [0, qv): w, v_{i-1} and v_i in shared memory (w from global
-// memory at pass 0, stored into shared memory); each thread the rows
-// q = threadIdx.x (mod IGM_MGS_BLOCK)
+// resident rows [0, qv): w, v_{i-1} and v_i in shared memory (at pass 0 w
+// from global memory unless line 5 left it in shared memory; stored into
+// shared memory); each thread the rows q = threadIdx.x (mod IGM_MGS_BLOCK)
 template <int MODE, bool HS32>
 __device__ __forceinline__ void pass_res(const MPass &P, i128 &part, unsigned &evA,
                                          unsigned &evB) {
@@ -416,7 +406,7 @@ __device__ __forceinline__ void pass_res(const MPass &P, i128 &part, unsigned &e
     for (int u = 0; u < IGM_RPT; ++u) {
       const int q = q0 + u * IGM_MGS_BLOCK;
       const bool ok = q < P.qv;
-      wv[u] = !ok ? 0 : MODE == 0 ? P.wg[q] : P.ws[q];
+      wv[u] = !ok ? 0 : (MODE == 0 && !P.w0s) ? P.wg[q] : P.ws[q];
       pv[u] = (MODE > 0 && ok) ? P.vps[q] : 0;
       qq[u] = (MODE < 2 && ok) ? P.vis[q] : 0;
     }
@@ -443,7 +433,7 @@ __device__ __forceinline__ void pass_glob(const MPass &P, const VT *vp, const VT
     for (int u = 0; u < R; ++u) {
       const int q = q0 + u * IGM_MGS_BLOCK;
       const bool ok = q < P.nr;
-      wv[u] = !ok ? 0 : (MODE > 0 && q < P.qw) ? P.ws[q] : P.wg[q];
+      wv[u] = !ok ? 0 : ((MODE > 0 || P.w0s) && q < P.qw) ? P.ws[q] : P.wg[q];
       pv[u] = (MODE > 0 && ok) ? vp[q] : 0;
       qq[u] = (MODE < 2 && ok) ? vi[q] : 0;
     }
@@ -480,19 +470,86 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
 #define IGM_MGS_VB(S) ((((S) + 3) & ~3) + IGM_MGS_VPAD)
 #define IGM_MGS_SMEM(S) (IGM_MGS_VOFF(S) + 2 * sizeof(int) * (size_t)IGM_MGS_VB(S))
 
-// Grid mode: every CTA owns the same rows in every pass (a balanced partition
-// of all systems' rows, planned on the host).  The first B.mgs_wrows of them
-// (in segments among the first IGM_MGS_GCACHE) are resident in shared
-// memory: w from pass 0 to line 11, and (while every basis entry of the
-// inner solve fits int32) the int32 words of v_{i-1} and v_i in two
+// line 5 (Table 3) for the rows of segment c in the fused kernel: exact
+// int128 row sums over the SELL-32 copy of Abar_0 (one term, s = 0), the
+// basis vector read from L2 (other CTAs wrote it during this launch), w into
+// shared memory for the resident rows and global memory for the others;
+// each thread the rows q = threadIdx.x (mod IGM_MGS_BLOCK), the rows it owns
+// in the passes
+template <bool NAR>
+__device__ __forceinline__ void seg_spmv(const SysDev *s, const MSegC &c, int j, int qw, i64 *ws,
+                                         unsigned &ev) {
+  const i64 *vj = s->V + (size_t)j * c.n;
+  const int *vj32 = s->V32 + (size_t)j * c.n;
+  const long long *sptr = s->sptr;
+  const i64 *sval = s->sval;
+  const int *scol = s->scol;
+  for (int q = threadIdx.x; q < c.nrows; q += IGM_MGS_BLOCK) {
+    const int i = c.row0 + q;
+    const int sl = i >> 5;
+    const long long base = sptr[sl] + (i & 31);
+    const int len = (int)((sptr[sl + 1] - sptr[sl]) >> 5);
+    i128 acc = 0;
+    for (int k0 = 0; k0 < len; k0 += 8) {
+      i64 a[8];
+      int cc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = k0 + u < len;
+        a[u] = ok ? __ldcs(sval + base + 32 * (k0 + u)) : 0;
+        cc[u] = ok ? __ldcs(scol + base + 32 * (k0 + u)) : i;
+      }
+      i64 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = NAR ? (i64)__ldcg(vj32 + cc[u]) : __ldcg(vj + cc[u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
+    }
+    ev += out64(acc);
+    const i64 w = wrap(acc);
+    if (q < qw) ws[q] = w;
+    else c.w[q] = w;
+  }
+}
+
+// spin (bounded) until every segment of system `sys` has published tag in
+// mvtag; one segment per thread; false (in every thread) when the bound
+// expired or a CTA has reported an expired wait
+__device__ bool mvtag_wait(const BatchDev &B, int sys, unsigned tag, const unsigned *err0) {
+  const int lo = B.sys_seg[sys], hi = B.sys_seg[sys + 1];
+  bool ok = true;
+  for (int g = lo + threadIdx.x; g < hi && ok; g += blockDim.x)
+    for (int it = 0; ld_relaxed_u32(B.mvtag + g) != tag; ++it) {
+      if (it > IGM_SPIN_MAX || ((it & 255) == 255 && (ld_relaxed_u32(err0) & ERR_TIMEOUT))) {
+        ok = false;
+        break;
+      }
+      if (it > 32) __nanosleep(32);
+    }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Grid mode: every CTA owns the same rows in every pass (a partition of all
+// systems' rows planned on the host).  The first B.mgs_wrows of them (in
+// segments among the first IGM_MGS_GCACHE) are resident in shared memory: w
+// from line 5 (FUSED) or pass 0 to line 11, and (while every basis entry of
+// the inner solve fits int32) the int32 words of v_{i-1} and v_i in two
 // buffers; v_{i+1} is bulk-copied into the buffer of v_{i-1} while the
 // pass's sums travel, so a pass over resident rows reads nothing from global
 // memory.  Further rows keep w in global memory and read the basis from
-// global memory (the next vector prefetched into L2 during the pass).  There is no grid
-// barrier: each CTA publishes its tagged sum of the pass per segment and
-// reads those of its systems' segments, so a CTA waits only for the CTAs
-// that share a system with it.
-__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j) {
+// global memory (the next vector prefetched into L2 during the pass).
+// There is no grid barrier: each CTA publishes its tagged sum of the pass
+// per segment and reads those of its systems' segments, so a CTA waits only
+// for the CTAs that share a system with it; a system held by one CTA alone
+// uses the CTA's sum directly.
+//
+// Not FUSED: lines 6-19 of step j0 (line 5 ran before).  FUSED: steps j0 ..
+// j1-1 each with line 5 first (systems without preconditioner and without
+// correction terms); after line 11 and lines 12-19 of step j the CTA
+// publishes (j, its segments) in mvtag, and before line 5 of step j + 1 a
+// CTA waits for every segment of its systems, so v_{j+1} is complete.
+template <bool FUSED>
+__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j0, int j1) {
   constexpr int BS = IGM_MGS_BLOCK;
   extern __shared__ __align__(16) unsigned char smem[];
   const int S = B.mgs_wrows;  // resident rows of this CTA
@@ -501,8 +558,10 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
   const int vb = IGM_MGS_VB(S);                               // words of one
   __shared__ MSegC s_seg[IGM_MGS_GCACHE + 1];  // + one slot for the others in turn
   __shared__ i64 s_h[IGM_MGS_GCACHE];
+  __shared__ i128 s_tot[IGM_MGS_GCACHE];  // pass totals of systems held by this CTA alone
   __shared__ __align__(8) u64 s_vbar[2];  // bulk copies into basis buffer 0 / 1
-  __shared__ unsigned s_epoch, s_vbytes;
+  __shared__ unsigned s_vn[2];            // copies issued into each buffer
+  __shared__ unsigned s_epoch;
   __shared__ int s_fail;
   unsigned *err0 = &B.sys[0]->sc->err;
   const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
@@ -510,23 +569,25 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
   // now, before this CTA publishes anything) in mseg_act
   for (int k = threadIdx.x; k < ns; k += BS) {
     if (k < IGM_MGS_GCACHE) {
-      mseg_make(B, g0 + k, j, s_seg[k]);
+      mseg_make(B, g0 + k, j0, s_seg[k]);
     } else {
       MSegC c;
-      mseg_make(B, g0 + k, j, c);
+      mseg_make(B, g0 + k, j0, c);
       B.mseg_act[g0 + k] = c.active | (c.narrow << 1);
     }
   }
   if (threadIdx.x == 0) {
     s_epoch = ld_relaxed_u32(B.bar + 2);
     s_fail = 0;
+    s_vn[0] = s_vn[1] = 0;
     mbar_init(&s_vbar[0], 1);
     mbar_init(&s_vbar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const unsigned epoch = s_epoch;
-  // a segment's descriptor with the flags taken at the start (into c)
+  const unsigned e16 = (s_epoch & 0xffffu) << 16;
+  int j = j0;
+  // a segment's descriptor with the flags of the current step (into c)
   auto seg_make = [&](int k, MSegC &c) {
     mseg_make(B, g0 + k, j, c);
     const int f = B.mseg_act[g0 + k];
@@ -542,6 +603,10 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     __syncthreads();
     return s_seg[IGM_MGS_GCACHE];
   };
+  // a cached segment whose system no other CTA holds
+  auto alone = [&](const MSegC &c, int k) {
+    return k < IGM_MGS_GCACHE && B.sys_seg[c.sys + 1] - B.sys_seg[c.sys] == 1;
+  };
   // resident rows of segment k: w (res_w) and the basis (res_v: cached
   // segments while narrow)
   auto res_w = [&](const MSegC &c) { return min(max(S - c.off, 0), c.nrows); };
@@ -554,19 +619,17 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     return sv + (size_t)(i & 1) * vb + ((c.off + 3) & ~3) + 12 * k +
            (int)(((size_t)i * c.n + c.row0) & 3);
   };
-  // bulk-copy v_i of every resident segment into buffer i & 1 (thread 0,
-  // after a block barrier behind the last reads of that buffer)
+  // thread 0: bulk-copy v_i of every resident segment into buffer i & 1
+  // (after a block barrier behind the last reads of that buffer)
   auto stage = [&](int i) {
     unsigned bytes = 0;
     for (int k = 0; k < ns && k < IGM_MGS_GCACHE; ++k) {
       const MSegC &c = s_seg[k];
       const int qv = c.active ? res_v(c, k) : 0;
       if (qv == 0) continue;
-      const size_t e0 = (size_t)i * c.n + c.row0;
-      const int pad = (int)(e0 & 3);
+      const int pad = (int)(((size_t)i * c.n + c.row0) & 3);
       bytes += 4u * (unsigned)((pad + qv + 3) & ~3);
     }
-    s_vbytes = bytes;
     if (bytes == 0) return;
     fence_proxy_async();
     mbar_expect_tx(&s_vbar[i & 1], bytes);
@@ -579,87 +642,138 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
       bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)((pad + qv + 3) & ~3),
                &s_vbar[i & 1]);
     }
+    s_vn[i & 1] += 1;
   };
-  if (threadIdx.x == 0) stage(0);
-  __syncthreads();
-  const bool vst = s_vbytes != 0;  // the same for every vector
-  int staged = 0;                  // the last vector copied
-  for (int i = 0; i <= j + 1; ++i) {
-    const unsigned tag = (epoch << 8) | (unsigned)(i + 1);
-    // v_i of the resident rows is in place (v_{i-1} already was)
-    if (vst && i <= j && !mbar_wait(&s_vbar[i & 1], (unsigned)(i >> 1) & 1u, err0, 1000000000ull))
-      s_fail = 1;
-    for (int k = 0; k < ns; ++k) {
-      const MSegC &c = seg(k);
-      if (!c.active) continue;
-      MPass P;
-      P.nr = c.nrows;
-      P.qw = res_w(c);
-      P.qv = res_v(c, k);
-      // pull the global rows of v_{i+1} into L2 while this pass runs
-      if (i + 1 <= j && P.qv < P.nr) {
-        const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
-        const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
-        const size_t bytes = (size_t)(P.nr - P.qv) * (c.narrow ? sizeof(int) : sizeof(i64));
-        for (size_t a = (size_t)threadIdx.x * 128; a < bytes; a += (size_t)BS * 128)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(base + a));
-      }
-      P.hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
-      P.wg = c.w;
-      P.ws = sw + c.off;
-      P.s8 = shc(c.df - c.b8);
-      P.sA = i <= j ? shc(c.b7) : shc(c.b10);
-      if (P.qv > 0) {
-        P.vps = vbase(c, k, i > 0 ? i - 1 : 0);
-        P.vis = vbase(c, k, i <= j ? i : 0);
-      }
-      const bool hs32 = P.hs == (i64)(int)P.hs;
-      i128 part = 0;
-      unsigned evA = 0, evB = 0;
-      if (i == 0) pass_seg<0, true>(P, c, i, j, part, evA, evB);
-      else if (i <= j) {
-        if (hs32) pass_seg<1, true>(P, c, i, j, part, evA, evB);
-        else pass_seg<1, false>(P, c, i, j, part, evA, evB);
-      } else {
-        if (hs32) pass_seg<2, true>(P, c, i, j, part, evA, evB);
-        else pass_seg<2, false>(P, c, i, j, part, evA, evB);
-      }
-      flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
-      flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
-      part = block_sum_i128(part);
-      if (threadIdx.x == 0) mslot_put(mslot(B, i & 1, g0 + k), part, tag);
-    }
-    // every read of pass i is behind the block barriers of the sums: v_{i+1}
-    // may overwrite the buffer of v_{i-1}
+  // wait for the last copy into buffer b (an expired wait fails the launch)
+  auto vwait = [&](int b) {
+    const unsigned nb = s_vn[b];
+    if (nb > 0 && !mbar_wait(&s_vbar[b], (nb - 1) & 1u, err0, 1000000000ull)) s_fail = 1;
+  };
+  if (!FUSED) {
+    if (threadIdx.x == 0) stage(0);
     __syncthreads();
-    if (vst && i + 1 <= j && !s_fail) {
-      if (threadIdx.x == 0) stage(i + 1);
-      staged = i + 1;
-    }
-    // each segment's coefficient from its system's total (tagged slots)
-    for (int k = 0; k < ns && !s_fail; ++k) {
-      const MSegC &c = seg(k);
-      if (!c.active) continue;
-      i128 tot;
-      if (!mseg_total(B, c.sys, i & 1, tag, err0, tot)) {
-        if (threadIdx.x == 0) s_fail = 1;
-        __syncthreads();
-        break;
-      }
-      if (threadIdx.x == 0) {
-        const i64 h = mseg_coef(c, tot, i, j);
-        if (k < IGM_MGS_GCACHE) s_h[k] = h;
-        else B.mseg_h[g0 + k] = h;
-      }
-    }
-    __syncthreads();
-    if (s_fail) break;
   }
-  if (s_fail) {
-    // the copy in flight lands before the CTA leaves (bounded again)
-    if (vst) mbar_wait(&s_vbar[staged & 1], (unsigned)(staged >> 1) & 1u, err0, 1000000000ull);
-    if (threadIdx.x == 0) atomicOr(err0, ERR_TIMEOUT);
-  } else {
+  for (; j < j1 && !s_fail; ++j) {
+    if (FUSED) {
+      if (j > j0) {
+        // v_j of every active system: each of its segments published step j - 1
+        for (int k = 0; k < ns && !s_fail; ++k) {
+          const MSegC &c = seg(k);
+          if (!c.active || alone(c, k)) continue;
+          if (!mvtag_wait(B, c.sys, e16 | ((unsigned)(j - 1) << 8) | 0xffu, err0)) {
+            if (threadIdx.x == 0) s_fail = 1;
+            __syncthreads();
+          }
+        }
+        __threadfence();
+        __syncthreads();
+        if (s_fail) break;
+        // the flags of step j (a breakdown or the end of a system's steps
+        // at step j - 1, a basis entry outside int32 from line 11)
+        for (int k = threadIdx.x; k < ns; k += BS) {
+          MSegC c;
+          if (k < IGM_MGS_GCACHE) c = s_seg[k];
+          else seg_make(k, c);
+          const SysDev *s = B.sys[c.sys];
+          const int act = c.active && m_step(s, j);
+          const int nar = c.narrow && s->sc->vwide == 0;
+          if (k < IGM_MGS_GCACHE) {
+            s_seg[k].active = act;
+            s_seg[k].narrow = nar;
+          } else {
+            B.mseg_act[g0 + k] = act | (nar << 1);
+          }
+        }
+        __syncthreads();
+      }
+      // v_0 for pass 0 travels while line 5 runs
+      if (threadIdx.x == 0) stage(0);
+      // line 5
+      for (int k = 0; k < ns; ++k) {
+        const MSegC &c = seg(k);
+        if (!c.active) continue;
+        const SysDev *s = B.sys[c.sys];
+        unsigned ev = 0;
+        if (c.narrow) seg_spmv<true>(s, c, j, res_w(c), sw + c.off, ev);
+        else seg_spmv<false>(s, c, j, res_w(c), sw + c.off, ev);
+        flush_ev(ev, &c.sc->ev[IGM_EV_L5]);
+      }
+      __syncthreads();
+    }
+    for (int i = 0; i <= j + 1; ++i) {
+      const unsigned tag = e16 | ((unsigned)j << 8) | (unsigned)(i + 1);
+      // v_i of the resident rows is in place (v_{i-1} already was)
+      if (i <= j) vwait(i & 1);
+      for (int k = 0; k < ns; ++k) {
+        const MSegC &c = seg(k);
+        if (!c.active) continue;
+        MPass P;
+        P.nr = c.nrows;
+        P.qw = res_w(c);
+        P.qv = res_v(c, k);
+        P.w0s = FUSED;
+        // pull the global rows of v_{i+1} into L2 while this pass runs
+        if (i + 1 <= j && P.qv < P.nr) {
+          const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
+          const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
+          const size_t bytes = (size_t)(P.nr - P.qv) * (c.narrow ? sizeof(int) : sizeof(i64));
+          for (size_t a = (size_t)threadIdx.x * 128; a < bytes; a += (size_t)BS * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(base + a));
+        }
+        P.hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
+        P.wg = c.w;
+        P.ws = sw + c.off;
+        P.s8 = shc(c.df - c.b8);
+        P.sA = i <= j ? shc(c.b7) : shc(c.b10);
+        if (P.qv > 0) {
+          P.vps = vbase(c, k, i > 0 ? i - 1 : 0);
+          P.vis = vbase(c, k, i <= j ? i : 0);
+        }
+        const bool hs32 = P.hs == (i64)(int)P.hs;
+        i128 part = 0;
+        unsigned evA = 0, evB = 0;
+        if (i == 0) pass_seg<0, true>(P, c, i, j, part, evA, evB);
+        else if (i <= j) {
+          if (hs32) pass_seg<1, true>(P, c, i, j, part, evA, evB);
+          else pass_seg<1, false>(P, c, i, j, part, evA, evB);
+        } else {
+          if (hs32) pass_seg<2, true>(P, c, i, j, part, evA, evB);
+          else pass_seg<2, false>(P, c, i, j, part, evA, evB);
+        }
+        flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
+        flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+        part = block_sum_i128(part);
+        if (threadIdx.x == 0) {
+          if (alone(c, k)) s_tot[k] = part;
+          else mslot_put(mslot(B, i & 1, g0 + k), part, tag);
+        }
+      }
+      // every read of pass i is behind the block barriers of the sums: v_{i+1}
+      // may overwrite the buffer of v_{i-1}
+      __syncthreads();
+      if (i + 1 <= j && !s_fail && threadIdx.x == 0) stage(i + 1);
+      // each segment's coefficient from its system's total
+      for (int k = 0; k < ns && !s_fail; ++k) {
+        const MSegC &c = seg(k);
+        if (!c.active) continue;
+        i128 tot = 0;
+        if (alone(c, k)) {
+          tot = s_tot[k];
+        } else if (!mseg_total(B, c.sys, i & 1, tag, err0, tot)) {
+          if (threadIdx.x == 0) s_fail = 1;
+          __syncthreads();
+          break;
+        }
+        if (threadIdx.x == 0) {
+          const i64 h = mseg_coef(c, tot, i, j);
+          if (k < IGM_MGS_GCACHE) s_h[k] = h;
+          else B.mseg_h[g0 + k] = h;
+        }
+      }
+      __syncthreads();
+      if (s_fail) break;
+    }
+    if (s_fail) break;
     // line 11 for every system whose divisor is non-zero
     for (int k = 0; k < ns; ++k) {
       const MSegC &c = seg(k);
@@ -694,6 +808,9 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
       if (__syncthreads_or(evr != 0) && threadIdx.x == 0) atomicOr(&c.sc->vwide, 1);
       flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
     }
+    // this CTA's basis rows, written through the generic proxy, are read by
+    // its later bulk copies
+    if (FUSED) fence_proxy_async_global();
     // lines 10 (store) and 12-19, one thread per system, after line 11: the
     // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
     __syncthreads();
@@ -706,6 +823,25 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
         if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
       }
     }
+    if (FUSED) {
+      // publish step j: the CTA's basis rows, flags and (first CTA) lines
+      // 12-19 before the tags
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        for (int k = 0; k < ns; ++k) {
+          const bool act = k < IGM_MGS_GCACHE ? s_seg[k].active : (B.mseg_act[g0 + k] & 1);
+          if (act) st_relaxed_u32(B.mvtag + g0 + k, e16 | ((unsigned)j << 8) | 0xffu);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (s_fail) {
+    // the copies in flight land before the CTA leaves (bounded again)
+    vwait(0);
+    vwait(1);
+    if (threadIdx.x == 0) atomicOr(err0, ERR_TIMEOUT);
   }
   // the last CTA to finish moves the launch epoch on (every CTA of this
   // launch read it before publishing anything)
@@ -714,7 +850,7 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     const unsigned done = atom_add_acq_rel_u32(B.bar + 3, 1u);
     if (done == gridDim.x - 1) {
       st_relaxed_u32(B.bar + 3, 0u);
-      st_relaxed_u32(B.bar + 2, epoch + 1u);
+      st_relaxed_u32(B.bar + 2, s_epoch + 1u);
     }
   }
 }
@@ -845,12 +981,18 @@ int persistent_grid(int ntiles) {
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     // co-resident CTAs with the most dynamic shared memory a plan may give
     // the integer step (IGM_MGS_WMAX resident rows)
-    cudaFuncSetAttribute(k_mgs_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mgs_grid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_grid, IGM_MGS_BLOCK,
+    cudaFuncSetAttribute(k_mgs_grid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
+    int a = 0, a2 = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_grid<false>, IGM_MGS_BLOCK,
                                                       IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_mgs_grid<true>, IGM_MGS_BLOCK,
+                                                      IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
+      a2 = 1;
+    a = a < a2 ? a : a2;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f_mgs_step, IGM_MGS_BLOCK, 0) !=
         cudaSuccess)
       b = 1;
@@ -872,8 +1014,14 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   f_givens_step<<<(B.nsys + 127) / 128, 128, 0, st>>>(B, j, G);
 }
 
-void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::vector<int> &ptr,
-              std::vector<Tile> &seg, int &wrows, int &rows, std::vector<int> &sys_seg) {
+// The Arnoldi step's partition: CTA c takes the contiguous global rows
+// [b_c, b_{c+1}) of the batch (systems in order), b_c = N c / G (equal
+// shares); with snap > 0 a boundary inside a system moves to that system's
+// nearer end when it is within snap % of a share, so that more systems lie
+// in one CTA whole (no exchange of pass sums) at the price of balance.
+void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, int &G,
+              std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows,
+              std::vector<int> &sys_seg) {
   // rows a CTA may keep resident in shared memory: 0 automatic, -1 none,
   // k > 0 at most k (never above what the kernel reserves)
   const int cap = wmax == 0 ? IGM_MGS_WMAX : wmax < 0 ? 0 : std::min(wmax, IGM_MGS_WMAX);
@@ -884,10 +1032,29 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int &G, std::ve
   G = (int)(g < 1 ? 1 : g);
   ptr.assign(G + 1, 0);
   seg.clear();
+  // CTA boundaries (snapped to system ends where close enough)
+  std::vector<long long> bnd(G + 1);
+  {
+    std::vector<long long> first(n.size() + 1, 0);
+    for (size_t k = 0; k < n.size(); ++k) first[k + 1] = first[k] + n[k];
+    const long long share = (N + G - 1) / G, tol = share * (long long)std::max(snap, 0) / 100;
+    size_t k = 0;
+    for (int c = 0; c <= G; ++c) {
+      long long b = N * c / G;
+      if (snap > 0 && c > 0 && c < G) {
+        while (first[k + 1] <= b) ++k;  // b inside system k: [first[k], first[k+1])
+        const long long dlo = b - first[k], dhi = first[k + 1] - b;
+        if (dlo > 0 && dlo <= tol && dlo <= dhi) b = first[k];
+        else if (dlo > 0 && dhi <= tol) b = first[k + 1];
+      }
+      bnd[c] = c > 0 ? std::max(b, bnd[c - 1]) : 0;
+    }
+    bnd[G] = N;
+  }
   int s = 0, maxrows = 0;
   long long base = 0;  // first global row of system s
   for (int c = 0; c < G; ++c) {
-    const long long lo = N * c / G, hi = N * (c + 1) / G;
+    const long long lo = bnd[c], hi = bnd[c + 1];
     ptr[c] = (int)seg.size();
     int off = 0;
     for (long long r = lo; r < hi;) {
@@ -915,10 +1082,22 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   persistent_grid(1);  // sets the kernel's shared-memory attribute once
   int G = B.mgs_g;
   BatchDev b = B;
-  void *args[] = {&b, &j};
+  int j1 = j + 1;
+  void *args[] = {&b, &j, &j1};
   // cooperative: every CTA resident at once (CTAs wait for each other's sums)
-  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid, dim3(G), dim3(IGM_MGS_BLOCK),
-                                          args, IGM_MGS_SMEM(B.mgs_wrows), st));
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid<false>, dim3(G),
+                                          dim3(IGM_MGS_BLOCK), args, IGM_MGS_SMEM(B.mgs_wrows),
+                                          st));
+}
+
+void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st) {
+  persistent_grid(1);
+  int G = B.mgs_g;
+  BatchDev b = B;
+  void *args[] = {&b, &j0, &j1};
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid<true>, dim3(G),
+                                          dim3(IGM_MGS_BLOCK), args, IGM_MGS_SMEM(B.mgs_wrows),
+                                          st));
 }
 
 }  // namespace igm

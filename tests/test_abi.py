@@ -54,12 +54,14 @@ def test_struct_layouts(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "igm.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(igm_params),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+        ' sizeof(igm_params),'
         ' sizeof(igm_report), offsetof(igm_params, tol), offsetof(igm_params, inner),'
         ' offsetof(igm_report, relres), offsetof(igm_report, relres_hist),'
         ' offsetof(igm_params, shift_tune), offsetof(igm_report, shift_retries),'
         ' offsetof(igm_report, beta_final), offsetof(igm_params, mgs_wmax),'
-        ' offsetof(igm_params, test_stall)); return 0;}\n')
+        ' offsetof(igm_params, test_stall), offsetof(igm_params, plan_snap),'
+        ' offsetof(igm_report, plan_snap)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
@@ -68,7 +70,8 @@ def test_struct_layouts(tmp_path):
                    L.Params.inner.offset, L.Report.relres.offset, L.Report.relres_hist.offset,
                    L.Params.shift_tune.offset, L.Report.shift_retries.offset,
                    L.Report.beta_final.offset, L.Params.mgs_wmax.offset,
-                   L.Params.test_stall.offset]
+                   L.Params.test_stall.offset, L.Params.plan_snap.offset,
+                   L.Report.plan_snap.offset]
 
 
 def test_no_oracle_in_product_path():

@@ -138,6 +138,82 @@ def test_wide_basis_bit_exact(L, orc, prec, df, dd, wmax, wide):
     _check_ir(L, orc, s, P)
 
 
+FUSED = [
+    ("banded_20000", lambda: W.banded_random(20000, np.random.default_rng(330)), 30),
+    ("cd2d_120", lambda: W.small_cd2d(120), 30),
+    ("banded_3001", lambda: W.banded_random(3001, np.random.default_rng(331)), 20),
+]
+
+
+@pytest.mark.parametrize("fuse,snap,wmax", [(0, 0, 0), (30, -1, 0), (7, 50, 0), (1, 25, 600),
+                                            (4, -1, -1), (-1, 0, 0)])
+@pytest.mark.parametrize("name,sf,m", FUSED, ids=[c[0] for c in FUSED])
+def test_fused_arnoldi_bit_exact(L, orc, name, sf, m, fuse, snap, wmax):
+    """Lines 5-19 of several steps in one persistent launch (systems without
+    preconditioner): one inner solve and the refinement loop equal the
+    oracle bit for bit for every number of steps per launch, every row
+    partition and every residency (automatic, none, a cap), and the report
+    names the launch configuration that ran (chosen by the autotuner when
+    left open)."""
+    s = sf()
+    P = L.params_default(0, m)
+    P.fuse_steps, P.plan_snap, P.mgs_wmax = fuse, snap, wmax
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    bk = d["b"] / np.abs(d["b"]).max()
+    x0 = np.random.default_rng(9).standard_normal(s.n) * 1e-3
+    o = orc.int_gmres(_oparams(orc, P), d, bk, x0)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    _compare_inner(solver.state(), o)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    solver.close()
+    xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    x, rep = solver.ir_solve(_dev(s.b))
+    assert rep["status"] == ro.status and rep["refinements"] == ro.refinements
+    np.testing.assert_array_equal(rep["ev"], ro.ev)
+    np.testing.assert_array_equal(x.cpu().numpy(), xo)
+    if fuse > 0:
+        assert rep["fuse_steps"] == min(fuse, m)
+    elif fuse < 0:
+        assert rep["fuse_steps"] == 0
+    else:
+        assert 0 <= rep["fuse_steps"] <= m
+    if snap > 0:
+        assert rep["plan_snap"] == snap
+    elif snap < 0:
+        assert rep["plan_snap"] == 0
+    else:
+        assert rep["plan_snap"] in (0, 25, 50)
+    solver.close()
+
+
+@pytest.mark.parametrize("fuse,snap", [(0, 0), (30, 50), (3, -1), (-1, 25)])
+def test_fused_batch_bit_exact(L, orc, fuse, snap):
+    """A batch of uneven systems without preconditioner (n log-uniform over
+    [1k, 20k], banded random) through the fused Arnoldi kernel, with whole
+    systems inside one CTA and systems split over several: every system's
+    result equals the oracle's bit for bit."""
+    import torch
+    rng = np.random.default_rng(340)
+    ns = [int(v) for v in np.exp(rng.uniform(np.log(1000), np.log(20000), 24))]
+    systems = [W.banded_random(n, rng) for n in ns]
+    P = L.params_default(0, 30)
+    P.fuse_steps, P.plan_snap = fuse, snap
+    svs = [L.Solver(_dev(sy.rowptr), _dev(sy.col), _dev(sy.val), P) for sy in systems]
+    out = [torch.empty(sy.n, dtype=torch.float64, device="cuda") for sy in systems]
+    reps = L.ir_solve_batched(svs, [_dev(sy.b) for sy in systems], out)
+    for k, sy in enumerate(systems):
+        xo, ro = orc.ir_solve(sy.rowptr, sy.col, sy.val, sy.b, _oparams(orc, P))
+        assert reps[k]["status"] == ro.status and reps[k]["refinements"] == ro.refinements
+        np.testing.assert_array_equal(reps[k]["ev"], ro.ev)
+        np.testing.assert_array_equal(out[k].cpu().numpy(), xo)
+    for sv in svs:
+        sv.close()
+
+
 def test_arnoldi_global_w_batched_equals_solo(L, orc):
     """A batch whose Arnoldi step keeps w in global memory: each system's
     result equals the oracle's (and so its solo solve)."""
