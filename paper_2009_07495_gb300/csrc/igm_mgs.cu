@@ -95,6 +95,10 @@ __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
 }
 
 #define IGM_RPT 4           // rows in flight per thread
+// threads of a grid-mode CTA (one CTA per SM)
+#ifndef IGM_MGS_GBS
+#define IGM_MGS_GBS 1024
+#endif
 #define IGM_MGS_GCACHE 32   // segment descriptors a CTA of the grid mode keeps in shared memory
 // CTA rows of the grid mode resident in shared memory: w (int64) and two
 // int32 basis vectors, 16 bytes a row (218 KB)
@@ -383,7 +387,7 @@ __device__ __forceinline__ void rows_pass(i64 (&wv)[R], const VT (&pv)[R], const
   for (int u = 0; u < R; ++u) part += (i128)pr[u];
 }
 
-// a segment's pass in the grid mode (see k_mgs_grid)
+// a segment's pass in the grid mode (k_mgs_step_grid, k_mgs_fused)
 struct MPass {
   i64 hs;
   int s8, sA;
@@ -395,16 +399,16 @@ struct MPass {
 
 // resident rows [0, qv): w, v_{i-1} and v_i in shared memory (at pass 0 w
 // from global memory unless line 5 left it in shared memory; stored into
-// shared memory); each thread the rows q = threadIdx.x (mod IGM_MGS_BLOCK)
+// shared memory); each thread the rows q = threadIdx.x (mod IGM_MGS_GBS)
 template <int MODE, bool HS32>
 __device__ __forceinline__ void pass_res(const MPass &P, i128 &part, unsigned &evA,
                                          unsigned &evB) {
-  for (int q0 = threadIdx.x; q0 < P.qv; q0 += IGM_RPT * IGM_MGS_BLOCK) {
+  for (int q0 = threadIdx.x; q0 < P.qv; q0 += IGM_RPT * IGM_MGS_GBS) {
     i64 wv[IGM_RPT];
     int pv[IGM_RPT], qq[IGM_RPT];
 #pragma unroll
     for (int u = 0; u < IGM_RPT; ++u) {
-      const int q = q0 + u * IGM_MGS_BLOCK;
+      const int q = q0 + u * IGM_MGS_GBS;
       const bool ok = q < P.qv;
       wv[u] = !ok ? 0 : (MODE == 0 && !P.w0s) ? P.wg[q] : P.ws[q];
       pv[u] = (MODE > 0 && ok) ? P.vps[q] : 0;
@@ -413,7 +417,7 @@ __device__ __forceinline__ void pass_res(const MPass &P, i128 &part, unsigned &e
     rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
 #pragma unroll
     for (int u = 0; u < IGM_RPT; ++u) {
-      const int q = q0 + u * IGM_MGS_BLOCK;
+      const int q = q0 + u * IGM_MGS_GBS;
       if (q < P.qv) P.ws[q] = wv[u];
     }
   }
@@ -426,12 +430,12 @@ template <int MODE, bool HS32, typename VT>
 __device__ __forceinline__ void pass_glob(const MPass &P, const VT *vp, const VT *vi, i128 &part,
                                           unsigned &evA, unsigned &evB) {
   constexpr int R = sizeof(VT) == 4 ? IGM_RPT : IGM_RPT / 2;
-  for (int q0 = P.qv + threadIdx.x; q0 < P.nr; q0 += R * IGM_MGS_BLOCK) {
+  for (int q0 = P.qv + threadIdx.x; q0 < P.nr; q0 += R * IGM_MGS_GBS) {
     i64 wv[R];
     VT pv[R], qq[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const int q = q0 + u * IGM_MGS_BLOCK;
+      const int q = q0 + u * IGM_MGS_GBS;
       const bool ok = q < P.nr;
       wv[u] = !ok ? 0 : ((MODE > 0 || P.w0s) && q < P.qw) ? P.ws[q] : P.wg[q];
       pv[u] = (MODE > 0 && ok) ? vp[q] : 0;
@@ -440,7 +444,7 @@ __device__ __forceinline__ void pass_glob(const MPass &P, const VT *vp, const VT
     rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const int q = q0 + u * IGM_MGS_BLOCK;
+      const int q = q0 + u * IGM_MGS_GBS;
       if (q >= P.nr) continue;
       if (q < P.qw) P.ws[q] = wv[u];
       else if (MODE > 0) P.wg[q] = wv[u];
@@ -474,7 +478,7 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
 // int128 row sums over the SELL-32 copy of Abar_0 (one term, s = 0), the
 // basis vector read from L2 (other CTAs wrote it during this launch), w into
 // shared memory for the resident rows and global memory for the others;
-// each thread the rows q = threadIdx.x (mod IGM_MGS_BLOCK), the rows it owns
+// each thread the rows q = threadIdx.x (mod IGM_MGS_GBS), the rows it owns
 // in the passes
 template <bool NAR>
 __device__ __forceinline__ void seg_spmv(const SysDev *s, const MSegC &c, int j, int qw, i64 *ws,
@@ -484,7 +488,7 @@ __device__ __forceinline__ void seg_spmv(const SysDev *s, const MSegC &c, int j,
   const long long *sptr = s->sptr;
   const i64 *sval = s->sval;
   const int *scol = s->scol;
-  for (int q = threadIdx.x; q < c.nrows; q += IGM_MGS_BLOCK) {
+  for (int q = threadIdx.x; q < c.nrows; q += IGM_MGS_GBS) {
     const int i = c.row0 + q;
     const int sl = i >> 5;
     const long long base = sptr[sl] + (i & 31);
@@ -529,28 +533,258 @@ __device__ bool mvtag_wait(const BatchDev &B, int sys, unsigned tag, const unsig
   return __syncthreads_and(ok) != 0;
 }
 
-// Grid mode: every CTA owns the same rows in every pass (a partition of all
-// systems' rows planned on the host).  The first B.mgs_wrows of them (in
-// segments among the first IGM_MGS_GCACHE) are resident in shared memory: w
-// from line 5 (FUSED) or pass 0 to line 11, and (while every basis entry of
-// the inner solve fits int32) the int32 words of v_{i-1} and v_i in two
+// Grid mode: every CTA owns the same rows in every pass (a balanced partition
+// of all systems' rows, planned on the host).  The first B.mgs_wrows of them
+// (in segments among the first IGM_MGS_GCACHE) are resident in shared
+// memory: w from pass 0 to line 11, and (while every basis entry of the
+// inner solve fits int32) the int32 words of v_{i-1} and v_i in two
 // buffers; v_{i+1} is bulk-copied into the buffer of v_{i-1} while the
 // pass's sums travel, so a pass over resident rows reads nothing from global
 // memory.  Further rows keep w in global memory and read the basis from
 // global memory (the next vector prefetched into L2 during the pass).
 // There is no grid barrier: each CTA publishes its tagged sum of the pass
 // per segment and reads those of its systems' segments, so a CTA waits only
-// for the CTAs that share a system with it; a system held by one CTA alone
-// uses the CTA's sum directly.
-//
-// Not FUSED: lines 6-19 of step j0 (line 5 ran before).  FUSED: steps j0 ..
-// j1-1 each with line 5 first (systems without preconditioner and without
-// correction terms); after line 11 and lines 12-19 of step j the CTA
-// publishes (j, its segments) in mvtag, and before line 5 of step j + 1 a
-// CTA waits for every segment of its systems, so v_{j+1} is complete.
-template <bool FUSED>
-__global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j0, int j1) {
-  constexpr int BS = IGM_MGS_BLOCK;
+// for the CTAs that share a system with it.  Lines 6-19 of step j (line 5
+// ran before).
+__global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, int j) {
+  constexpr int BS = IGM_MGS_GBS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int S = B.mgs_wrows;  // resident rows of this CTA
+  i64 *sw = reinterpret_cast<i64 *>(smem);                    // w of the resident rows
+  int *sv = reinterpret_cast<int *>(smem + IGM_MGS_VOFF(S));  // 2 basis buffers
+  const int vb = IGM_MGS_VB(S);                               // words of one
+  __shared__ MSegC s_seg[IGM_MGS_GCACHE + 1];  // + one slot for the others in turn
+  __shared__ i64 s_h[IGM_MGS_GCACHE];
+  __shared__ __align__(8) u64 s_vbar[2];  // bulk copies into basis buffer 0 / 1
+  __shared__ unsigned s_epoch, s_vbytes;
+  __shared__ int s_fail;
+  unsigned *err0 = &B.sys[0]->sc->err;
+  const int g0 = B.mseg_ptr[blockIdx.x], ns = B.mseg_ptr[blockIdx.x + 1] - g0;
+  // descriptors; segments beyond the cache keep their step flags (taken
+  // now, before this CTA publishes anything) in mseg_act
+  for (int k = threadIdx.x; k < ns; k += BS) {
+    if (k < IGM_MGS_GCACHE) {
+      mseg_make(B, g0 + k, j, s_seg[k]);
+    } else {
+      MSegC c;
+      mseg_make(B, g0 + k, j, c);
+      B.mseg_act[g0 + k] = c.active | (c.narrow << 1);
+    }
+  }
+  if (threadIdx.x == 0) {
+    s_epoch = ld_relaxed_u32(B.bar + 2);
+    s_fail = 0;
+    mbar_init(&s_vbar[0], 1);
+    mbar_init(&s_vbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch, e16 = (epoch & 0xffffu) << 16;
+  // a segment's descriptor with the flags taken at the start (into c)
+  auto seg_make = [&](int k, MSegC &c) {
+    mseg_make(B, g0 + k, j, c);
+    const int f = B.mseg_act[g0 + k];
+    c.active = f & 1;
+    c.narrow = f >> 1;
+  };
+  // the descriptor of segment k in shared memory (all threads call it in
+  // step): beyond the cache, thread 0 builds it in the spare slot
+  auto seg = [&](int k) -> const MSegC & {
+    if (k < IGM_MGS_GCACHE) return s_seg[k];
+    __syncthreads();
+    if (threadIdx.x == 0) seg_make(k, s_seg[IGM_MGS_GCACHE]);
+    __syncthreads();
+    return s_seg[IGM_MGS_GCACHE];
+  };
+  // resident rows of segment k: w (res_w) and the basis (res_v: cached
+  // segments while narrow)
+  auto res_w = [&](const MSegC &c) { return min(max(S - c.off, 0), c.nrows); };
+  auto res_v = [&](const MSegC &c, int k) {
+    return (k < IGM_MGS_GCACHE && c.narrow) ? res_w(c) : 0;
+  };
+  // where vector i of cached segment k starts in its basis buffer: at a
+  // 16-byte aligned offset, plus the vector's misalignment
+  auto vbase = [&](const MSegC &c, int k, int i) -> int * {
+    return sv + (size_t)(i & 1) * vb + ((c.off + 3) & ~3) + 12 * k +
+           (int)(((size_t)i * c.n + c.row0) & 3);
+  };
+  // bulk-copy v_i of every resident segment into buffer i & 1 (thread 0,
+  // after a block barrier behind the last reads of that buffer)
+  auto stage = [&](int i) {
+    unsigned bytes = 0;
+    for (int k = 0; k < ns && k < IGM_MGS_GCACHE; ++k) {
+      const MSegC &c = s_seg[k];
+      const int qv = c.active ? res_v(c, k) : 0;
+      if (qv == 0) continue;
+      const size_t e0 = (size_t)i * c.n + c.row0;
+      const int pad = (int)(e0 & 3);
+      bytes += 4u * (unsigned)((pad + qv + 3) & ~3);
+    }
+    s_vbytes = bytes;
+    if (bytes == 0) return;
+    fence_proxy_async();
+    mbar_expect_tx(&s_vbar[i & 1], bytes);
+    for (int k = 0; k < ns && k < IGM_MGS_GCACHE; ++k) {
+      const MSegC &c = s_seg[k];
+      const int qv = c.active ? res_v(c, k) : 0;
+      if (qv == 0) continue;
+      const size_t e0 = (size_t)i * c.n + c.row0;
+      const int pad = (int)(e0 & 3);
+      bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)((pad + qv + 3) & ~3),
+               &s_vbar[i & 1]);
+    }
+  };
+  if (threadIdx.x == 0) stage(0);
+  __syncthreads();
+  const bool vst = s_vbytes != 0;  // the same for every vector
+  int staged = 0;                  // the last vector copied
+  for (int i = 0; i <= j + 1; ++i) {
+    const unsigned tag = e16 | ((unsigned)j << 8) | (unsigned)(i + 1);
+    // v_i of the resident rows is in place (v_{i-1} already was)
+    if (vst && i <= j && !mbar_wait(&s_vbar[i & 1], (unsigned)(i >> 1) & 1u, err0, 1000000000ull))
+      s_fail = 1;
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      MPass P;
+      P.nr = c.nrows;
+      P.qw = res_w(c);
+      P.qv = res_v(c, k);
+      P.w0s = false;
+      // pull the global rows of v_{i+1} into L2 while this pass runs
+      if (i + 1 <= j && P.qv < P.nr) {
+        const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
+        const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
+        const size_t bytes = (size_t)(P.nr - P.qv) * (c.narrow ? sizeof(int) : sizeof(i64));
+        for (size_t a = (size_t)threadIdx.x * 128; a < bytes; a += (size_t)BS * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(base + a));
+      }
+      P.hs = i == 0 ? 0 : (k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k]);
+      P.wg = c.w;
+      P.ws = sw + c.off;
+      P.s8 = shc(c.df - c.b8);
+      P.sA = i <= j ? shc(c.b7) : shc(c.b10);
+      if (P.qv > 0) {
+        P.vps = vbase(c, k, i > 0 ? i - 1 : 0);
+        P.vis = vbase(c, k, i <= j ? i : 0);
+      }
+      const bool hs32 = P.hs == (i64)(int)P.hs;
+      i128 part = 0;
+      unsigned evA = 0, evB = 0;
+      if (i == 0) pass_seg<0, true>(P, c, i, j, part, evA, evB);
+      else if (i <= j) {
+        if (hs32) pass_seg<1, true>(P, c, i, j, part, evA, evB);
+        else pass_seg<1, false>(P, c, i, j, part, evA, evB);
+      } else {
+        if (hs32) pass_seg<2, true>(P, c, i, j, part, evA, evB);
+        else pass_seg<2, false>(P, c, i, j, part, evA, evB);
+      }
+      flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
+      flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
+      part = block_sum_i128(part);
+      if (threadIdx.x == 0) mslot_put(mslot(B, i & 1, g0 + k), part, tag);
+    }
+    // every read of pass i is behind the block barriers of the sums: v_{i+1}
+    // may overwrite the buffer of v_{i-1}
+    __syncthreads();
+    if (vst && i + 1 <= j && !s_fail) {
+      if (threadIdx.x == 0) stage(i + 1);
+      staged = i + 1;
+    }
+    // each segment's coefficient from its system's total (tagged slots)
+    for (int k = 0; k < ns && !s_fail; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      i128 tot;
+      if (!mseg_total(B, c.sys, i & 1, tag, err0, tot)) {
+        if (threadIdx.x == 0) s_fail = 1;
+        __syncthreads();
+        break;
+      }
+      if (threadIdx.x == 0) {
+        const i64 h = mseg_coef(c, tot, i, j);
+        if (k < IGM_MGS_GCACHE) s_h[k] = h;
+        else B.mseg_h[g0 + k] = h;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+  }
+  if (s_fail) {
+    // the copy in flight lands before the CTA leaves (bounded again)
+    if (vst) mbar_wait(&s_vbar[staged & 1], (unsigned)(staged >> 1) & 1u, err0, 1000000000ull);
+    if (threadIdx.x == 0) atomicOr(err0, ERR_TIMEOUT);
+  } else {
+    // line 11 for every system whose divisor is non-zero
+    for (int k = 0; k < ns; ++k) {
+      const MSegC &c = seg(k);
+      if (!c.active) continue;
+      const i64 hn = k < IGM_MGS_GCACHE ? s_h[k] : B.mseg_h[g0 + k];
+      if (shr(hn, c.b11b) == 0) continue;
+      const int qw = res_w(c);
+      i64 *vn = c.V + (size_t)(j + 1) * c.n + c.row0;
+      int *vn32 = c.V32 + (size_t)(j + 1) * c.n + c.row0;
+      const i64 *wg = c.w, *ws = sw + c.off;
+      unsigned ev = 0, evr = 0;
+      for (int q0 = threadIdx.x; q0 < c.nrows; q0 += IGM_RPT * BS) {
+        i64 wv[IGM_RPT];
+#pragma unroll
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * BS;
+          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : wg[q];
+        }
+#pragma unroll
+        for (int u = 0; u < IGM_RPT; ++u) {
+          const int q = q0 + u * BS;
+          if (q >= c.nrows) continue;
+          const i64 v = fx_div(wv[u], hn, c.b11a, c.b11b, c.df, ev);
+          evr += (v < INT32_MIN || v > INT32_MAX);
+          vn[q] = v;
+          vn32[q] = (int)v;
+        }
+      }
+      flush_ev(ev, &c.sc->ev[IGM_EV_L11]);
+      // an entry outside int32: the readers of the next steps (SpMV, these
+      // passes, the update) switch to the int64 copy for this inner solve
+      if (__syncthreads_or(evr != 0) && threadIdx.x == 0) atomicOr(&c.sc->vwide, 1);
+      flush_ev(evr, &c.sc->ev[IGM_EV_VRANGE]);
+    }
+    // lines 10 (store) and 12-19, one thread per system, after line 11: the
+    // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += BS) {
+      if (k < IGM_MGS_GCACHE) {
+        if (s_seg[k].active && s_seg[k].first) givens_tail(B, s_seg[k], j, s_h[k]);
+      } else {
+        MSegC c;
+        seg_make(k, c);
+        if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
+      }
+    }
+  }
+  // the last CTA to finish moves the launch epoch on (every CTA of this
+  // launch read it before publishing anything)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned done = atom_add_acq_rel_u32(B.bar + 3, 1u);
+    if (done == gridDim.x - 1) {
+      st_relaxed_u32(B.bar + 3, 0u);
+      st_relaxed_u32(B.bar + 2, epoch + 1u);
+    }
+  }
+}
+
+
+// The fused grid-mode kernel: steps j0 .. j1-1 of the Arnoldi process, each
+// with line 5 first, for systems without preconditioner and without
+// correction terms; the same partition, residency and tagged pass sums as
+// k_mgs_step_grid, and w of the resident rows stays in shared memory from
+// line 5 to line 11.  After line 11 and lines 12-19 of step j a CTA
+// publishes (j, its segments) in mvtag; before line 5 of step j + 1 it waits
+// for every segment of its systems, so v_{j+1} is complete.  A system held
+// by one CTA alone uses the CTA's pass sums directly.
+__global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_fused(BatchDev B, int j0, int j1) {
+  constexpr int BS = IGM_MGS_GBS;
   extern __shared__ __align__(16) unsigned char smem[];
   const int S = B.mgs_wrows;  // resident rows of this CTA
   i64 *sw = reinterpret_cast<i64 *>(smem);                    // w of the resident rows
@@ -649,12 +883,8 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     const unsigned nb = s_vn[b];
     if (nb > 0 && !mbar_wait(&s_vbar[b], (nb - 1) & 1u, err0, 1000000000ull)) s_fail = 1;
   };
-  if (!FUSED) {
-    if (threadIdx.x == 0) stage(0);
-    __syncthreads();
-  }
   for (; j < j1 && !s_fail; ++j) {
-    if (FUSED) {
+    {
       if (j > j0) {
         // v_j of every active system: each of its segments published step j - 1
         for (int k = 0; k < ns && !s_fail; ++k) {
@@ -711,7 +941,7 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
         P.nr = c.nrows;
         P.qw = res_w(c);
         P.qv = res_v(c, k);
-        P.w0s = FUSED;
+        P.w0s = true;
         // pull the global rows of v_{i+1} into L2 while this pass runs
         if (i + 1 <= j && P.qv < P.nr) {
           const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
@@ -810,7 +1040,7 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
     }
     // this CTA's basis rows, written through the generic proxy, are read by
     // its later bulk copies
-    if (FUSED) fence_proxy_async_global();
+    fence_proxy_async_global();
     // lines 10 (store) and 12-19, one thread per system, after line 11: the
     // CTA holding the system's row 0 recorded h_{0..j,j} and has h_{j+1,j}
     __syncthreads();
@@ -823,7 +1053,7 @@ __global__ void __launch_bounds__(IGM_MGS_BLOCK, 1) k_mgs_grid(BatchDev B, int j
         if (c.active && c.first) givens_tail(B, c, j, B.mseg_h[g0 + k]);
       }
     }
-    if (FUSED) {
+    {
       // publish step j: the CTA's basis rows, flags and (first CTA) lines
       // 12-19 before the tags
       __syncthreads();
@@ -981,15 +1211,15 @@ int persistent_grid(int ntiles) {
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     // co-resident CTAs with the most dynamic shared memory a plan may give
     // the integer step (IGM_MGS_WMAX resident rows)
-    cudaFuncSetAttribute(k_mgs_grid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mgs_step_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
-    cudaFuncSetAttribute(k_mgs_grid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
     int a = 0, a2 = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_grid<false>, IGM_MGS_BLOCK,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step_grid, IGM_MGS_GBS,
                                                       IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_mgs_grid<true>, IGM_MGS_BLOCK,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_mgs_fused, IGM_MGS_GBS,
                                                       IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a2 = 1;
     a = a < a2 ? a : a2;
@@ -1082,11 +1312,10 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   persistent_grid(1);  // sets the kernel's shared-memory attribute once
   int G = B.mgs_g;
   BatchDev b = B;
-  int j1 = j + 1;
-  void *args[] = {&b, &j, &j1};
+  void *args[] = {&b, &j};
   // cooperative: every CTA resident at once (CTAs wait for each other's sums)
-  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid<false>, dim3(G),
-                                          dim3(IGM_MGS_BLOCK), args, IGM_MGS_SMEM(B.mgs_wrows),
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_step_grid, dim3(G),
+                                          dim3(IGM_MGS_GBS), args, IGM_MGS_SMEM(B.mgs_wrows),
                                           st));
 }
 
@@ -1095,8 +1324,8 @@ void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st) {
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j0, &j1};
-  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_grid<true>, dim3(G),
-                                          dim3(IGM_MGS_BLOCK), args, IGM_MGS_SMEM(B.mgs_wrows),
+  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_fused, dim3(G),
+                                          dim3(IGM_MGS_GBS), args, IGM_MGS_SMEM(B.mgs_wrows),
                                           st));
 }
 
