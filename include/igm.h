@@ -86,9 +86,10 @@ typedef struct {
   int max_refine;/* maximum inner solves in Fig. 1                           */
   int inner;     /* 0: int-GMRES (Fig. 2); 1: FP64 GMRES(m) ("Double")       */
   int trsv_chunk;/* rows per chunk of the line-5' substitutions (0: automatic)*/
-  int trsv_cluster;/* chunks per thread-block cluster of the substitutions:
-                    0 automatic, 1 none, 2, 4 or 8 (results do not depend
-                    on it)                                               */
+  int trsv_cluster;/* kept for layout compatibility: 0, 1, 2, 4 or 8 are
+                    accepted and ignored (the substitutions hand values
+                    between chunks through global memory, with no
+                    thread-block clusters)                                 */
   int s;         /* correction terms of Sec. IV-C, eq. (AA), used in every
                     refinement (s(k) = s, 0 ... IGM_MAX_S): the matrix is
                     Abar_0 + sum_l Abar_l / 2^alpha_l and line 5 adds each
@@ -171,9 +172,14 @@ igm_status igm_params_default(igm_params *p, int precond, int m);
  * (Abar_0 = trunc(A), s = 0), and with precond = 1 the FP64 ILU(0) of
  * eq. (ilu) and its integer factors Lbar, Ubar of eq. (dldr)-(ilu2).
  * n >= 1 rows, nnz entries; rowptr/col/val as in the conventions above.
- * On success *out owns all device state of the system (about
- * nnz*(12 + 8*precond... ) + (m+8)*8*n bytes).  Errors: IGM_EINVAL,
- * IGM_EZERO_ROW, IGM_EZERO_PIVOT, IGM_EOOM, IGM_ECUDA. */
+ * On success *out owns all device state of the system: about 40 bytes per
+ * stored entry (the scaled, cast and SELL-32 copies of A) plus
+ * 12 (m + 1) + 92 bytes per row (the basis as int64 and int32 words, work
+ * vectors); precond = 1 adds about 16 bytes per entry and 24 K + 120 bytes
+ * per row (factors, schedules and packed substitution blocks; K the
+ * longest strict row of a factor).  int_gmres_device_bytes gives the exact
+ * figure.  Errors: IGM_EINVAL, IGM_EZERO_ROW, IGM_EZERO_PIVOT, IGM_EOOM,
+ * IGM_ECUDA. */
 igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
                            const double *val, const igm_params *params,
                            void *stream, igm_handle *out);
@@ -266,12 +272,14 @@ igm_status igm_time_kernels(igm_handle h, int reps, double *ms, void *stream);
 long long igm_kernel_launches(void);
 
 /* ---- Serving: continuous batching of independent solves ---------------
- * A server owns a worker thread and a CUDA stream.  Submitted requests
- * (host arrays, copied at submission) wait in a FIFO queue; the worker
- * admits them while the device memory of admitted systems stays within
- * budget_bytes (and at most max_active are active), sets each one up on the
- * device (int_gmres_setup) and keeps its matrix, factors, basis and
- * refinement state resident until it finishes.  Work proceeds in rounds:
+ * A server owns two threads, each with its CUDA stream.  Submitted requests
+ * (host arrays, copied at submission) wait in a FIFO queue; the admission
+ * thread admits them in order while the device memory of admitted systems
+ * stays within budget_bytes (and at most max_active are admitted; the
+ * footprint is estimated before set-up and corrected after it), sets each
+ * one up on the device (int_gmres_setup) while rounds run, and keeps its
+ * matrix, factors, basis and refinement state resident until it finishes.
+ * The round thread's work proceeds in rounds:
  * one convergence test (Fig. 1) and one inner solve (Fig. 2) for every
  * active system in the same kernels; requests that arrive meanwhile join
  * at the next round, finished ones leave.  Each result is bit-identical to

@@ -191,6 +191,7 @@ igm_status build_batch(const std::vector<igm_handle> &hs, Batch **out) {
   B.bar = d_bar;
   B.cpart = d_cpart;
   B.maxg = maxg;
+  B.max_m = b->m;
   B.trsv_maxk = maxk;
   B.max_colors = max_colors;
   B.max_ns = 0;

@@ -246,6 +246,7 @@ struct BatchDev {
   unsigned *mvtag;         // per segment: the last step whose basis rows
                            // the fused Arnoldi kernel published (tagged)
   int fuse;                // steps per fused Arnoldi launch (0: not fused)
+  int max_m;               // Arnoldi steps of the batch's systems (all equal)
   const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
   int mgs_wrows;           // rows each CTA keeps resident in shared memory
   int mgs_rows;            // most rows of a CTA

@@ -7,6 +7,8 @@
 // exact (int128 partials, or the reproducible FP64 norm) and finished by
 // the last CTA of the system, so every result is independent of the tile
 // schedule and of the other systems in the batch.
+#include <mutex>
+
 #include "igm_dev.cuh"
 #include "igm_launch.h"
 
@@ -368,25 +370,40 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// lines 21-22: y = ||r0|| H^-1 g in FP64 (one thread per system)
+// lines 21-22: y = ||r0|| H^-1 g in FP64, one CTA per system.  The CTA
+// stages the upper triangle of H (as the doubles h 2^-df) in shared memory
+// with coalesced loads; then, row by row from the last, its threads form
+// the products h_ab z_b (b > a) at once and thread 0 subtracts them from
+// g_a 2^-df in ascending b, each operation rounded as written, so z is the
+// same as with one thread doing the whole sum.
 // ---------------------------------------------------------------------------
-__global__ void k_backsub(BatchDev B) {
-  int si = blockIdx.x * blockDim.x + threadIdx.x;
-  if (si >= B.nsys) return;
-  SysDev *s = B.sys[si];
+#define IGM_BACKSUB_BLOCK 64
+
+__global__ void __launch_bounds__(IGM_BACKSUB_BLOCK) k_backsub(BatchDev B) {
+  extern __shared__ double sH[];  // jeff x jeff, row-major: sH[a jeff + b] (b >= a)
+  __shared__ double z[IGM_MAX_M], p[IGM_MAX_M];
+  SysDev *s = B.sys[blockIdx.x];
   SysScal *sc = s->sc;
   if (!g_cyc(sc)) return;
   const int jeff = sc->jeff, ld = s->ld, df = s->p.df;
-  // y in thread-local memory while it is formed: the loads of H do not
-  // wait for the stores of y
-  double z[IGM_MAX_M];
-  for (int a = jeff - 1; a >= 0; --a) {
-    double acc = scalbn((double)s->g[a], -df);
-    for (int b = a + 1; b < jeff; ++b)
-      acc = __dsub_rn(acc, __dmul_rn(scalbn((double)s->H[a + b * ld], -df), z[b]));
-    z[a] = __ddiv_rn(acc, scalbn((double)s->H[a + a * ld], -df));
+  for (int idx = threadIdx.x; idx < jeff * jeff; idx += blockDim.x) {
+    const int a = idx % jeff, b = idx / jeff;  // consecutive threads: consecutive rows of H
+    if (a <= b) sH[a * jeff + b] = scalbn((double)s->H[a + b * ld], -df);
   }
-  for (int a = 0; a < jeff; ++a) s->yfp[a] = __dmul_rn(sc->nu, z[a]);
+  __syncthreads();
+  for (int a = jeff - 1; a >= 0; --a) {
+    for (int b = a + 1 + threadIdx.x; b < jeff; b += blockDim.x)
+      p[b] = __dmul_rn(sH[a * jeff + b], z[b]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = scalbn((double)s->g[a], -df);
+      for (int b = a + 1; b < jeff; ++b) acc = __dsub_rn(acc, p[b]);
+      z[a] = __ddiv_rn(acc, sH[a * jeff + a]);
+    }
+    __syncthreads();
+  }
+  for (int a = threadIdx.x; a < jeff; a += blockDim.x) s->yfp[a] = __dmul_rn(sc->nu, z[a]);
+  if (threadIdx.x != 0) return;
   // shift auto-tuning (refinement loop only): an inner solve that raised
   // events at a shifted line raises those lines' shifts by one (up to d_f)
   // and is discarded; the next test of Fig. 1 sees the same x and repeats
@@ -558,7 +575,13 @@ void launch_spmv(const BatchDev &B, int j, cudaStream_t st) {
   else k_spmv<false><<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
 }
 void launch_backsub(const BatchDev &B, cudaStream_t st) {
-  k_backsub<<<nb_sys(B), 128, 0, st>>>(B);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * IGM_MAX_M * IGM_MAX_M));
+  });
+  const size_t sm = sizeof(double) * (size_t)B.max_m * B.max_m;
+  k_backsub<<<B.nsys, IGM_BACKSUB_BLOCK, sm, st>>>(B);
 }
 void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st) {
   k_gather_state<<<nb_sys(B), 128, 0, st>>>(B, out);

@@ -610,9 +610,9 @@ def test_chunk_schedule_does_not_change_results(L, orc, chunk):
 
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8])
 def test_substitution_clusters_do_not_change_results(L, orc, cluster):
-    """Chunks of the substitutions may run as thread-block clusters (the next
-    chunk reads the previous one's shared memory); with 16 chunks, clusters of
-    1, 2, 4 or 8 CTAs all give the oracle's result bit for bit."""
+    """The cluster knob is accepted and ignored: with 16 chunks of the
+    substitutions every accepted value (1, 2, 4, 8) gives the oracle's
+    result bit for bit."""
     s = W.small_cd3d(16, seed=45)
     P = L.params_default(1, 30)
     P.trsv_chunk = 256
