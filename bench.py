@@ -93,6 +93,9 @@ def parse():
                     help="shift auto-tuning budget (Sec. VII-D): inner solves that may "
                          "be discarded and rerun with raised shifts")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--side", type=int, default=0,
+                    help="cfg4 only: grid side of the 27-point workload (0: 200; smaller "
+                         "sides are for profiling captures, not bench lines)")
     ap.add_argument("--trsv-chunk", type=int, default=0,
                     help="rows per chunk of the substitutions (0: automatic)")
     ap.add_argument("--shifts", type=int, default=None,
@@ -705,6 +708,11 @@ def run_serve(args, wl):
 
 def main():
     args = parse()
+    if args.side and args.workload == "cfg4":
+        side = args.side
+        WORKLOADS["cfg4"] = dict(WORKLOADS["cfg4"], gen=lambda: W.config4(N=side),
+                                 desc=WORKLOADS["cfg4"]["desc"].replace(
+                                     "200^3 (n=8,000,000, nnz~216M)", f"{side}^3 (n={side ** 3:,})"))
     if args.oracle_sample:  # one worker of the all-core CPU baseline
         dt, refs, n, nnz = _oracle_sample_solve(args.oracle_sample)
         print(json.dumps({"dt": dt, "refinements": refs}), flush=True)
