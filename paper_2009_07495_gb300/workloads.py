@@ -64,37 +64,25 @@ def _assemble(shape, offsets, coef, diag):
         coords.append(rem % shape[d])
         rem //= shape[d]
     strides = [int(np.prod(shape[:d])) for d in range(dims)]
-    entries = [(0, None, diag)]
+    entries = [(0, (0,) * dims, diag)]
     for off, c in zip(offsets, coef):
         lin = sum(o * s for o, s in zip(off, strides))
-        entries.append((lin, off, c))
+        entries.append((lin, tuple(off), c))
     entries.sort(key=lambda e: e[0])
-    masks = []
-    for lin, off, c in entries:
-        if off is None:
-            masks.append(np.ones(n, dtype=bool))
-        else:
-            m = np.ones(n, dtype=bool)
-            for d in range(dims):
-                if off[d]:
-                    q = coords[d] + off[d]
-                    m &= (q >= 0) & (q < shape[d])
-            masks.append(m)
-    counts = np.zeros(n, dtype=np.int64)
-    for m in masks:
-        counts += m
+    # one (row, entry) table in entry order (= column order), compacted row
+    # by row
+    lins = np.array([e[0] for e in entries], dtype=np.int64)
+    offs = np.array([e[1] for e in entries], dtype=np.int64)  # (E, dims)
+    m2 = np.ones((n, len(entries)), dtype=bool)
+    for d in range(dims):
+        q = coords[d][:, None] + offs[None, :, d]
+        m2 &= (q >= 0) & (q < shape[d])
+    counts = m2.sum(axis=1)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
-    nnz = int(rowptr[-1])
-    col = np.empty(nnz, dtype=np.int32)
-    val = np.empty(nnz, dtype=np.float64)
-    fill = rowptr[:-1].copy()
-    for (lin, off, c), m in zip(entries, masks):
-        pos = fill[m]
-        col[pos] = (idx[m] + lin).astype(np.int32)
-        val[pos] = c[m]
-        fill[m] += 1
-    return rowptr.astype(np.int32), col, val
+    c2 = (idx[:, None] + lins[None, :]).astype(np.int32)
+    v2 = np.stack([e[2] for e in entries], axis=1)
+    return rowptr.astype(np.int32), c2[m2], v2[m2]
 
 
 def _harmonic(k1, k2):
