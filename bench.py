@@ -662,7 +662,10 @@ def run_batched(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl["desc"], "systems": nsys, "rows": int(sum(x.n for x in systems)),
                        "nnz": int(sum(x.nnz for x in systems)),
-                       "refinements_max": max(r["refinements"] for r in reps)},
+                       "refinements_max": max(r["refinements"] for r in reps),
+                       "arnoldi_launch": {"fuse_steps": reps[0]["fuse_steps"],
+                                          "plan_snap": reps[0]["plan_snap"],
+                                          "chosen_by": "autotuner"}},
             "one_solve_per_launch": {"value": nsys / dt_one, "unit": "solves/s",
                                      "p50_ms": 1000 * float(np.percentile(lat, 50)),
                                      "p99_ms": 1000 * float(np.percentile(lat, 99))},
