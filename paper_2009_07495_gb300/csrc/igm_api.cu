@@ -59,11 +59,13 @@ igm_status set_plan(Batch *b, int snap) {
   const int ns = (int)b->hs.size();
   std::vector<int> sysn(ns);
   for (int s = 0; s < ns; ++s) sysn[s] = b->hs[s]->n;
-  int G = 1, wrows = 0, rows = 0;
+  int G = 1, wrows = 0, rows = 0, ring = 0;
   std::vector<int> mptr, sys_seg;
   std::vector<Tile> mseg;
-  mgs_plan(sysn, persistent_grid(1 << 30), b->hs[0]->prm.mgs_wmax, snap, G, mptr, mseg, wrows,
-           rows, sys_seg);
+  // ring mode only where the fused kernel never runs (it keeps every
+  // resident row it can)
+  mgs_plan(sysn, persistent_grid(1 << 30), b->hs[0]->prm.mgs_wmax, snap, !b->fuse_ok, G, mptr,
+           mseg, wrows, rows, ring, sys_seg);
   const int MS = (int)mseg.size();
   Arena a;
   int *d_mptr, *d_sysseg, *d_mact;
@@ -102,6 +104,7 @@ igm_status set_plan(Batch *b, int snap) {
   B.sys_seg = d_sysseg;
   B.mgs_wrows = wrows;
   B.mgs_rows = rows;
+  B.mgs_ring = ring;
   return IGM_OK;
 }
 

@@ -250,6 +250,7 @@ struct BatchDev {
   const int *sys_seg;      // system s owns segments [sys_seg[s], sys_seg[s+1])
   int mgs_wrows;           // rows each CTA keeps resident in shared memory
   int mgs_rows;            // most rows of a CTA
+  int mgs_ring;            // single-step kernel streams further rows (ring mode)
   int trsv_maxk;           // most strict entries of one factor row
   int max_ns;              // most correction terms of eq. (AA) of a system
   int max_colors;          // most colours of a multicolour-ordered system

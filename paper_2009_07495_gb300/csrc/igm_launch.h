@@ -88,8 +88,8 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st);
 int persistent_grid(int ntiles);  // CTAs of the persistent kernels
 // the row partition of the integer Arnoldi step over systems of sizes n
-void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, int &G,
-              std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows,
+void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, bool ring_ok, int &G,
+              std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows, int &ring,
               std::vector<int> &sys_seg);
 void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st);
 void launch_backsub(const BatchDev &B, cudaStream_t st);

@@ -464,6 +464,105 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
   }
 }
 
+// Ring mode of the single-step grid kernel (rows beyond a CTA's resident
+// ones, basis as int32 words): the copy engine streams tiles of
+// IGM_MGS_T rows through IGM_MGS_NST stages in shared memory, w and the
+// basis words in with one mbarrier per stage, w back out with bulk stores,
+// so that memory traffic and row arithmetic overlap.  A stage holds w (8T
+// bytes), v_{i-1} and v_i (4T + 16 bytes each: a copy starts at the 16-byte
+// boundary below the tile, the misalignment kept as an offset).
+#define IGM_MGS_T IGM_MGS_GBS
+#define IGM_MGS_NST 4
+#define IGM_MGS_STG (16 * IGM_MGS_T + 32)
+#define IGM_MGS_RING (IGM_MGS_NST * IGM_MGS_STG)
+// resident rows of a CTA in ring mode
+#define IGM_MGS_WRING 9728
+
+struct MRing {
+  unsigned char *base;  // IGM_MGS_NST stages
+  u64 *full;            // one mbarrier per stage
+  unsigned tt;          // tiles streamed so far in this launch (all threads)
+};
+
+// the sums a streamed span adds to its pass
+struct MStreamOut {
+  i128 part;
+  unsigned evA, evB;
+};
+
+// rows [qa, qb) of segment c (qb - qa even; w 16-byte aligned at qa) in
+// pass i, one row a thread a tile; thread 0 issues the copies; tt0: the
+// tiles streamed before in this launch (the caller adds this span's)
+template <int MODE, bool HS32>
+__device__ __noinline__ MStreamOut pass_stream(const MPass P, const MSegC &c, int i, int qa,
+                                               int qb, unsigned char *base, u64 *full,
+                                               unsigned tt0, int *s_fail, unsigned *err0) {
+  constexpr int T = IGM_MGS_T, NS = IGM_MGS_NST;
+  const int L = qb - qa, nt = (L + T - 1) / T;
+  i128 part = 0;
+  unsigned evA = 0, evB = 0;
+  const size_t ep = (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0, ei = (size_t)i * c.n + c.row0;
+  auto stg = [&](int t) { return base + (size_t)((tt0 + t) % NS) * IGM_MGS_STG; };
+  auto bar = [&](int t) { return &full[(tt0 + t) % NS]; };
+  auto par = [&](int t) { return ((tt0 + t) / NS) & 1u; };
+  auto issue = [&](int t) {
+    const int r0 = qa + t * T, len = min(T, qb - r0);
+    unsigned char *b = stg(t);
+    const int pp = (int)((ep + r0) & 3), pc = (int)((ei + r0) & 3);
+    const unsigned bw = 8u * len, bp = MODE > 0 ? 4u * ((pp + len + 3) & ~3) : 0u,
+                   bc = MODE < 2 ? 4u * ((pc + len + 3) & ~3) : 0u;
+    mbar_expect_tx(bar(t), bw + bp + bc);
+    bulk_g2s(b, c.w + r0, bw, bar(t));
+    if (MODE > 0) bulk_g2s(b + 8 * T, c.V32 + (ep + r0 - pp), bp, bar(t));
+    if (MODE < 2) bulk_g2s(b + 12 * T + 16, c.V32 + (ei + r0 - pc), bc, bar(t));
+  };
+  int ni = 0;  // tiles issued (thread 0)
+  if (threadIdx.x == 0) {
+    bulk_wait<0>();       // w stored by the last pass has landed before it is read again
+    fence_proxy_async();  // the stages' last generic reads before their refill
+    for (; ni < nt && ni < NS - 1; ++ni) issue(ni);
+  }
+  __syncthreads();
+  int t = 0;
+  for (; t < nt && !*s_fail; ++t) {
+    const int r0 = qa + t * T, len = min(T, qb - r0);
+    unsigned char *b = stg(t);
+    const bool ok = mbar_wait(bar(t), par(t), err0, 1000000000ull);
+    if (!ok) *s_fail = 1;
+    const int q = threadIdx.x;
+    if (ok && q < len) {
+      i64 *ws = reinterpret_cast<i64 *>(b);
+      i64 wv[1] = {ws[q]};
+      int pv[1] = {0}, qq[1] = {0};
+      if (MODE > 0) pv[0] = reinterpret_cast<const int *>(b + 8 * T)[((ep + r0) & 3) + q];
+      if (MODE < 2) qq[0] = reinterpret_cast<const int *>(b + 12 * T + 16)[((ei + r0) & 3) + q];
+      rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
+      if (MODE > 0) ws[q] = wv[0];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !*s_fail) {
+      fence_proxy_async();  // the tile's generic accesses before the async ones
+      if (MODE > 0) {       // pass 0 leaves w as it is
+        bulk_s2g(c.w + r0, b, 8u * len);
+        bulk_commit();
+      }
+      if (ni < nt) {  // ni = t + NS - 1 reuses the stage of tile t - 1
+        bulk_wait_read<1>();
+        issue(ni++);
+      }
+    }
+  }
+  // an expired wait: the tiles already issued land before anything moves on
+  if (threadIdx.x == 0)
+    for (; t < ni; ++t) mbar_wait(bar(t), par(t), err0, 1000000000ull);
+  return MStreamOut{part, evA, evB};
+}
+
+// tiles of a streamed span [qa, qb)
+__host__ __device__ __forceinline__ int stream_tiles(int qa, int qb) {
+  return (qb - qa + IGM_MGS_T - 1) / IGM_MGS_T;
+}
+
 // resident basis buffers: per pass parity IGM_MGS_WMAX rows plus room for
 // each cached segment's alignment (a bulk copy starts on a 16-byte boundary
 // of the basis vector, up to 3 words before the segment's first row)
@@ -473,6 +572,9 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
 #define IGM_MGS_VOFF(S) (((size_t)(S) * 8 + 15) & ~(size_t)15)
 #define IGM_MGS_VB(S) ((((S) + 3) & ~3) + IGM_MGS_VPAD)
 #define IGM_MGS_SMEM(S) (IGM_MGS_VOFF(S) + 2 * sizeof(int) * (size_t)IGM_MGS_VB(S))
+// ... in ring mode the stages follow at a 128-byte boundary
+#define IGM_MGS_RINGOFF(S) ((IGM_MGS_SMEM(S) + 127) & ~(size_t)127)
+#define IGM_MGS_SMEM_RING(S) (IGM_MGS_RINGOFF(S) + (size_t)IGM_MGS_RING)
 
 // line 5 (Table 3) for the rows of segment c in the fused kernel: exact
 // int128 row sums over the SELL-32 copy of Abar_0 (one term, s = 0), the
@@ -546,16 +648,19 @@ __device__ bool mvtag_wait(const BatchDev &B, int sys, unsigned tag, const unsig
 // per segment and reads those of its systems' segments, so a CTA waits only
 // for the CTAs that share a system with it.  Lines 6-19 of step j (line 5
 // ran before).
+template <bool RING>
 __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, int j) {
   constexpr int BS = IGM_MGS_GBS;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int S = B.mgs_wrows;  // resident rows of this CTA
   i64 *sw = reinterpret_cast<i64 *>(smem);                    // w of the resident rows
   int *sv = reinterpret_cast<int *>(smem + IGM_MGS_VOFF(S));  // 2 basis buffers
   const int vb = IGM_MGS_VB(S);                               // words of one
+  constexpr bool ring = RING;  // further rows of narrow segments streamed
   __shared__ MSegC s_seg[IGM_MGS_GCACHE + 1];  // + one slot for the others in turn
   __shared__ i64 s_h[IGM_MGS_GCACHE];
   __shared__ __align__(8) u64 s_vbar[2];  // bulk copies into basis buffer 0 / 1
+  __shared__ __align__(8) u64 s_full[IGM_MGS_NST];  // ring stages
   __shared__ unsigned s_epoch, s_vbytes;
   __shared__ int s_fail;
   unsigned *err0 = &B.sys[0]->sc->err;
@@ -576,10 +681,12 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
     s_fail = 0;
     mbar_init(&s_vbar[0], 1);
     mbar_init(&s_vbar[1], 1);
+    for (int q = 0; q < IGM_MGS_NST; ++q) mbar_init(&s_full[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
   const unsigned epoch = s_epoch, e16 = (epoch & 0xffffu) << 16;
+  MRing R{smem + IGM_MGS_RINGOFF(S), s_full, 0u};
   // a segment's descriptor with the flags taken at the start (into c)
   auto seg_make = [&](int k, MSegC &c) {
     mseg_make(B, g0 + k, j, c);
@@ -651,8 +758,10 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
       P.qw = res_w(c);
       P.qv = res_v(c, k);
       P.w0s = false;
+      // ring mode: this segment's further rows are streamed
+      const bool strm = ring && c.narrow && k < IGM_MGS_GCACHE;
       // pull the global rows of v_{i+1} into L2 while this pass runs
-      if (i + 1 <= j && P.qv < P.nr) {
+      if (!strm && i + 1 <= j && P.qv < P.nr) {
         const size_t o = (size_t)(i + 1) * c.n + c.row0 + P.qv;
         const char *base = c.narrow ? (const char *)(c.V32 + o) : (const char *)(c.V + o);
         const size_t bytes = (size_t)(P.nr - P.qv) * (c.narrow ? sizeof(int) : sizeof(i64));
@@ -671,13 +780,45 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
       const bool hs32 = P.hs == (i64)(int)P.hs;
       i128 part = 0;
       unsigned evA = 0, evB = 0;
-      if (i == 0) pass_seg<0, true>(P, c, i, j, part, evA, evB);
+      auto run = [&](auto mode_tag, auto hs_tag) {
+        constexpr int MODE = decltype(mode_tag)::value;
+        constexpr bool HS = decltype(hs_tag)::value;
+        if (!RING || !strm) {
+          pass_seg<MODE, HS>(P, c, i, j, part, evA, evB);
+          return;
+        }
+        pass_res<MODE, HS>(P, part, evA, evB);
+        // the streamed span [qa, qb): w 16-byte aligned at qa, an even
+        // number of rows; the row before and the row after it (if any) go
+        // the per-thread way
+        int qa = P.qv;
+        if (qa < P.nr && (reinterpret_cast<uintptr_t>(c.w + qa) & 15)) ++qa;
+        const int qb = qa + ((P.nr - qa) & ~1);
+        const size_t op = (size_t)(i > 0 ? i - 1 : 0) * c.n + c.row0;
+        const size_t oi = (size_t)(i <= j ? i : 0) * c.n + c.row0;
+        MPass Q = P;
+        Q.nr = qa;
+        pass_glob<MODE, HS, int>(Q, c.V32 + op, c.V32 + oi, part, evA, evB);
+        const MStreamOut so =
+            pass_stream<MODE, HS>(P, c, i, qa, qb, R.base, R.full, R.tt, &s_fail, err0);
+        R.tt += stream_tiles(qa, qb);
+        part += so.part;
+        evA += so.evA;
+        evB += so.evB;
+        Q = P;
+        Q.qv = qb;
+        pass_glob<MODE, HS, int>(Q, c.V32 + op, c.V32 + oi, part, evA, evB);
+      };
+      using I0 = std::integral_constant<int, 0>;
+      using I1 = std::integral_constant<int, 1>;
+      using I2 = std::integral_constant<int, 2>;
+      if (i == 0) run(I0{}, std::true_type{});
       else if (i <= j) {
-        if (hs32) pass_seg<1, true>(P, c, i, j, part, evA, evB);
-        else pass_seg<1, false>(P, c, i, j, part, evA, evB);
+        if (hs32) run(I1{}, std::true_type{});
+        else run(I1{}, std::false_type{});
       } else {
-        if (hs32) pass_seg<2, true>(P, c, i, j, part, evA, evB);
-        else pass_seg<2, false>(P, c, i, j, part, evA, evB);
+        if (hs32) run(I2{}, std::true_type{});
+        else run(I2{}, std::false_type{});
       }
       flush_ev(evB, &c.sc->ev[IGM_EV_L8]);
       flush_ev(evA, &c.sc->ev[i <= j ? IGM_EV_L7 : IGM_EV_L10]);
@@ -710,6 +851,15 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
     __syncthreads();
     if (s_fail) break;
   }
+  // ring mode: the last pass's w stores have landed and are visible to the
+  // plain loads below
+  if (ring) {
+    if (threadIdx.x == 0) {
+      bulk_wait<0>();
+      fence_proxy_async_global();
+    }
+    __syncthreads();
+  }
   if (s_fail) {
     // the copy in flight lands before the CTA leaves (bounded again)
     if (vst) mbar_wait(&s_vbar[staged & 1], (unsigned)(staged >> 1) & 1u, err0, 1000000000ull);
@@ -731,7 +881,8 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
           const int q = q0 + u * BS;
-          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : wg[q];
+          // (from L2: in ring mode the copy engine wrote these rows)
+          wv[u] = q >= c.nrows ? 0 : q < qw ? ws[q] : __ldcg(wg + q);
         }
 #pragma unroll
         for (int u = 0; u < IGM_RPT; ++u) {
@@ -785,7 +936,7 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
 // by one CTA alone uses the CTA's pass sums directly.
 __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_fused(BatchDev B, int j0, int j1) {
   constexpr int BS = IGM_MGS_GBS;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int S = B.mgs_wrows;  // resident rows of this CTA
   i64 *sw = reinterpret_cast<i64 *>(smem);                    // w of the resident rows
   int *sv = reinterpret_cast<int *>(smem + IGM_MGS_VOFF(S));  // 2 basis buffers
@@ -1211,14 +1362,22 @@ int persistent_grid(int ntiles) {
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     // co-resident CTAs with the most dynamic shared memory a plan may give
     // the integer step (IGM_MGS_WMAX resident rows)
-    cudaFuncSetAttribute(k_mgs_step_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mgs_step_grid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
+    cudaFuncSetAttribute(k_mgs_step_grid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)IGM_MGS_SMEM_RING(IGM_MGS_WRING));
     cudaFuncSetAttribute(k_mgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)IGM_MGS_SMEM(IGM_MGS_WMAX));
     int a = 0, a2 = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step_grid, IGM_MGS_GBS,
+    int a3 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs_step_grid<false>, IGM_MGS_GBS,
                                                       IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a3, k_mgs_step_grid<true>, IGM_MGS_GBS,
+                                                      IGM_MGS_SMEM_RING(IGM_MGS_WRING)) !=
+        cudaSuccess)
+      a3 = 1;
+    a = a < a3 ? a : a3;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_mgs_fused, IGM_MGS_GBS,
                                                       IGM_MGS_SMEM(IGM_MGS_WMAX)) != cudaSuccess)
       a2 = 1;
@@ -1249,8 +1408,11 @@ void launch_fp64_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
 // shares); with snap > 0 a boundary inside a system moves to that system's
 // nearer end when it is within snap % of a share, so that more systems lie
 // in one CTA whole (no exchange of pass sums) at the price of balance.
-void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, int &G,
-              std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows,
+// ring_ok: the single-step kernel may stream the rows beyond the resident
+// ones (ring mode: fewer resident rows, room for the stages); chosen when
+// some CTA has more rows than fit resident without it.
+void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, bool ring_ok, int &G,
+              std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows, int &ring,
               std::vector<int> &sys_seg) {
   // rows a CTA may keep resident in shared memory: 0 automatic, -1 none,
   // k > 0 at most k (never above what the kernel reserves)
@@ -1299,6 +1461,8 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, int &
   ptr[G] = (int)seg.size();
   wrows = std::min(maxrows, cap);
   rows = maxrows;
+  ring = ring_ok && maxrows > wrows;
+  if (ring) wrows = std::min(wrows, IGM_MGS_WRING);
   // segments run in system order: system s owns [sys_seg[s], sys_seg[s+1])
   sys_seg.assign(n.size() + 1, (int)seg.size());
   for (int g = (int)seg.size() - 1; g >= 0; --g) sys_seg[seg[g].sys] = g;
@@ -1313,10 +1477,11 @@ void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   int G = B.mgs_g;
   BatchDev b = B;
   void *args[] = {&b, &j};
+  const size_t sm = B.mgs_ring ? IGM_MGS_SMEM_RING(B.mgs_wrows) : IGM_MGS_SMEM(B.mgs_wrows);
   // cooperative: every CTA resident at once (CTAs wait for each other's sums)
-  note_launch(cudaLaunchCooperativeKernel((const void *)k_mgs_step_grid, dim3(G),
-                                          dim3(IGM_MGS_GBS), args, IGM_MGS_SMEM(B.mgs_wrows),
-                                          st));
+  const void *k = B.mgs_ring ? (const void *)k_mgs_step_grid<true>
+                             : (const void *)k_mgs_step_grid<false>;
+  note_launch(cudaLaunchCooperativeKernel(k, dim3(G), dim3(IGM_MGS_GBS), args, sm, st));
 }
 
 void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st) {

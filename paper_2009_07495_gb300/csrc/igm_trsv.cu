@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   typedef typename TrsvT<KIND>::V V;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_t;
+  __shared__ int s_poison;     // a compute-side wait expired: no slot is read again
   __shared__ unsigned s_done;  // groups the compute warps have finished
   __shared__ __align__(8) u64 s_blk[IGM_TRSV_NA_MAX];  // a slot's block has landed
   __shared__ __align__(8) u64 s_rdy[IGM_TRSV_NA_MAX];  // ... and its right-hand sides
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   if (threadIdx.x == 0) {
     s_t = (int)atomicAdd(&B.ticket[tk], 1u);
     s_done = 0;
+    s_poison = 0;
     for (int k = 0; k < IGM_TRSV_NA_MAX; ++k) {
       mbar_init(&s_blk[k], 1);
       mbar_init(&s_rdy[k], 33);  // the gather warp's 32 copy arrivals and lane 0
@@ -612,13 +614,14 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
     return;
   }
 
-  // compute warps.  A thread whose wait for a slot expired never reads a
-  // slot's contents again (they may be stale or never written): it keeps
-  // its barrier obligations and leaves its rows alone; the call reports
-  // IGM_ETIMEOUT.
+  // compute warps.  One idle-most thread (the last) waits for group l's
+  // slot and predecessor copies before the group's barrier, which then
+  // passes their arrival on to every compute thread.  If that wait expires
+  // no compute thread reads a slot's contents again (they may be stale or
+  // never written): they keep their barrier obligations and leave their
+  // rows alone; the call reports IGM_ETIMEOUT.
   const int tid = threadIdx.x;
   unsigned ev = 0;
-  bool poisoned = false;
   auto late = [&](int code) -> V {
     const int pj = -1 - code;
     if (!single && pj < first)
@@ -629,15 +632,16 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   int cs = 0, us = 0;  // slot of group l and its uses before l (l mod na, l / na)
   int cb = 0, up = 0;  // barrier of group l's predecessor copy (l mod NB, l / NB)
   for (int l = 0; l < nlev; ++l) {
-    __syncwarp();
-    // the previous group's ring values are visible
-    asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC) : "memory");
-    if (tid == 0 && l > 0) st_release_cta(&s_done, (unsigned)l);
-    const int p0 = LPTR(l), w = LPTR(l + 1) - p0;
-    if (tid < w && !poisoned &&
+    if (tid == IGM_TRSV_NC - 1 && !s_poison &&
         !(mbar_wait(&s_rdy[cs], (unsigned)us & 1u, err, 2 * wns) &&
           mbar_wait(&s_barp[cb], (unsigned)up & 1u, err, 2 * wns)))
-      poisoned = true;
+      s_poison = 1;
+    __syncwarp();
+    // the previous group's ring values and group l's slot are visible
+    asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC) : "memory");
+    if (tid == IGM_TRSV_NC - 2 && l > 0) st_release_cta(&s_done, (unsigned)l);
+    const int p0 = LPTR(l), w = LPTR(l + 1) - p0;
+    const bool poisoned = s_poison != 0;
     if (tid < w && !poisoned) {
       const unsigned wp = trsv_wp(w);
       const unsigned char *blk = smem + Ly.oSlots + (size_t)cs * Ly.szSlot;
@@ -745,7 +749,7 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
   }
   __syncwarp();
   asm volatile("bar.sync 2, %0;" ::"n"(IGM_TRSV_NC) : "memory");
-  if (tid == 0) st_release_cta(&s_done, (unsigned)nlev);
+  if (tid == IGM_TRSV_NC - 2) st_release_cta(&s_done, (unsigned)nlev);
   if (KIND == TK_INT) flush_ev(ev, &sc->ev[IGM_EV_L5P]);
 #undef LPTR
 #undef NEED

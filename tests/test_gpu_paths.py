@@ -214,6 +214,35 @@ def test_fused_batch_bit_exact(L, orc, fuse, snap):
         sv.close()
 
 
+@pytest.mark.parametrize("wmax", [-1, 500])
+def test_arnoldi_ring_tiles_bit_exact(L, orc, wmax):
+    """The single-step Arnoldi kernel's ring mode (preconditioned systems
+    whose CTAs hold more rows than stay resident): 216,000 rows over 152
+    CTAs are 1,421 rows a CTA, streamed through the copy engine's stage ring
+    as one full and one partial tile after 0 or 500 resident rows, at every
+    alignment of a CTA's first row.  One inner solve (basis, Hessenberg
+    matrix, rotations, x, overflow counts) equals the oracle's bit for bit."""
+    s = W.small_cd3d(60, seed=303)
+    P = L.params_default(1, 12)
+    P.mgs_wmax = wmax
+    d = orc.setup(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
+    bk = d["b"] / np.abs(d["b"]).max()
+    x0 = np.random.default_rng(11).standard_normal(s.n) * 1e-3
+    o = orc.int_gmres(_oparams(orc, P), d, bk, x0)
+    solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    _compare_inner(solver.state(), o)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    np.testing.assert_array_equal(rep["ev"], o["ev"])
+    # a second inner solve on the same handle (the stage ring's barriers go
+    # on counting across launches)
+    xk = _dev(x0)
+    rep = solver.inner_solve(_dev(bk), xk)
+    np.testing.assert_array_equal(xk.cpu().numpy(), o["x"])
+    solver.close()
+
+
 def test_arnoldi_global_w_batched_equals_solo(L, orc):
     """A batch whose Arnoldi step keeps w in global memory: each system's
     result equals the oracle's (and so its solo solve)."""
