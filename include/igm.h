@@ -112,9 +112,12 @@ typedef struct {
                     used by int_gmres_solve.                              */
   /* Launch-configuration knobs (the results do not depend on them; tests use
      them to reach every code path on small systems). */
-  int mgs_wmax;  /* rows of w one CTA of the Arnoldi step (lines 6-11) may
-                    keep in shared memory: 0 automatic (26,624), -1 none (w
-                    stays in global memory), k > 0 at most k rows; a CTA's
+  int mgs_wmax;  /* rows one CTA of the Arnoldi step (lines 5/6-11) may keep
+                    resident in shared memory (w and the int32 basis words):
+                    0 automatic (13,952; 9,728 when the step streams the
+                    CTA's further rows through the copy engine, which it
+                    does for preconditioned systems with more rows a CTA
+                    than that), -1 none, k > 0 at most k rows; a CTA's
                     further rows keep w in global memory.  In a batch the
                     first system's value applies.                         */
   int wait_us;   /* bound of each device wait of the line-1'/5' substitutions

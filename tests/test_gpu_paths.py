@@ -1,6 +1,8 @@
 """GPU parity on the paths the small cases do not reach: the Arnoldi step
-with w in global memory (the path of CTAs with more than 26,624 rows,
-forced here on small systems by params.mgs_wmax), basis entries outside
+with w in global memory (the path of CTAs with more rows than stay resident
+in shared memory, forced here on small systems by params.mgs_wmax; for
+preconditioned systems those rows stream through the copy engine's stage
+ring), basis entries outside
 int32 (d_f > 30: the readers switch from the int32 copy of the basis to
 the int64 one), the 27-point
 sigma = 2.5 / convection +-100 coefficient regime of the largest
