@@ -471,12 +471,13 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
 // so that memory traffic and row arithmetic overlap.  A stage holds w (8T
 // bytes), v_{i-1} and v_i (4T + 16 bytes each: a copy starts at the 16-byte
 // boundary below the tile, the misalignment kept as an offset).
-#define IGM_MGS_T IGM_MGS_GBS
-#define IGM_MGS_NST 4
+#define IGM_MGS_TR 2  // rows a thread a tile
+#define IGM_MGS_T (IGM_MGS_TR * IGM_MGS_GBS)
+#define IGM_MGS_NST 3
 #define IGM_MGS_STG (16 * IGM_MGS_T + 32)
 #define IGM_MGS_RING (IGM_MGS_NST * IGM_MGS_STG)
 // resident rows of a CTA in ring mode
-#define IGM_MGS_WRING 9728
+#define IGM_MGS_WRING 7680
 
 struct MRing {
   unsigned char *base;  // IGM_MGS_NST stages
@@ -491,7 +492,7 @@ struct MStreamOut {
 };
 
 // rows [qa, qb) of segment c (qb - qa even; w 16-byte aligned at qa) in
-// pass i, one row a thread a tile; thread 0 issues the copies; tt0: the
+// pass i, IGM_MGS_TR rows a thread a tile; thread 0 issues the copies; tt0: the
 // tiles streamed before in this launch (the caller adds this span's)
 template <int MODE, bool HS32>
 __device__ __noinline__ MStreamOut pass_stream(const MPass P, const MSegC &c, int i, int qa,
@@ -529,15 +530,28 @@ __device__ __noinline__ MStreamOut pass_stream(const MPass P, const MSegC &c, in
     unsigned char *b = stg(t);
     const bool ok = mbar_wait(bar(t), par(t), err0, 1000000000ull);
     if (!ok) *s_fail = 1;
-    const int q = threadIdx.x;
-    if (ok && q < len) {
+    if (ok) {
       i64 *ws = reinterpret_cast<i64 *>(b);
-      i64 wv[1] = {ws[q]};
-      int pv[1] = {0}, qq[1] = {0};
-      if (MODE > 0) pv[0] = reinterpret_cast<const int *>(b + 8 * T)[((ep + r0) & 3) + q];
-      if (MODE < 2) qq[0] = reinterpret_cast<const int *>(b + 12 * T + 16)[((ei + r0) & 3) + q];
+      const int *vp = reinterpret_cast<const int *>(b + 8 * T) + ((ep + r0) & 3);
+      const int *vc = reinterpret_cast<const int *>(b + 12 * T + 16) + ((ei + r0) & 3);
+      i64 wv[IGM_MGS_TR];
+      int pv[IGM_MGS_TR], qq[IGM_MGS_TR];
+#pragma unroll
+      for (int u = 0; u < IGM_MGS_TR; ++u) {
+        const int q = threadIdx.x + u * IGM_MGS_GBS;
+        const bool in = q < len;
+        wv[u] = in ? ws[q] : 0;
+        pv[u] = (MODE > 0 && in) ? vp[q] : 0;
+        qq[u] = (MODE < 2 && in) ? vc[q] : 0;
+      }
       rows_pass<MODE, HS32>(wv, pv, qq, P.hs, P.s8, P.sA, part, evA, evB);
-      if (MODE > 0) ws[q] = wv[0];
+      if (MODE > 0) {
+#pragma unroll
+        for (int u = 0; u < IGM_MGS_TR; ++u) {
+          const int q = threadIdx.x + u * IGM_MGS_GBS;
+          if (q < len) ws[q] = wv[u];
+        }
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0 && !*s_fail) {
