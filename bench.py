@@ -542,6 +542,8 @@ def run_ours(args, wl):
                        "shifts_start": [P.beta7, P.beta8, P.beta10, P.beta13, P.beta15],
                        "shift_retries": rep["shift_retries"],
                        "shifts_final": list(rep["beta_final"]),
+                       "arnoldi_launch": {"fuse_steps": rep["fuse_steps"],
+                                          "plan_snap": rep["plan_snap"]},
                        "l2": f"working set (~{ws_bytes / 1e9:.0f} GB) > L2 "
                              "(129 MB), no flush",
                        "parallelism": f"replicas x{world}"},

@@ -114,7 +114,7 @@ typedef struct {
      them to reach every code path on small systems). */
   int mgs_wmax;  /* rows one CTA of the Arnoldi step (lines 5/6-11) may keep
                     resident in shared memory (w and the int32 basis words):
-                    0 automatic (13,952; 7,680 when the step streams the
+                    0 automatic (13,952; 3,584 when the step streams the
                     CTA's further rows through the copy engine, which it
                     does for preconditioned systems with more rows a CTA
                     than that), -1 none, k > 0 at most k rows; a CTA's

@@ -473,11 +473,11 @@ __device__ __forceinline__ void pass_seg(const MPass &P, const MSegC &c, int i, 
 // boundary below the tile, the misalignment kept as an offset).
 #define IGM_MGS_TR 2  // rows a thread a tile
 #define IGM_MGS_T (IGM_MGS_TR * IGM_MGS_GBS)
-#define IGM_MGS_NST 3
+#define IGM_MGS_NST 5
 #define IGM_MGS_STG (16 * IGM_MGS_T + 32)
 #define IGM_MGS_RING (IGM_MGS_NST * IGM_MGS_STG)
 // resident rows of a CTA in ring mode
-#define IGM_MGS_WRING 7680
+#define IGM_MGS_WRING 3584
 
 struct MRing {
   unsigned char *base;  // IGM_MGS_NST stages

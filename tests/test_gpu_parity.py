@@ -466,15 +466,18 @@ def test_shift_tune_batched_and_served(L, orc):
         sv.close()
 
 
+@pytest.mark.parametrize("fuse", [-1, 10])
 @pytest.mark.parametrize("count", [64, 80])
-def test_batched_many_tiny_systems(L, orc, count):
+def test_batched_many_tiny_systems(L, orc, count, fuse):
     """Tiny systems (n = 9) batched so that every row fits one CTA: 64
     systems run the Arnoldi step's one-CTA mode (its segment cache full),
     80 the cooperative grid mode with one CTA whose segments overflow the
-    cache.  Every result equals the oracle's bit for bit."""
+    cache, one step a launch or (fuse = 10) ten steps a fused launch.
+    Every result equals the oracle's bit for bit."""
     import torch
     systems = [W.small_cd2d(3, seed=200 + k) for k in range(count)]
     P = L.params_default(0, 10)
+    P.fuse_steps = fuse
     svs = [L.Solver(_dev(sy.rowptr), _dev(sy.col), _dev(sy.val), P) for sy in systems]
     out = [torch.empty(sy.n, dtype=torch.float64, device="cuda") for sy in systems]
     reps = L.ir_solve_batched(svs, [_dev(sy.b) for sy in systems], out)
@@ -488,13 +491,15 @@ def test_batched_many_tiny_systems(L, orc, count):
         sv.close()
 
 
+@pytest.mark.parametrize("fuse", [-1, 30])
 @pytest.mark.parametrize("n", [1024, 1025])
-def test_arnoldi_mode_boundary(L, orc, n):
+def test_arnoldi_mode_boundary(L, orc, n, fuse):
     """n = 1024 is the largest system of the one-CTA Arnoldi mode, 1025 the
-    smallest of the grid mode (two CTAs): both equal the oracle bit for
-    bit, including the basis and Hessenberg state of the last inner solve."""
+    smallest of the grid mode (two CTAs, one Arnoldi launch a step or a
+    whole cycle in one fused launch): all equal the oracle bit for bit."""
     s = W.config0() if n == 1024 else W.banded_random(1025, np.random.default_rng(7))
     P = L.params_default(0, 30)
+    P.fuse_steps = fuse
     xo, ro = orc.ir_solve(s.rowptr, s.col, s.val, s.b, _oparams(orc, P))
     solver = L.Solver(_dev(s.rowptr), _dev(s.col), _dev(s.val), P)
     x, rep = solver.ir_solve(_dev(s.b))

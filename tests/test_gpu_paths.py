@@ -105,21 +105,25 @@ def test_arnoldi_global_w_bit_exact(L, orc, name, sf, prec, m, wmax):
 # entries outside int32 at line 11): short solves cut by overflow breakdowns
 # and full ones where the basis leaves int32 partway (d_f = 34 with shifts
 # raised by 4 gives 2 such entries late in the 30 steps)
-WIDE = [(0, 31, 0, 500, False), (0, 32, 2, -1, False), (0, 34, 0, 0, True),
-        (1, 33, 1, -1, True), (1, 34, 4, 500, True)]
+WIDE = [(0, 31, 0, 500, False, 0), (0, 32, 2, -1, False, 0), (0, 34, 0, 0, True, -1),
+        (0, 34, 0, 0, True, 30), (0, 34, 0, 0, True, 7), (1, 33, 1, -1, True, 0),
+        (1, 34, 4, 500, True, 0)]
 
 
-@pytest.mark.parametrize("prec,df,dd,wmax,wide", WIDE,
-                         ids=[f"p{c[0]}_df{c[1]}_dd{c[2]}_w{c[3]}" for c in WIDE])
-def test_wide_basis_bit_exact(L, orc, prec, df, dd, wmax, wide):
+@pytest.mark.parametrize("prec,df,dd,wmax,wide,fuse", WIDE,
+                         ids=[f"p{c[0]}_df{c[1]}_dd{c[2]}_w{c[3]}_f{c[5]}" for c in WIDE])
+def test_wide_basis_bit_exact(L, orc, prec, df, dd, wmax, wide, fuse):
     """With d_f > 30 a basis entry (at most 2^d_f in magnitude) can leave
     int32, which the kernels detect (at line 2 or line 11) and answer by
-    reading the int64 copy of the basis for the rest of the inner solve:
-    the basis, Hessenberg matrix, rotations, x and every overflow count equal
-    the oracle's bit for bit, line 11's basis entries outside int32 are
-    counted alike, and the refinement loop agrees."""
+    reading the int64 copy of the basis for the rest of the inner solve
+    (one Arnoldi launch a step, or the fused kernel with a whole cycle or 7
+    steps a launch, or as the autotuner chooses): the basis,
+    Hessenberg matrix, rotations, x and every overflow count equal the
+    oracle's bit for bit, line 11's basis entries outside int32 are counted
+    alike, and the refinement loop agrees."""
     s = W.small_cd2d(60) if prec else W.banded_random(6000, np.random.default_rng(320))
     P = L.params_default(prec, 30)
+    P.fuse_steps = fuse
     P.df = df
     for f in ("beta7", "beta8", "beta10", "beta11a", "beta11b", "beta13", "beta15",
               "beta16a", "beta16b"):
