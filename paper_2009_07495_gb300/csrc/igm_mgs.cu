@@ -90,6 +90,12 @@ __device__ __forceinline__ void mgs_cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// every group but the N most recent complete
+template <int N>
+__device__ __forceinline__ void mgs_cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ bool m_step(const SysDev *s, int j) {
   return s->sc->cyc != 0 && s->sc->early == 0 && j < s->p.m;
 }
@@ -182,40 +188,44 @@ __device__ __forceinline__ void givens_tail(const BatchDev &B, const MSegC &c, i
 // One CTA of IGM_MGS_ONE_BLOCK threads holds every row of every system
 // (small batches, mgs_one_cta): each system is one segment of it, w stays in
 // shared memory, the pass totals stay in shared memory and a block barrier
-// ends each pass; the basis vectors are staged in shared memory (v_{i+1}
-// copied asynchronously during pass i, so no pass waits on a global load).
+// ends each pass; the basis vectors are staged in shared memory, v_{i+D}
+// copied asynchronously while pass i runs (D = IGM_ONE_NBUF - 2 passes
+// ahead, so a pass waits on no global load).
+#define IGM_ONE_NBUF 5
 __global__ void __launch_bounds__(IGM_MGS_ONE_BLOCK, 1) k_mgs_one(BatchDev B, int j) {
-  constexpr int BS = IGM_MGS_ONE_BLOCK;
-  extern __shared__ i64 sw[];  // every row of w
+  constexpr int BS = IGM_MGS_ONE_BLOCK, NB = IGM_ONE_NBUF, D = IGM_ONE_NBUF - 2;
+  extern __shared__ i64 s_dyn[];
+  i64 (*s_v)[IGM_MGS_BLOCK] = reinterpret_cast<i64 (*)[IGM_MGS_BLOCK]>(s_dyn);  // v_i: s_v[i % NB]
+  i64 *sw = s_dyn + NB * IGM_MGS_BLOCK;                                        // every row of w
   __shared__ MSegC s_seg[IGM_MSEG_CACHE];
   __shared__ i64 s_h[IGM_MSEG_CACHE];
   __shared__ i128 s_tot[IGM_MSEG_CACHE];
-  __shared__ i64 s_v[3][IGM_MGS_BLOCK];  // v_{i-1}, v_i, v_{i+1}
   const int ns = B.mseg_ptr[1];
   for (int k = threadIdx.x; k < ns; k += BS) mseg_make(B, k, j, s_seg[k]);
   __syncthreads();
-  // stage v_i into s_v[i % 3]
+  // stage v_i into s_v[i % NB] (nothing for i > j); one copy group either way
   auto stage = [&](int i) {
-    for (int k = 0; k < ns; ++k) {
+    for (int k = 0; k < ns && i <= j; ++k) {
       const MSegC &c = s_seg[k];
       if (!c.active) continue;
       const i64 *src = c.V + (size_t)i * c.n + c.row0;
-      i64 *dst = &s_v[i % 3][c.off];
+      i64 *dst = &s_v[i % NB][c.off];
       for (int q = threadIdx.x; q < c.nrows; q += BS) mgs_cp_async8(dst + q, src + q);
     }
     mgs_cp_async_commit();
   };
-  stage(0);
-  mgs_cp_async_wait_all();
+  for (int t = 0; t < D; ++t) stage(t);
+  mgs_cp_async_wait<D - 1>();  // v_0
   __syncthreads();
   for (int i = 0; i <= j + 1; ++i) {
-    if (i + 1 <= j) stage(i + 1);
+    // into the buffer of v_{i-2}, last read in pass i - 1
+    stage(i + D);
     for (int k = 0; k < ns; ++k) {
       const MSegC &c = s_seg[k];
       if (!c.active) continue;
       const i64 hs = i == 0 ? 0 : s_h[k];
       const int nr = c.nrows;
-      const i64 *vp = &s_v[(i + 2) % 3][c.off], *vi = &s_v[i % 3][c.off];
+      const i64 *vp = &s_v[(i + NB - 1) % NB][c.off], *vi = &s_v[i % NB][c.off];
       const i64 *wg = c.w;
       i64 *ws = sw + c.off;
       const int s8 = shc(c.df - c.b8), s7 = shc(c.b7), s10 = shc(c.b10);
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(IGM_MGS_ONE_BLOCK, 1) k_mgs_one(BatchDev B, in
     __syncthreads();
     for (int k = threadIdx.x; k < ns; k += BS)
       if (s_seg[k].active) s_h[k] = mseg_coef(s_seg[k], s_tot[k], i, j);
-    mgs_cp_async_wait_all();  // v_{i+1} is in place for pass i+1
+    mgs_cp_async_wait<D - 1>();  // v_{i+1} is in place for pass i+1
     __syncthreads();
   }
   // line 11 for every system whose divisor is non-zero
@@ -1484,7 +1494,13 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, bool 
 
 void launch_mgs_step(const BatchDev &B, int j, cudaStream_t st) {
   if (mgs_one_cta(B, B.nsys)) {
-    k_mgs_one<<<1, IGM_MGS_ONE_BLOCK, (size_t)B.mgs_wrows * sizeof(i64), st>>>(B, j);
+    static std::once_flag one_attr;  // basis buffers + w: beyond 48 KB
+    std::call_once(one_attr, [] {
+      cudaFuncSetAttribute(k_mgs_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((IGM_ONE_NBUF + 1) * IGM_MGS_BLOCK * sizeof(i64)));
+    });
+    k_mgs_one<<<1, IGM_MGS_ONE_BLOCK,
+                (size_t)(IGM_ONE_NBUF * IGM_MGS_BLOCK + B.mgs_wrows) * sizeof(i64), st>>>(B, j);
     return;
   }
   persistent_grid(1);  // sets the kernel's shared-memory attribute once

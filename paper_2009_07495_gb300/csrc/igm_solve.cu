@@ -430,8 +430,11 @@ __global__ void __launch_bounds__(IGM_BACKSUB_BLOCK) k_backsub(BatchDev B) {
 }
 
 // line 23 and eq. (update): x^(k) = sum_i y_i v_i; refinement mode adds
-// gamma x^(k) to x, single-solve mode adds the sum to the caller's guess
-__global__ void k_update(BatchDev B) {
+// gamma x^(k) to x, single-solve mode adds the sum to the caller's guess.
+// Each tile is split over gridDim.y CTAs, one row a thread: the sums are
+// FP64 chains, so a small system spreads them over several SMs.
+#define IGM_UPD_SPLIT 8
+__global__ void __launch_bounds__(IGM_TILE / IGM_UPD_SPLIT) k_update(BatchDev B) {
   Tile tl = B.tiles[blockIdx.x];
   const SysDev *s = B.sys[tl.sys];
   SysScal *sc = s->sc;
@@ -446,7 +449,9 @@ __global__ void k_update(BatchDev B) {
   // operations (GB300's FP64 rate is low); the basis as int32 words unless an
   // entry of this inner solve left int32
   const bool narrow = sc->vwide == 0;
-  TILE_LOOP(l) {
+  const int r0 = tl.row0 + (int)blockIdx.y * (IGM_TILE / IGM_UPD_SPLIT),
+            r1 = min(tl.row0 + tl.nrows, r0 + IGM_TILE / IGM_UPD_SPLIT);
+  for (int l = r0 + (int)threadIdx.x; l < r1; l += blockDim.x) {
     double acc = ir ? 0.0 : s->xk[l];
 #pragma unroll 8
     for (int i = 0; i < jeff; ++i) {
@@ -587,7 +592,7 @@ void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st) {
   k_gather_state<<<nb_sys(B), 128, 0, st>>>(B, out);
 }
 void launch_update(const BatchDev &B, cudaStream_t st) {
-  k_update<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);
+  k_update<<<dim3(B.ntiles, IGM_UPD_SPLIT), IGM_TILE / IGM_UPD_SPLIT, 0, st>>>(B);
 }
 
 }  // namespace igm
