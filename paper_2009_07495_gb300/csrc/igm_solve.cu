@@ -305,7 +305,7 @@ __global__ void k_cast_v1(BatchDev B) {
 // ---------------------------------------------------------------------------
 template <bool MT>
 __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     B.ticket[2] = 0;
     B.ticket[3] = 0;
   }
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   const SysDev *s = B.sys[tl.sys];
   SysScal *sc = s->sc;
   if (!g_step(sc) || j >= s->p.m) return;
-  if (blockIdx.x == tl.first && threadIdx.x == 0) sc->seq += 1;
+  if (blockIdx.x == tl.first && blockIdx.y == 0 && threadIdx.x == 0) sc->seq += 1;
   const i64 *vj = s->V + (size_t)j * s->n;
   const int *vj32 = s->V32 + (size_t)j * s->n;
   // the basis as int32 words unless an entry of this inner solve left int32
@@ -326,7 +326,11 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
   // values and columns is one coalesced 256 / 128-byte access; padding
   // entries have value 0 (no product, no event)
   const int ns = MT ? s->ns : 0;
-  TILE_LOOP(i) {
+  // gridDim.y CTAs share a tile (few tiles: the rows' load latency spread
+  // over more SMs)
+  const int span = IGM_TILE / (int)gridDim.y;
+  const int r0 = tl.row0 + (int)blockIdx.y * span, r1 = min(tl.row0 + tl.nrows, r0 + span);
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
     const int sl = i >> 5;
     const long long base = sptr[sl] + (i & 31);
     const int len = (int)((sptr[sl + 1] - sptr[sl]) >> 5);
@@ -575,9 +579,15 @@ void launch_arm(const BatchDev &B, cudaStream_t st) {
 void launch_cast_v1(const BatchDev &B, cudaStream_t st) {
   k_cast_v1<<<B.ntiles, IGM_BLOCK, 0, st>>>(B);
 }
+#define IGM_SPMV_SPLIT 8
+#define IGM_SPMV_SMALL 152
 void launch_spmv(const BatchDev &B, int j, cudaStream_t st) {
-  if (B.max_ns > 0) k_spmv<true><<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
-  else k_spmv<false><<<B.ntiles, IGM_BLOCK, 0, st>>>(B, j);
+  // fewer tiles than SMs: each tile over IGM_SPMV_SPLIT CTAs, one row a thread
+  const int y = B.ntiles < IGM_SPMV_SMALL ? IGM_SPMV_SPLIT : 1;
+  const dim3 g(B.ntiles, y);
+  const int bs = y > 1 ? IGM_TILE / y : IGM_BLOCK;
+  if (B.max_ns > 0) k_spmv<true><<<g, bs, 0, st>>>(B, j);
+  else k_spmv<false><<<g, bs, 0, st>>>(B, j);
 }
 void launch_backsub(const BatchDev &B, cudaStream_t st) {
   static std::once_flag attr_once;
