@@ -257,6 +257,7 @@ void enqueue_inner(Batch *b, cudaStream_t st) {
 }
 
 igm_status capture_graphs(Batch *b) {
+  IGM_RANGE("capture the launch graphs of Fig. 1 and Fig. 2");
   if (b->g_check && b->g_cycle) return IGM_OK;
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -451,6 +452,18 @@ igm_status err_status(unsigned e) {
   return IGM_OK;
 }
 
+#ifdef IGM_CHECKS
+// checked builds: a failed device check (the first failing site of each
+// translation unit, igm_dev.cuh CheckSite)
+igm_status device_checks() {
+  const unsigned m = checks_read_mgs(), t = checks_read_trsv(), v = checks_read_solve();
+  if (m | t | v)
+    return fail(IGM_ECUDA, "device check failed (first sites: Arnoldi %u, substitution %u, SpMV %u)",
+                m, t, v);
+  return IGM_OK;
+}
+#endif
+
 void fill_report(const SysScal &sc, igm_report *rep) {
   if (!rep) return;
   memset(rep, 0, sizeof(*rep));
@@ -528,6 +541,7 @@ igm_status int_gmres_setup(int n, int nnz, const int *rowptr, const int *col,
                            const double *val, const igm_params *params, void *stream,
                            igm_handle *out) {
   g_err.clear();
+  IGM_RANGE("int_gmres_setup: scaling, cast, ILU(0) (Sec. III, IV-B, VI-A)");
   if (!out) return fail(IGM_EINVAL, "out is NULL");
   *out = nullptr;
   igm_status st = check_params(params);
@@ -1139,6 +1153,9 @@ igm_status check_errors(Batch *b, cudaStream_t s) {
   unsigned e = 0;
   CK(cudaMemcpyAsync(&e, &b->hs[0]->d_sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+#ifdef IGM_CHECKS
+  if (igm_status c = device_checks()) return c;
+#endif
   return e ? err_status(e) : IGM_OK;
 }
 
@@ -1150,6 +1167,7 @@ igm_status check_errors(Batch *b, cudaStream_t s) {
 // from its own set-up (k_init_scal resets every counter the trial touched).
 igm_status tune_batch(Batch *b, cudaStream_t s) {
   if (!b->tune) return IGM_OK;
+  IGM_RANGE("autotuner: Arnoldi launch configuration");
   b->tune = false;
   const igm_params &P = b->hs[0]->prm;
   const int m = b->m, ns = (int)b->hs.size();
@@ -1232,6 +1250,7 @@ igm_status run_ir(Batch *b, cudaStream_t s) {
   int maxr = 0;  // refinements plus the inner solves auto-tuning may discard
   for (auto h : b->hs) maxr = std::max(maxr, h->prm.max_refine + h->prm.shift_tune);
   for (int k = 0; k <= maxr + 1; ++k) {
+    IGM_RANGE("refinement: Fig. 1 test, then one Fig. 2 inner solve");
     CK(cudaGraphLaunch(b->g_check, s));
     g_launches += b->nodes_check;
     CK(cudaMemcpyAsync(b->h_nact, B.nact, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1256,6 +1275,12 @@ igm_status collect_host(igm_handle h, igm_report *rep, cudaStream_t s) {
     rep->fuse_steps = h->ran_fuse;
     rep->plan_snap = h->ran_snap;
   }
+#ifdef IGM_CHECKS
+  if (igm_status c = device_checks()) {
+    if (rep) rep->status = c;
+    return c;
+  }
+#endif
   if (e) {
     igm_status st = err_status(e);
     if (rep) rep->status = st;
@@ -1270,6 +1295,7 @@ extern "C" {
 igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *rep,
                     void *stream) {
   g_err.clear();
+  IGM_RANGE("ir_solve (Fig. 1)");
   if (!h || !bhat || !xhat) return fail(IGM_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   {
@@ -1288,6 +1314,7 @@ igm_status ir_solve(igm_handle h, const double *bhat, double *xhat, igm_report *
 igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat,
                             double *const *xhat, igm_report *reps, void *stream) {
   g_err.clear();
+  IGM_RANGE("ir_solve_batched (Fig. 1 over a batch)");
   if (count < 1 || !hs || !bhat || !xhat) return fail(IGM_EINVAL, "bad batch arguments");
   std::vector<igm_handle> v(hs, hs + count);
   for (int i = 0; i < count; ++i) {
@@ -1331,6 +1358,7 @@ igm_status ir_solve_batched(int count, igm_handle *hs, const double *const *bhat
 igm_status int_gmres_solve(igm_handle h, const double *bk, double *xk, igm_report *rep,
                            void *stream) {
   g_err.clear();
+  IGM_RANGE("int_gmres_solve (Fig. 2)");
   if (!h || !bk || !xk) return fail(IGM_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   Batch *b = h->solo;

@@ -17,6 +17,35 @@ typedef unsigned __int128 u128;
 
 namespace igm {
 
+// ---- checked builds (-DIGM_CHECKS: build variant "checks") ----------------
+// IGM_OK(cond, site) is true in normal builds (cond is not evaluated).  In a
+// checked build a false cond records the first failing site in the
+// translation unit's igm_chk word, which the host reads after each solve
+// (the call then fails with IGM_ECUDA naming the site), and the caller skips
+// the access the condition guards.
+enum CheckSite : unsigned {
+  CHK_BULK_G2S = 1,   // bulk copy global -> shared: 16-byte addresses and size
+  CHK_BULK_S2G = 2,   // bulk copy shared -> global: the same
+  CHK_SPMV_COL = 3,   // SpMV gather (line 5): column inside the system
+  CHK_TRSV_RHS = 4,   // substitution gather (line 5'): right-hand side row
+  CHK_MGS_STAGE = 5,  // Arnoldi basis copy inside its shared-memory buffer
+};
+#ifdef IGM_CHECKS
+static __device__ unsigned igm_chk;
+#define IGM_OK(cond, site) \
+  ((cond) ? true : (atomicCAS(&::igm::igm_chk, 0u, (unsigned)(site)), false))
+// host reader of this translation unit's record (0: every check passed)
+#define IGM_CHECKS_READER(fn)                                  \
+  unsigned fn() {                                              \
+    unsigned v = 0;                                            \
+    if (cudaMemcpyFromSymbol(&v, igm_chk, sizeof(v)) != cudaSuccess) v = ~0u; \
+    return v;                                                  \
+  }
+#else
+#define IGM_OK(cond, site) true
+#define IGM_CHECKS_READER(fn)
+#endif
+
 __device__ __forceinline__ bool out64(i128 x) { return x != (i128)(i64)(u64)x; }
 __device__ __forceinline__ i64 wrap(i128 x) { return (i64)(u64)x; }
 
@@ -481,6 +510,7 @@ __device__ __forceinline__ void fence_mbar_init() {
 // bytes (a multiple of 16) from 16-byte aligned global memory to 16-byte
 // aligned shared memory, completing on bar
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar) {
+  if (!IGM_OK(((smem_u32(dst) | (unsigned)(size_t)src | bytes) & 15u) == 0, CHK_BULK_G2S)) return;
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
@@ -503,6 +533,7 @@ __device__ __forceinline__ void fence_proxy_async() {
 // bytes (a multiple of 16) from 16-byte aligned shared memory to 16-byte
 // aligned global memory, in this thread's current bulk group
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
+  if (!IGM_OK((((unsigned)(size_t)dst | smem_u32(src) | bytes) & 15u) == 0, CHK_BULK_S2G)) return;
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
                    __cvta_generic_to_global(dst)),
                "r"(smem_u32(src)), "r"(bytes)

@@ -27,6 +27,25 @@
     if (e_ != cudaSuccess) return fail(IGM_ECUDA, "launch: %s", cudaGetErrorString(e_)); \
   } while (0)
 
+// NVTX ranges around the host-side phases (build variant "nvtx", -DIGM_NVTX;
+// nothing otherwise): visible in a profiler's timeline
+#ifdef IGM_NVTX
+#include <nvtx3/nvToolsExt.h>
+namespace igm {
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace igm
+#define IGM_RANGE_CAT2(a, b) a##b
+#define IGM_RANGE_CAT(a, b) IGM_RANGE_CAT2(a, b)
+#define IGM_RANGE(name) ::igm::NvtxRange IGM_RANGE_CAT(igm_range_, __LINE__)(name)
+#else
+#define IGM_RANGE(name) ((void)0)
+#endif
+
 using igm::BatchDev;
 using igm::SysDev;
 using igm::SysScal;

@@ -92,6 +92,12 @@ void mgs_plan(const std::vector<int> &n, int max_ctas, int wmax, int snap, bool 
               std::vector<int> &ptr, std::vector<Tile> &seg, int &wrows, int &rows, int &ring,
               std::vector<int> &sys_seg);
 void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st);
+#ifdef IGM_CHECKS
+// checked builds: the first failed device check of each translation unit
+unsigned checks_read_mgs();
+unsigned checks_read_trsv();
+unsigned checks_read_solve();
+#endif
 void launch_backsub(const BatchDev &B, cudaStream_t st);
 void launch_update(const BatchDev &B, cudaStream_t st);
 int norm2_grid(int n);

@@ -631,7 +631,9 @@ __device__ __forceinline__ void seg_spmv(const SysDev *s, const MSegC &c, int j,
       }
       i64 x[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) x[u] = NAR ? (i64)__ldcg(vj32 + cc[u]) : __ldcg(vj + cc[u]);
+      for (int u = 0; u < 8; ++u)
+        x[u] = !IGM_OK((unsigned)cc[u] < (unsigned)c.n, CHK_SPMV_COL) ? 0
+               : NAR ? (i64)__ldcg(vj32 + cc[u]) : __ldcg(vj + cc[u]);
 #pragma unroll
       for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
     }
@@ -760,9 +762,9 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_step_grid(BatchDev B, in
       const int qv = c.active ? res_v(c, k) : 0;
       if (qv == 0) continue;
       const size_t e0 = (size_t)i * c.n + c.row0;
-      const int pad = (int)(e0 & 3);
-      bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)((pad + qv + 3) & ~3),
-               &s_vbar[i & 1]);
+      const int pad = (int)(e0 & 3), words = (pad + qv + 3) & ~3;
+      if (IGM_OK(vbase(c, k, i) - pad + words <= sv + (size_t)((i & 1) + 1) * vb, CHK_MGS_STAGE))
+        bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)words, &s_vbar[i & 1]);
     }
   };
   if (threadIdx.x == 0) stage(0);
@@ -1047,9 +1049,9 @@ __global__ void __launch_bounds__(IGM_MGS_GBS, 1) k_mgs_fused(BatchDev B, int j0
       const int qv = c.active ? res_v(c, k) : 0;
       if (qv == 0) continue;
       const size_t e0 = (size_t)i * c.n + c.row0;
-      const int pad = (int)(e0 & 3);
-      bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)((pad + qv + 3) & ~3),
-               &s_vbar[i & 1]);
+      const int pad = (int)(e0 & 3), words = (pad + qv + 3) & ~3;
+      if (IGM_OK(vbase(c, k, i) - pad + words <= sv + (size_t)((i & 1) + 1) * vb, CHK_MGS_STAGE))
+        bulk_g2s(vbase(c, k, i) - pad, c.V32 + (e0 - pad), 4u * (unsigned)words, &s_vbar[i & 1]);
     }
     s_vn[i & 1] += 1;
   };
@@ -1523,5 +1525,7 @@ void launch_mgs_fused(const BatchDev &B, int j0, int j1, cudaStream_t st) {
                                           dim3(IGM_MGS_GBS), args, IGM_MGS_SMEM(B.mgs_wrows),
                                           st));
 }
+
+IGM_CHECKS_READER(checks_read_mgs)
 
 }  // namespace igm

@@ -92,6 +92,7 @@ void finish(igm_server_s *S, Request *r, igm_status st) {
 // set-up and Fig. 1 initialisation of one admitted request (admission
 // thread, on its stream)
 igm_status admit(igm_server_s *S, Request *r) {
+  IGM_RANGE("serve: admit one request (set-up)");
   igm_status st = int_gmres_setup(r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(),
                                   &r->prm, S->astream, &r->h);
   if (st) return st;
@@ -247,6 +248,7 @@ void worker_main(igm_server_s *S) {
       }
     }
     auto t0 = clk::now();
+    IGM_RANGE("serve: one round over the active requests");
     igm_status st = round(S);
     S->st.busy_s += std::chrono::duration<double>(clk::now() - t0).count();
     if (st) {  // a failed round fails every active request

@@ -356,10 +356,12 @@ __global__ void __launch_bounds__(IGM_BLOCK) k_spmv(BatchDev B, int j) {
         i64 x[8];
         if (narrow) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) x[u] = vj32[c[u]];
+          for (int u = 0; u < 8; ++u)
+            x[u] = IGM_OK((unsigned)c[u] < (unsigned)s->n, CHK_SPMV_COL) ? vj32[c[u]] : 0;
         } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) x[u] = vj[c[u]];
+          for (int u = 0; u < 8; ++u)
+            x[u] = IGM_OK((unsigned)c[u] < (unsigned)s->n, CHK_SPMV_COL) ? vj[c[u]] : 0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc += (i128)mulw(a[u], x[u], ev);
@@ -604,5 +606,7 @@ void launch_gather_state(const BatchDev &B, int4 *out, cudaStream_t st) {
 void launch_update(const BatchDev &B, cudaStream_t st) {
   k_update<<<dim3(B.ntiles, IGM_UPD_SPLIT), IGM_TILE / IGM_UPD_SPLIT, 0, st>>>(B);
 }
+
+IGM_CHECKS_READER(checks_read_solve)
 
 }  // namespace igm

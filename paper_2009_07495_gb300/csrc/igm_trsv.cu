@@ -605,7 +605,8 @@ __global__ void __launch_bounds__(IGM_TRSV_THREADS, 1)
       if (ok) {  // the block's orders are in place
         const int *bord = reinterpret_cast<const int *>(sl) + (size_t)K * trsv_wp(w);
         V *rhs = reinterpret_cast<V *>(sl + Ly.szBlk);
-        for (int r = lane; r < w; r += 32) cp_async8(rhs + r, in + bord[r]);
+        for (int r = lane; r < w; r += 32)
+          if (IGM_OK((unsigned)bord[r] < (unsigned)n, CHK_TRSV_RHS)) cp_async8(rhs + r, in + bord[r]);
       }
       cp_async_arrive_noinc(&s_rdy[k]);
       if (lane == 0) mbar_arrive(&s_rdy[k]);
@@ -977,5 +978,7 @@ void launch_trsv_lv(const BatchDev &B, int kind, int lower, int which, cudaStrea
     else launch_lv<TK_FP, IGM_TRSV_KC_LARGE>(B, lower, which, st);
   }
 }
+
+IGM_CHECKS_READER(checks_read_trsv)
 
 }  // namespace igm

@@ -30,6 +30,19 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), f"libigm.so does not export {n}"
 
 
+def test_checked_and_nvtx_build_exports(lib):
+    """The build variant with device bounds and alignment checks and NVTX
+    ranges (build.py IGM_BUILD=checks+nvtx) compiles for sm_103a and its
+    library loads and exports every entry point of the header (no GPU)."""
+    import ctypes as C
+    from paper_2009_07495_gb300 import build
+    path = build.build(variant="checks+nvtx")
+    assert path != build.LIB and os.path.exists(path)
+    var = C.CDLL(path)
+    for n in _declared_functions():
+        assert hasattr(var, n), f"the checks+nvtx build does not export {n}"
+
+
 def test_default_params_are_the_papers(lib):
     """igm_params_default follows Table 4 / Table 5 and Sec. VII-B (host-only
     call, no device work)."""
