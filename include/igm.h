@@ -47,7 +47,10 @@ typedef enum {
   IGM_ENOCONV = 5,      /* Fig. 1 loop reached max_refine above tol         */
   IGM_EOOM = 6,         /* device memory budget or cudaMalloc exhausted     */
   IGM_ETIMEOUT = 7,     /* a bounded device wait expired                    */
-  IGM_ECUDA = 8         /* a CUDA runtime call failed                       */
+  IGM_ECUDA = 8         /* a CUDA runtime call failed (in the library's
+                           "checks" build variant also: a device bounds or
+                           alignment check failed; igm_last_error names
+                           the site)                                        */
 } igm_status;
 
 /* Indices of igm_report.ev: overflow events per line of Fig. 2. */
